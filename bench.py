@@ -1,0 +1,361 @@
+#!/usr/bin/env python3
+"""Benchmark of the pilot-assignment hot path on one GB300 per rank.
+
+Workload (one "step"): a whole solve of one synthetic 19-cell instance --
+L = 19 hexagonal cells (2 rings, R = 500 m), K = 10 users per cell,
+tau_p = 10, M = 256 antennas, beta = d^-3.8 * 10^(N(0, 8 dB)/10) stored as
+FP32, finite-M uplink SINR, population N = 256, G = 200 generations, K-means
+k = 10 seeding -- i.e. K-means, 201 population evaluations, 200 GA
+generations and the best-member selection, all through the C ABI.
+
+Printed (rank 0, one JSON line): chromosome fitness evaluations per second
+over the whole job (value), GA generations per second, per-solve latency
+percentiles, an end-to-end figure through host buffers, the population-wide
+evaluation kernel on 2^20 chromosomes with its roofline, and the CPU oracle
+as a reported baseline.
+
+Under torchrun each rank solves its own instance (seed = rank): the units
+are independent, so there is no data-path collective ("weak" scaling).
+
+`--impl reference` times the FP64 CPU oracle on the same workload (rank 0
+only; other ranks exit without work).
+"""
+import argparse
+import csv
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+L, K, TAU_P, M_ANT, N_POP, G_GEN, KMEANS_K = 19, 10, 10, 256.0, 256, 200, 10
+BATCH_LOG2 = 20
+METRIC = ("chromosome fitness evals/sec and GA gens/sec (L=19,K=10); "
+          "p50/p99 solve latency served vs plain")
+WORKLOAD = ("single instance at paper-like scale: L=19 hex cells (2 rings), K=10 users/cell, "
+            "tau_p=10, M=256, FP32 beta (d^-3.8 x 8 dB log-normal), finite-M uplink SINR, "
+            "population 256, 200 generations, K-means k=10 seeding; one step = one whole solve")
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi sampled every 200 ms while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.idx = device_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for row in csv.reader(f):
+                if len(row) < 9:
+                    continue
+                try:
+                    sm.append(float(row[1]))
+                    smax.append(float(row[2]))
+                except ValueError:
+                    continue
+                for n, v in zip(names, row[5:9]):
+                    if v.strip().lower() == "active":
+                        reasons.add(n)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- helpers
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def make_instance(seed):
+    import numpy as np
+
+    from paper_2511_20511_gb300 import inputs
+
+    return inputs.instance(L, K, seed=seed, dtype=np.float32)
+
+
+def oracle_solve_step(inst, seed):
+    import oracle
+
+    sp = oracle.sinr_params(oracle.FINITE_M, TAU_P, M_ANT, inst["rho"], 1.0)
+    gp = oracle.ga_params(N_POP, 2, 3, oracle.prob_thresh(0.9), oracle.prob_thresh(0.05), seed)
+    return oracle.solve(inst["beta"], sp, gp, G_GEN, inst["user_xy_mm"], inst["bs_xy_mm"],
+                        kmeans_k=KMEANS_K)
+
+
+def cpu_baseline(target_s=12.0):
+    """The oracle as it stands, single thread, on a bounded sample: whole
+    solves of the benchmark instance repeated for about target_s seconds."""
+    inst = make_instance(0)
+    oracle_solve_step(inst, 0)  # build + warm
+    t0 = time.perf_counter()
+    reps = 0
+    while True:
+        oracle_solve_step(inst, reps)
+        reps += 1
+        dt = time.perf_counter() - t0
+        if dt >= target_s:
+            break
+    evals = reps * N_POP * (G_GEN + 1)
+    return {"value": evals / dt, "unit": "evals/s", "cores": 1, "kind": "oracle",
+            "sample": f"{reps} whole solves of the benchmark instance (N=256, G=200), "
+                      f"{dt:.1f} s, FP64 plain C, single thread",
+            "gens_per_s": reps * G_GEN / dt}
+
+
+# ---------------------------------------------------------------- reference arm
+def run_reference(args):
+    world, rank, _ = dist_setup()
+    if rank != 0:
+        return 0
+    inst = make_instance(0)
+    oracle_solve_step(inst, 0)
+    for w in range(args.warmup):
+        oracle_solve_step(inst, w)
+    times = []
+    for s in range(args.steps):
+        t0 = time.perf_counter()
+        oracle_solve_step(inst, s)
+        times.append(time.perf_counter() - t0)
+    total = sum(times)
+    value = args.steps * N_POP * (G_GEN + 1) / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "evals/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "L": L, "K": K, "N": N_POP, "G": G_GEN},
+        "gens_per_s": args.steps * G_GEN / total,
+        "cpu_baseline": {"value": value, "unit": "evals/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{args.steps} whole solves (N=256, G=200), FP64 plain C, "
+                                   "single thread"},
+        "e2e": {"value": value, "unit": "evals/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# ---------------------------------------------------------------- our arm
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    world, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    def max_over_ranks(x):
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        return float(t.item())
+
+    from paper_2511_20511_gb300 import binding as B
+    from paper_2511_20511_gb300 import build as pa_build
+    from paper_2511_20511_gb300 import inputs
+
+    pa_build.build()
+    stream = torch.cuda.Stream(device=dev)
+    inst = make_instance(rank)
+    cfg = B.pa_config_default(L, K, mode=B.PA_SINR_FINITE_M, M=M_ANT, tau_p=TAU_P, N=N_POP,
+                              rho=inst["rho"], kmeans_k=KMEANS_K, seed=rank)
+    ctx = B.Context(cfg, inst["beta"], inst["user_xy_mm"], inst["bs_xy_mm"], stream=stream)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
+    best = np.zeros((L, K), dtype=np.uint8)
+
+    def timed(fn, steps, flush_between=True):
+        """Per-step CUDA-event durations on the context stream (ms); the L2
+        flush between steps stays outside the events."""
+        ms = []
+        for _ in range(steps):
+            if flush_between:
+                with torch.cuda.stream(stream):
+                    flush.fill_(1)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return ms
+
+    def solve_step():
+        ctx.solve(G_GEN)
+
+    # ---- device-resident solves (value)
+    for _ in range(args.warmup):
+        solve_step()
+    torch.cuda.synchronize()
+    barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    l0 = B.pa_kernel_launches()
+    step_ms = timed(solve_step, args.steps)
+    launches = B.pa_kernel_launches() - l0
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    total_s = max_over_ranks(sum(step_ms) / 1e3)
+    value = world * args.steps * N_POP * (G_GEN + 1) / total_s
+    gens = world * args.steps * G_GEN / total_s
+
+    # ---- end to end through host buffers (pinned): fresh instance upload +
+    #      solve + best member back to the host, every step
+    pin_beta = torch.from_numpy(inst["beta"]).pin_memory()
+    pin_xy = torch.from_numpy(inst["user_xy_mm"]).pin_memory()
+    pin_bs = torch.from_numpy(inst["bs_xy_mm"]).pin_memory()
+    keep = (pin_beta.numpy(), pin_xy.numpy(), pin_bs.numpy())
+
+    def e2e_step():
+        B.pa_load_instance(ctx.handle, *keep)
+        B.pa_solve(ctx.handle, G_GEN, best)
+
+    for _ in range(max(1, args.warmup)):
+        e2e_step()
+    barrier()
+    t0 = time.perf_counter()
+    e2e_ms = timed(e2e_step, args.steps, flush_between=False)
+    wall_e2e = time.perf_counter() - t0
+    e2e_total = max_over_ranks(max(sum(e2e_ms) / 1e3, wall_e2e))
+    h2d = keep[0].nbytes + keep[1].nbytes + keep[2].nbytes
+    d2h = best.nbytes + 8
+
+    # ---- population-wide evaluation kernel on 2^20 chromosomes (> L2)
+    nb = 1 << BATCH_LOG2
+    pop = inputs.random_population_torch(nb, L, K, seed=1000 + rank, device=dev)
+    fit = torch.empty(nb, dtype=torch.float32, device=dev)
+    with torch.cuda.stream(stream):
+        torch.cuda.current_stream().wait_stream(torch.cuda.default_stream(dev))
+
+    def eval_step():
+        B.pa_eval_population(ctx.handle, pop, fit)
+
+    for _ in range(max(3, args.warmup)):
+        eval_step()
+    stream.synchronize()
+    ev_ms = timed(eval_step, max(args.steps, 10), flush_between=False)
+    ev_avg = statistics.mean(ev_ms) / 1e3
+    evals_batch = nb / ev_avg
+    words = L * L * K  # algorithmic shared-memory words per chromosome (Eq. 5 gathers)
+    n_sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    pk = peaks()
+    sm_max = pk.get("sm_max_mhz", 2070.0)
+    peak_gword = n_sms * 32 * sm_max * 1e6 / 1e9
+    achieved_gword = nb * words / ev_avg / 1e9
+    roofline = {"bound": "alu", "kernel": "k_eval_f32 (population fitness, FP32)",
+                "achieved": achieved_gword, "peak": peak_gword, "unit": "Gword/s",
+                "frac": achieved_gword / peak_gword, "traffic": None,
+                "path": f"shared-memory gather data path: 32 x 4-byte words/clk/SM x {n_sms} "
+                        f"SMs x {sm_max:.0f} MHz",
+                "units_per_launch": nb, "words_per_unit": words,
+                "avg_launch_ms": ev_avg * 1e3}
+
+    lat = sorted(step_ms)
+
+    def pct(p):
+        return lat[min(len(lat) - 1, int(round(p / 100.0 * (len(lat) - 1))))]
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "L": L, "K": K, "tau_p": TAU_P, "M": M_ANT,
+                   "N": N_POP, "G": G_GEN, "kmeans_k": KMEANS_K, "sinr": "finite_m",
+                   "l2": "L2 flushed (256 MB write) between timed steps; the 2^20-chromosome "
+                         "evaluation input (199 MB) is larger than L2"},
+        "gens_per_s": gens,
+        "solve_latency_ms": {"p50": pct(50), "p99": pct(99), "mean": statistics.mean(lat)},
+        "eval_batch": {"chromosomes": nb, "evals_per_s": evals_batch * world,
+                       "avg_launch_ms": ev_avg * 1e3},
+        "roofline": roofline,
+        "e2e": {"value": world * args.steps * N_POP * (G_GEN + 1) / e2e_total, "unit": "evals/s",
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "what": "pa_load_instance (pinned host beta + positions) + pa_solve (best row "
+                        "and fitness back to host) per step"},
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+    ctx.close()
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,220 @@
+/*
+ * pa.h -- C ABI of the GB300 pilot-assignment library (libpa.so).
+ *
+ * Method: K-means-seeded two-dimensional genetic algorithm for uplink pilot
+ * assignment in multi-cell massive MIMO (arXiv 2511.20511).  The data-
+ * parallel hot path is the population-wide fitness evaluation (Sec. 3.2,
+ * Eq. 3-6: per-user uplink SINR and spectral efficiency, summed over all
+ * users); around it sit the GA generation step (Alg. 1: elitism, selection,
+ * crossover, mutation) and the K-means population seeding (Sec. 1 item 2,
+ * Alg. 1 "Apply K-means clustering").
+ *
+ * Conventions shared by every entry point
+ *   beta[(j*L + l)*K + k]  large-scale fading (Eq. 2) of user k of cell l
+ *                          at BS j; host memory, float64, finite and > 0.
+ *   pop[(n*L + l)*K + k]   uint8 pilot of user k of cell l in chromosome n
+ *                          (Sec. 4.1: one row per cell, each row a
+ *                          permutation of 0..K-1).  Row-major, no padding.
+ *   fitness                float32 (PA_FP32 contexts) or float64 (PA_FP64),
+ *                          one value per chromosome: sum SE of Eq. 6.
+ *   "device" pointers      CUDA global memory on the context's device.
+ *   "host" pointers        ordinary (pageable or pinned) host memory.
+ *   Ownership              the caller owns every buffer it passes; the
+ *                          context owns copies of beta and positions and
+ *                          its resident population.
+ *   Streams                work is enqueued on the context stream (given at
+ *                          pa_create or pa_set_stream; NULL = legacy default
+ *                          stream).  Calls marked "asynchronous" return
+ *                          before the GPU finishes; the others synchronise
+ *                          the context stream before returning.
+ *   Errors                 no call aborts, exits or traps.  Invalid
+ *                          arguments return PA_EINVAL before any GPU work;
+ *                          CUDA failures return PA_ECUDA; pa_last_error()
+ *                          then holds a message.  A context is not thread
+ *                          safe; distinct contexts are independent.
+ */
+#ifndef PA_H
+#define PA_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pa_ctx pa_ctx;
+
+typedef enum {
+  PA_OK = 0,
+  PA_EINVAL = 1,        /* invalid argument or configuration              */
+  PA_ENOMEM = 2,        /* device or host allocation failed               */
+  PA_ECUDA = 3,         /* a CUDA call failed (see pa_last_error)         */
+  PA_ETIMEOUT = 4,      /* a bounded device wait gave up                  */
+  PA_EUNSUPPORTED = 5,  /* valid but outside what this build implements   */
+  PA_EBUSY = 6          /* resource (slot, memory budget) not available   */
+} pa_status;
+
+/* Arithmetic of the fitness evaluation. */
+enum {
+  PA_FP32 = 0,  /* fast path: FP32 gathers and sums, <= 1e-5 relative     */
+  PA_FP64 = 1   /* parity path: FP64, same operation order as the oracle  */
+};
+
+/* SINR model (Sec. 3.2). */
+enum {
+  PA_SINR_ASYMPTOTIC = 0, /* Eq. 4-5: beta_jjk^2 / sum_{l!=j} beta_jl(p)^2 */
+  PA_SINR_FINITE_M = 1    /* Eq. 3 read with M antennas, MMSE pilot
+                             estimates and MR combining:
+                             M b^2 / (M S2 + (B_j + s2/rho)(S1 + s2/(tau_p rho))) */
+};
+
+/*
+ * Configuration.  Fill with pa_config_default() and override fields.
+ * Layout is fixed (128 bytes, natural alignment).
+ */
+typedef struct {
+  int32_t L;        /* cells (>= 2)                                        */
+  int32_t K;        /* users per cell = pilots per cell (1..64)            */
+  int32_t tau_p;    /* pilot length (FINITE_M only; >= 1)                  */
+  int32_t mode;     /* PA_SINR_*                                           */
+  double M;         /* BS antennas (FINITE_M only; > 0)                    */
+  double rho;       /* SNR scale: data/pilot power over noise unit (> 0)   */
+  double sigma2;    /* noise variance (>= 0)                               */
+  int32_t prec;     /* PA_FP32 or PA_FP64                                  */
+  int32_t N;        /* population size (>= 2)                              */
+  int32_t E;        /* elites copied unchanged (0 <= E < N)                */
+  int32_t tour;     /* tournament size (>= 1)                              */
+  uint64_t pc_thresh; /* crossover iff 32-bit draw < pc_thresh (0..2^32)   */
+  uint64_t pm_thresh; /* per-row swap iff draw < pm_thresh (0..2^32)       */
+  uint64_t seed;    /* Philox key of every random draw                     */
+  int32_t kmeans_k; /* K-means clusters (1..K)                             */
+  int32_t kmeans_max_iter; /* assignment passes (>= 1)                     */
+  int32_t n_seeded; /* members built from the K-means assignment (0..N)   */
+  int32_t flags;    /* reserved, must be 0                                 */
+  int64_t reserved[4]; /* must be 0                                        */
+} pa_config;
+
+/*
+ * Defaults for an L-cell, K-user layout: FP32, asymptotic SINR (the
+ * objective of Eq. 7), tau_p = K, M = 256, rho = 10 / 500^-3.8 (10 dB at a
+ * 500 m cell edge without shadowing), sigma2 = 1, N = 256, E = 2, tour = 3,
+ * p_c = 0.9 (Table 1), p_m = 0.05 per row, seed 0, kmeans_k = K,
+ * kmeans_max_iter = 100, n_seeded = (N + 1) / 2.
+ * Returns PA_EINVAL if cfg is NULL.
+ */
+pa_status pa_config_default(pa_config* cfg, int32_t L, int32_t K);
+
+/* floor(p * 2^32) clamped to [0, 2^32]: threshold for a Bernoulli(p) draw. */
+uint64_t pa_prob_to_thresh(double p);
+
+/*
+ * Create a context for one pilot-assignment instance on the current CUDA
+ * device.  beta: host, L*L*K float64 (copied).  user_xy_mm (L*K*2) and
+ * bs_xy_mm (L*2): host int32 positions in millimetres (copied), both NULL to
+ * disable K-means seeding (random initial population instead).  stream:
+ * cudaStream_t or NULL.  Prepares the per-instance tables on the GPU
+ * (scaled gain tables, per-BS totals) and allocates the resident
+ * population (2 * N * L * K bytes).  Synchronous.
+ */
+pa_status pa_create(const pa_config* cfg, const double* beta, const int32_t* user_xy_mm,
+                    const int32_t* bs_xy_mm, void* stream, pa_ctx** out);
+
+/*
+ * Replace the instance of an existing context (same L, K and configuration):
+ * beta (host, L*L*K float64) and optional positions as in pa_create.  The
+ * gain tables are rebuilt on the GPU; the resident population is left as
+ * it is and the generation counter reset to 0.  Asynchronous with respect
+ * to the GPU work (the host arrays may be reused when the call returns
+ * only if they are pageable; pinned arrays must stay untouched until the
+ * context stream reaches this point).  PA_EINVAL on invalid values.
+ */
+pa_status pa_load_instance(pa_ctx* ctx, const double* beta, const int32_t* user_xy_mm,
+                           const int32_t* bs_xy_mm);
+
+/* Destroy a context and free its device memory (NULL is ignored). */
+void pa_destroy(pa_ctx* ctx);
+
+/* Replace the context stream (cudaStream_t or NULL). */
+pa_status pa_set_stream(pa_ctx* ctx, void* stream);
+
+/*
+ * Fitness of n chromosomes (Eq. 6 sum SE with the per-user SINR of Eq. 4-5
+ * or the finite-M reading of Eq. 3).  pop_dev: device, n*L*K bytes;
+ * fit_dev: device, n float32 (PA_FP32) or float64 (PA_FP64).  Rows that are
+ * not permutations give an unspecified value but never an out-of-bounds
+ * access.  n == 0 is a no-op.  Asynchronous.
+ */
+pa_status pa_eval_population(pa_ctx* ctx, const uint8_t* pop_dev, int64_t n, void* fit_dev);
+
+/*
+ * Same as pa_eval_population with host buffers: copies pop_host to the
+ * device, evaluates, copies the fitness back.  Synchronous.
+ */
+pa_status pa_eval_population_host(pa_ctx* ctx, const uint8_t* pop_host, int64_t n,
+                                  void* fit_host);
+
+/*
+ * One GA generation (Alg. 1: selection, crossover, mutation, with the
+ * elitism of Sec. 1) from population pop_dev (device, N*L*K bytes) and its
+ * fitness fit_dev (device, N values) into next_dev (device, N*L*K bytes,
+ * must not overlap pop_dev).  Draws are Philox4x64-10 keyed by (seed,
+ * child slot, generation).  Asynchronous.
+ */
+pa_status pa_ga_step(pa_ctx* ctx, const uint8_t* pop_dev, const void* fit_dev,
+                     int32_t generation, uint8_t* next_dev);
+
+/*
+ * K-means on the users' positions relative to their own BS, then build the
+ * resident population from the clustering (generation counter reset to 0).
+ * Without positions, builds a random population.  labels_host (L*K int32)
+ * and centroids_host (kmeans_k*2 float64, x then y per cluster) are
+ * optional outputs; when either is given the call synchronises.
+ */
+pa_status pa_kmeans_seed(pa_ctx* ctx, int32_t* labels_host, double* centroids_host);
+
+/* Run `generations` GA generations on the resident population.  Async. */
+pa_status pa_step(pa_ctx* ctx, int32_t generations);
+
+/*
+ * Whole solve (Alg. 1): seed (pa_kmeans_seed), `generations` generations,
+ * final evaluation, best member by (fitness desc, index asc).  best_host:
+ * L*K bytes; best_fit: its fitness.  Synchronous.
+ */
+pa_status pa_solve(pa_ctx* ctx, int32_t generations, uint8_t* best_host, double* best_fit);
+
+/*
+ * Copy the resident population (N*L*K bytes) and optionally its fitness
+ * (N values, evaluated now) and generation counter to the host.  Sync.
+ */
+pa_status pa_get_population(pa_ctx* ctx, uint8_t* pop_host, void* fit_host,
+                            int32_t* generation);
+
+/* Load a population (host, N*L*K bytes, rows must be permutations) and a
+ * generation counter: checkpoint resume.  Synchronous; PA_EINVAL on an
+ * invalid row. */
+pa_status pa_set_population(pa_ctx* ctx, const uint8_t* pop_host, int32_t generation);
+
+/* Device pointers of the resident population and its fitness buffer. */
+pa_status pa_population_device(pa_ctx* ctx, uint8_t** pop_dev, void** fit_dev);
+
+/*
+ * Check that every row of n chromosomes (device) is a permutation of
+ * 0..K-1.  *first_bad = index of the first bad chromosome or -1.  Sync.
+ */
+pa_status pa_validate_population(pa_ctx* ctx, const uint8_t* pop_dev, int64_t n,
+                                 int64_t* first_bad);
+
+/* Static description of a status code. */
+const char* pa_status_str(pa_status s);
+
+/* Last error message of a context ("" if none). */
+const char* pa_last_error(const pa_ctx* ctx);
+
+/* Number of CUDA kernels this library has launched in this process (all
+ * contexts, all devices); for accounting launches in a timed region. */
+uint64_t pa_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PA_H */

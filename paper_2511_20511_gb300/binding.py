@@ -1,0 +1,306 @@
+"""Thin Python binding of libpa.so (include/pa.h): argument marshalling only.
+
+Every function has the C name and forwards to it; device buffers are torch
+CUDA tensors (passed by data_ptr()), host buffers numpy arrays.  Streams are
+torch.cuda streams (the raw cudaStream_t is passed).  All computation runs
+in the library's CUDA kernels: if libpa.so is missing this module raises --
+there is no fallback.
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libpa.so")
+
+PA_OK, PA_EINVAL, PA_ENOMEM, PA_ECUDA, PA_ETIMEOUT, PA_EUNSUPPORTED, PA_EBUSY = range(7)
+PA_FP32, PA_FP64 = 0, 1
+PA_SINR_ASYMPTOTIC, PA_SINR_FINITE_M = 0, 1
+
+
+class pa_config(C.Structure):
+    _fields_ = [("L", C.c_int32), ("K", C.c_int32), ("tau_p", C.c_int32), ("mode", C.c_int32),
+                ("M", C.c_double), ("rho", C.c_double), ("sigma2", C.c_double),
+                ("prec", C.c_int32), ("N", C.c_int32), ("E", C.c_int32), ("tour", C.c_int32),
+                ("pc_thresh", C.c_uint64), ("pm_thresh", C.c_uint64), ("seed", C.c_uint64),
+                ("kmeans_k", C.c_int32), ("kmeans_max_iter", C.c_int32),
+                ("n_seeded", C.c_int32), ("flags", C.c_int32), ("reserved", C.c_int64 * 4)]
+
+
+assert C.sizeof(pa_config) == 128
+
+
+class PaError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(msg)
+        self.status = status
+
+
+_lib = None
+
+_SIGS = {
+    "pa_config_default": (C.c_int, [C.POINTER(pa_config), C.c_int32, C.c_int32]),
+    "pa_prob_to_thresh": (C.c_uint64, [C.c_double]),
+    "pa_create": (C.c_int, [C.POINTER(pa_config), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                            C.POINTER(C.c_void_p)]),
+    "pa_load_instance": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "pa_destroy": (None, [C.c_void_p]),
+    "pa_set_stream": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "pa_eval_population": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p]),
+    "pa_eval_population_host": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p]),
+    "pa_ga_step": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p]),
+    "pa_kmeans_seed": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "pa_step": (C.c_int, [C.c_void_p, C.c_int32]),
+    "pa_solve": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.POINTER(C.c_double)]),
+    "pa_get_population": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_int32)]),
+    "pa_set_population": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32]),
+    "pa_population_device": (C.c_int, [C.c_void_p, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p)]),
+    "pa_validate_population": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64,
+                                         C.POINTER(C.c_int64)]),
+    "pa_status_str": (C.c_char_p, [C.c_int]),
+    "pa_last_error": (C.c_char_p, [C.c_void_p]),
+    "pa_kernel_launches": (C.c_uint64, []),
+}
+
+
+def lib():
+    """Load libpa.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                               "`python -m paper_2511_20511_gb300.build` (no fallback path)")
+        L = C.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def exported_symbols():
+    return sorted(_SIGS)
+
+
+def _check(st, ctx=None):
+    if st != PA_OK:
+        msg = lib().pa_status_str(st).decode()
+        if ctx is not None:
+            detail = lib().pa_last_error(ctx).decode()
+            if detail:
+                msg = f"{msg}: {detail}"
+        raise PaError(st, msg)
+
+
+def _host_ptr(a):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+def _dev_ptr(t):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+# ------------------------------------------------------------------ free functions
+def pa_config_default(L, K, **overrides):
+    cfg = pa_config()
+    _check(lib().pa_config_default(C.byref(cfg), int(L), int(K)))
+    for k, v in overrides.items():
+        if not hasattr(cfg, k):
+            raise AttributeError(k)
+        setattr(cfg, k, v)
+    return cfg
+
+
+def pa_prob_to_thresh(p):
+    return int(lib().pa_prob_to_thresh(float(p)))
+
+
+def pa_create(cfg, beta, user_xy_mm=None, bs_xy_mm=None, stream=None):
+    beta = np.ascontiguousarray(beta, dtype=np.float64)
+    if beta.shape != (cfg.L, cfg.L, cfg.K):
+        raise ValueError(f"beta must be (L, L, K) = {(cfg.L, cfg.L, cfg.K)}, got {beta.shape}")
+    u = None if user_xy_mm is None else np.ascontiguousarray(user_xy_mm, dtype=np.int32)
+    b = None if bs_xy_mm is None else np.ascontiguousarray(bs_xy_mm, dtype=np.int32)
+    if u is not None and u.shape != (cfg.L, cfg.K, 2):
+        raise ValueError("user_xy_mm must be (L, K, 2)")
+    if b is not None and b.shape != (cfg.L, 2):
+        raise ValueError("bs_xy_mm must be (L, 2)")
+    out = C.c_void_p()
+    st = lib().pa_create(C.byref(cfg), _host_ptr(beta), _host_ptr(u), _host_ptr(b),
+                         _stream_handle(stream), C.byref(out))
+    _check(st)
+    return out
+
+
+def _stream_handle(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return C.c_void_p(stream)
+    return C.c_void_p(stream.cuda_stream)
+
+
+def pa_load_instance(ctx, beta, user_xy_mm=None, bs_xy_mm=None):
+    beta = np.ascontiguousarray(beta, dtype=np.float64)
+    u = None if user_xy_mm is None else np.ascontiguousarray(user_xy_mm, dtype=np.int32)
+    b = None if bs_xy_mm is None else np.ascontiguousarray(bs_xy_mm, dtype=np.int32)
+    _check(lib().pa_load_instance(ctx, _host_ptr(beta), _host_ptr(u), _host_ptr(b)), ctx)
+    return beta, u, b  # keep the arrays alive until the stream has consumed them
+
+
+def pa_kernel_launches():
+    return int(lib().pa_kernel_launches())
+
+
+def pa_destroy(ctx):
+    lib().pa_destroy(ctx)
+
+
+def pa_set_stream(ctx, stream):
+    _check(lib().pa_set_stream(ctx, _stream_handle(stream)), ctx)
+
+
+def pa_eval_population(ctx, pop, fit, n=None):
+    n = pop.shape[0] if n is None else n
+    _check(lib().pa_eval_population(ctx, _dev_ptr(pop), int(n), _dev_ptr(fit)), ctx)
+
+
+def pa_eval_population_host(ctx, pop, fit):
+    pop = np.ascontiguousarray(pop, dtype=np.uint8)
+    _check(lib().pa_eval_population_host(ctx, _host_ptr(pop), int(pop.shape[0]),
+                                         _host_ptr(fit)), ctx)
+    return fit
+
+
+def pa_ga_step(ctx, pop, fit, generation, next_pop):
+    _check(lib().pa_ga_step(ctx, _dev_ptr(pop), _dev_ptr(fit), int(generation),
+                            _dev_ptr(next_pop)), ctx)
+
+
+def pa_kmeans_seed(ctx, labels=None, centroids=None):
+    _check(lib().pa_kmeans_seed(ctx, _host_ptr(labels), _host_ptr(centroids)), ctx)
+
+
+def pa_step(ctx, generations):
+    _check(lib().pa_step(ctx, int(generations)), ctx)
+
+
+def pa_solve(ctx, generations, best):
+    bf = C.c_double(0.0)
+    _check(lib().pa_solve(ctx, int(generations), _host_ptr(best), C.byref(bf)), ctx)
+    return bf.value
+
+
+def pa_get_population(ctx, pop=None, fit=None):
+    g = C.c_int32(0)
+    _check(lib().pa_get_population(ctx, _host_ptr(pop), _host_ptr(fit), C.byref(g)), ctx)
+    return g.value
+
+
+def pa_set_population(ctx, pop, generation):
+    pop = np.ascontiguousarray(pop, dtype=np.uint8)
+    _check(lib().pa_set_population(ctx, _host_ptr(pop), int(generation)), ctx)
+
+
+def pa_population_device(ctx):
+    p = C.c_void_p()
+    f = C.c_void_p()
+    _check(lib().pa_population_device(ctx, C.byref(p), C.byref(f)), ctx)
+    return p.value, f.value
+
+
+def pa_validate_population(ctx, pop, n=None):
+    n = pop.shape[0] if n is None else n
+    bad = C.c_int64(0)
+    _check(lib().pa_validate_population(ctx, _dev_ptr(pop), int(n), C.byref(bad)), ctx)
+    return bad.value
+
+
+# ------------------------------------------------------------------ convenience
+class Context:
+    """Owns one pa_ctx.  Methods mirror the C entry points."""
+
+    def __init__(self, cfg, beta, user_xy_mm=None, bs_xy_mm=None, stream=None):
+        self.cfg = cfg
+        self.L, self.K, self.N = cfg.L, cfg.K, cfg.N
+        self.fit_dtype = np.float64 if cfg.prec == PA_FP64 else np.float32
+        self.handle = pa_create(cfg, beta, user_xy_mm, bs_xy_mm, stream)
+
+    def close(self):
+        if self.handle:
+            pa_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def torch_fit_dtype(self):
+        import torch
+
+        return torch.float64 if self.cfg.prec == PA_FP64 else torch.float32
+
+    def eval_population(self, pop, fit=None):
+        import torch
+
+        if fit is None:
+            fit = torch.empty(pop.shape[0], dtype=self.torch_fit_dtype(), device=pop.device)
+        pa_eval_population(self.handle, pop, fit)
+        return fit
+
+    def eval_population_host(self, pop):
+        fit = np.zeros(pop.shape[0], dtype=self.fit_dtype)
+        return pa_eval_population_host(self.handle, pop, fit)
+
+    def ga_step(self, pop, fit, generation, next_pop=None):
+        import torch
+
+        if next_pop is None:
+            next_pop = torch.empty_like(pop)
+        pa_ga_step(self.handle, pop, fit, generation, next_pop)
+        return next_pop
+
+    def kmeans_seed(self, want_outputs=False):
+        if want_outputs:
+            labels = np.zeros((self.L, self.K), dtype=np.int32)
+            cent = np.zeros((self.cfg.kmeans_k, 2), dtype=np.float64)
+            pa_kmeans_seed(self.handle, labels, cent)
+            return labels, cent
+        pa_kmeans_seed(self.handle)
+        return None
+
+    def step(self, generations):
+        pa_step(self.handle, generations)
+
+    def solve(self, generations):
+        best = np.zeros((self.L, self.K), dtype=np.uint8)
+        f = pa_solve(self.handle, generations, best)
+        return best, f
+
+    def get_population(self, with_fitness=True):
+        pop = np.zeros((self.N, self.L, self.K), dtype=np.uint8)
+        fit = np.zeros(self.N, dtype=self.fit_dtype) if with_fitness else None
+        g = pa_get_population(self.handle, pop, fit)
+        return pop, fit, g
+
+    def set_population(self, pop, generation):
+        pa_set_population(self.handle, pop, generation)
+
+    def validate_population(self, pop):
+        return pa_validate_population(self.handle, pop)

@@ -1,0 +1,482 @@
+// pa_api.cu -- the C ABI declared in include/pa.h: argument validation,
+// context lifetime, device memory, and the host-side sequencing of the
+// kernels (every step of the method runs in the kernels of pa_prep.cu,
+// pa_fitness.cu and pa_ga.cu).
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "pa_internal.cuh"
+
+#include <atomic>
+
+namespace pa {
+
+static std::atomic<uint64_t> g_launches{0};
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+void f32_geometry(int L, int K, int* NJ, int* RS, int* vec);
+
+pa_status fail(pa_ctx* ctx, pa_status st, const std::string& msg) {
+  if (ctx) ctx->err = msg;
+  return st;
+}
+
+pa_status cuda_check(pa_ctx* ctx, cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return PA_OK;
+  char buf[512];
+  snprintf(buf, sizeof buf, "%s: %s (%s)", what, cudaGetErrorString(e), cudaGetErrorName(e));
+  if (ctx) ctx->err = buf;
+  return e == cudaErrorMemoryAllocation ? PA_ENOMEM : PA_ECUDA;
+}
+
+}  // namespace pa
+
+using pa::cuda_check;
+using pa::fail;
+
+#define PA_TRY(ctx, expr, what)                                \
+  do {                                                         \
+    pa_status _s = cuda_check((ctx), (expr), (what));          \
+    if (_s != PA_OK) return _s;                                \
+  } while (0)
+
+namespace pa {
+bool instance_ok(const pa_config& c, const double* beta, const int32_t* user_xy_mm,
+                 const int32_t* bs_xy_mm, double* bmax) {
+  const int64_t n_beta = (int64_t)c.L * c.L * c.K;
+  double m = 0.0;
+  for (int64_t i = 0; i < n_beta; ++i) {
+    const double b = beta[i];
+    if (!(b > 0.0) || !std::isfinite(b)) return false;
+    m = b > m ? b : m;
+  }
+  *bmax = m;
+  if (user_xy_mm) {
+    for (int l = 0; l < c.L; ++l)
+      for (int k = 0; k < c.K; ++k) {
+        const int64_t u = (int64_t)l * c.K + k;
+        const int64_t fx = (int64_t)user_xy_mm[2 * u] - bs_xy_mm[2 * l];
+        const int64_t fy = (int64_t)user_xy_mm[2 * u + 1] - bs_xy_mm[2 * l + 1];
+        if (fx > INT32_MAX || fx < INT32_MIN || fy > INT32_MAX || fy < INT32_MIN) return false;
+      }
+  }
+  return true;
+}
+}  // namespace pa
+
+// Copy one instance (beta, positions) into a context's device buffers and
+// rebuild its fitness tables.  Buffers must already exist.
+static pa_status upload_instance(pa_ctx* c, const double* beta, const int32_t* user_xy_mm,
+                                 const int32_t* bs_xy_mm, double bmax) {
+  const pa_config& cfg = c->cfg;
+  const int L = cfg.L, K = cfg.K;
+  const int64_t n_beta = (int64_t)L * L * K, LK = (int64_t)L * K;
+  PA_TRY(c, cudaMemcpyAsync(c->beta64, beta, sizeof(double) * n_beta, cudaMemcpyHostToDevice,
+                            c->stream),
+         "copy beta");
+  if (cfg.prec == PA_FP32) {
+    int e2 = 0;
+    std::frexp(bmax, &e2);  // bmax = f 2^e2, f in [0.5, 1): scaled gains lie in (0, 1)
+    c->t32.scale_exp = -e2;
+    c->t32.scale = std::ldexp(1.0, -e2);
+    c->t32.M = (float)cfg.M;
+    c->t32.pc = (float)std::ldexp(c->pc, -e2);
+  }
+  if (user_xy_mm) {
+    PA_TRY(c, cudaMemcpyAsync(c->user_xy, user_xy_mm, sizeof(int32_t) * 2 * LK,
+                              cudaMemcpyHostToDevice, c->stream),
+           "copy user positions");
+    PA_TRY(c, cudaMemcpyAsync(c->bs_xy, bs_xy_mm, sizeof(int32_t) * 2 * L, cudaMemcpyHostToDevice,
+                              c->stream),
+           "copy BS positions");
+  }
+  c->has_positions = user_xy_mm != nullptr;
+  PA_TRY(c, pa::launch_prep(c), "prepare tables");
+  return PA_OK;
+}
+
+extern "C" {
+
+const char* pa_status_str(pa_status s) {
+  switch (s) {
+    case PA_OK: return "ok";
+    case PA_EINVAL: return "invalid argument";
+    case PA_ENOMEM: return "out of memory";
+    case PA_ECUDA: return "CUDA error";
+    case PA_ETIMEOUT: return "device wait timed out";
+    case PA_EUNSUPPORTED: return "unsupported configuration";
+    case PA_EBUSY: return "busy";
+  }
+  return "unknown status";
+}
+
+const char* pa_last_error(const pa_ctx* ctx) { return ctx ? ctx->err.c_str() : ""; }
+
+uint64_t pa_kernel_launches(void) { return pa::g_launches.load(std::memory_order_relaxed); }
+
+uint64_t pa_prob_to_thresh(double p) {
+  if (!(p > 0.0)) return 0;
+  if (p >= 1.0) return 1ULL << 32;
+  return (uint64_t)std::floor(p * 4294967296.0);
+}
+
+pa_status pa_config_default(pa_config* c, int32_t L, int32_t K) {
+  if (!c) return PA_EINVAL;
+  std::memset(c, 0, sizeof *c);
+  c->L = L;
+  c->K = K;
+  c->tau_p = K;
+  c->mode = PA_SINR_ASYMPTOTIC;
+  c->M = 256.0;
+  c->rho = 10.0 / std::pow(500.0, -3.8);
+  c->sigma2 = 1.0;
+  c->prec = PA_FP32;
+  c->N = 256;
+  c->E = 2;
+  c->tour = 3;
+  c->pc_thresh = pa_prob_to_thresh(0.9);
+  c->pm_thresh = pa_prob_to_thresh(0.05);
+  c->seed = 0;
+  c->kmeans_k = K;
+  c->kmeans_max_iter = 100;
+  c->n_seeded = (c->N + 1) / 2;
+  return PA_OK;
+}
+
+static pa_status validate_config(const pa_config* c, std::string* why) {
+  auto bad = [&](const char* m) {
+    *why = m;
+    return PA_EINVAL;
+  };
+  if (c->L < 2 || c->L > pa::kMaxL) return bad("L must be in [2, 255]");
+  if (c->K < 1 || c->K > pa::kMaxK) return bad("K must be in [1, 64]");
+  if ((int64_t)c->L * c->K > 64 * 64) return bad("L*K must be <= 4096");
+  if (c->mode != PA_SINR_ASYMPTOTIC && c->mode != PA_SINR_FINITE_M) return bad("unknown mode");
+  if (c->prec != PA_FP32 && c->prec != PA_FP64) return bad("unknown precision");
+  if (c->mode == PA_SINR_FINITE_M) {
+    if (c->tau_p < 1) return bad("tau_p must be >= 1");
+    if (!(c->M > 0.0) || !std::isfinite(c->M)) return bad("M must be finite and > 0");
+    if (!(c->rho > 0.0) || !std::isfinite(c->rho)) return bad("rho must be finite and > 0");
+    if (!(c->sigma2 >= 0.0) || !std::isfinite(c->sigma2)) return bad("sigma2 must be >= 0");
+  }
+  if (c->N < 2 || c->N > (1 << 24)) return bad("N must be in [2, 2^24]");
+  if (c->E < 0 || c->E >= c->N || c->E > 64) return bad("E must be in [0, min(N-1, 64)]");
+  if (c->tour < 1 || c->tour > 64) return bad("tour must be in [1, 64]");
+  if (c->pc_thresh > (1ULL << 32) || c->pm_thresh > (1ULL << 32))
+    return bad("thresholds must be <= 2^32");
+  if (c->kmeans_k < 1 || c->kmeans_k > c->K) return bad("kmeans_k must be in [1, K]");
+  if (c->kmeans_max_iter < 1) return bad("kmeans_max_iter must be >= 1");
+  if (c->n_seeded < 0 || c->n_seeded > c->N) return bad("n_seeded must be in [0, N]");
+  if (c->flags != 0) return bad("flags must be 0");
+  for (int i = 0; i < 4; ++i)
+    if (c->reserved[i] != 0) return bad("reserved fields must be 0");
+  return PA_OK;
+}
+
+static void free_ctx(pa_ctx* c) {
+  if (!c) return;
+  cudaFree(c->beta64);
+  cudaFree(c->bnc64);
+  cudaFree(c->t32.tab);
+  cudaFree(c->t32.own);
+  cudaFree(c->t32.bn);
+  cudaFree(c->user_xy);
+  cudaFree(c->bs_xy);
+  cudaFree(c->labels);
+  cudaFree(c->centroids);
+  cudaFree(c->pop[0]);
+  cudaFree(c->pop[1]);
+  cudaFree(c->fit);
+  cudaFree(c->scratch_i64);
+  cudaFree(c->best_row);
+  cudaFree(c->stage_pop);
+  cudaFree(c->stage_fit);
+  delete c;
+}
+
+pa_status pa_create(const pa_config* cfg, const double* beta, const int32_t* user_xy_mm,
+                    const int32_t* bs_xy_mm, void* stream, pa_ctx** out) {
+  if (!out) return PA_EINVAL;
+  *out = nullptr;
+  if (!cfg || !beta) return PA_EINVAL;
+  if ((user_xy_mm == nullptr) != (bs_xy_mm == nullptr)) return PA_EINVAL;
+  std::string why;
+  if (validate_config(cfg, &why) != PA_OK) return PA_EINVAL;
+  double bmax = 0.0;
+  if (!pa::instance_ok(*cfg, beta, user_xy_mm, bs_xy_mm, &bmax)) return PA_EINVAL;
+  const int L = cfg->L, K = cfg->K;
+  if (cfg->prec == PA_FP32 && !pa::f32_supported(L, K, nullptr)) return PA_EUNSUPPORTED;
+
+  pa_ctx* c = new (std::nothrow) pa_ctx();
+  if (!c) return PA_ENOMEM;
+  c->cfg = *cfg;
+  c->stream = static_cast<cudaStream_t>(stream);
+  c->nc = cfg->sigma2 / cfg->rho;
+  c->pc = cfg->sigma2 / ((double)cfg->tau_p * cfg->rho);
+  pa_status st = PA_OK;
+  auto chk = [&](cudaError_t e, const char* what) {
+    if (st == PA_OK) st = cuda_check(c, e, what);
+    return st == PA_OK;
+  };
+  const int64_t n_beta = (int64_t)L * L * K, LK = (int64_t)L * K;
+  const size_t fsz = cfg->prec == PA_FP64 ? 8 : 4;
+  do {
+    if (!chk(cudaGetDevice(&c->device), "cudaGetDevice")) break;
+    if (!chk(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device),
+             "cudaDeviceGetAttribute"))
+      break;
+    if (!chk(cudaMalloc(&c->beta64, sizeof(double) * n_beta), "cudaMalloc beta")) break;
+    if (!chk(cudaMalloc(&c->bnc64, sizeof(double) * L), "cudaMalloc bnc")) break;
+    if (cfg->prec == PA_FP32) {
+      int NJ, RS, vec;
+      pa::f32_geometry(L, K, &NJ, &RS, &vec);
+      c->t32.NJ = NJ;
+      c->t32.RS = RS;
+      c->t32.vec = vec;
+      const int64_t tab_floats = ((LK * RS + 3) / 4) * 4;
+      if (!chk(cudaMalloc(&c->t32.tab, sizeof(float) * tab_floats), "cudaMalloc tab")) break;
+      if (!chk(cudaMalloc(&c->t32.own, sizeof(float) * LK), "cudaMalloc own")) break;
+      if (!chk(cudaMalloc(&c->t32.bn, sizeof(float) * L), "cudaMalloc bn")) break;
+    }
+    if (!chk(cudaMalloc(&c->user_xy, sizeof(int32_t) * 2 * LK), "cudaMalloc user_xy")) break;
+    if (!chk(cudaMalloc(&c->bs_xy, sizeof(int32_t) * 2 * L), "cudaMalloc bs_xy")) break;
+    if (!chk(cudaMalloc(&c->labels, sizeof(int32_t) * LK), "cudaMalloc labels")) break;
+    if (!chk(cudaMalloc(&c->centroids, sizeof(double) * 2 * cfg->kmeans_k), "cudaMalloc cent"))
+      break;
+    if (!chk(cudaMalloc(&c->pop[0], (size_t)cfg->N * LK), "cudaMalloc pop0")) break;
+    if (!chk(cudaMalloc(&c->pop[1], (size_t)cfg->N * LK), "cudaMalloc pop1")) break;
+    if (!chk(cudaMalloc(&c->fit, fsz * cfg->N), "cudaMalloc fit")) break;
+    if (!chk(cudaMalloc(&c->scratch_i64, sizeof(int64_t) * 8), "cudaMalloc scratch")) break;
+    if (!chk(cudaMalloc(&c->best_row, (size_t)LK), "cudaMalloc best")) break;
+    st = upload_instance(c, beta, user_xy_mm, bs_xy_mm, bmax);
+    if (st != PA_OK) break;
+    if (!chk(cudaStreamSynchronize(c->stream), "prepare sync")) break;
+  } while (0);
+  if (st != PA_OK) {
+    free_ctx(c);
+    return st;
+  }
+  *out = c;
+  return PA_OK;
+}
+
+pa_status pa_load_instance(pa_ctx* ctx, const double* beta, const int32_t* user_xy_mm,
+                           const int32_t* bs_xy_mm) {
+  if (!ctx) return PA_EINVAL;
+  if (!beta) return fail(ctx, PA_EINVAL, "null beta");
+  if ((user_xy_mm == nullptr) != (bs_xy_mm == nullptr))
+    return fail(ctx, PA_EINVAL, "user and BS positions must both be given or both be NULL");
+  double bmax = 0.0;
+  if (!pa::instance_ok(ctx->cfg, beta, user_xy_mm, bs_xy_mm, &bmax))
+    return fail(ctx, PA_EINVAL, "beta must be finite and > 0; positions within int32");
+  pa_status st = upload_instance(ctx, beta, user_xy_mm, bs_xy_mm, bmax);
+  if (st != PA_OK) return st;
+  ctx->cur = 0;
+  ctx->generation = 0;
+  return PA_OK;
+}
+
+void pa_destroy(pa_ctx* ctx) {
+  if (!ctx) return;
+  cudaStreamSynchronize(ctx->stream);
+  free_ctx(ctx);
+}
+
+pa_status pa_set_stream(pa_ctx* ctx, void* stream) {
+  if (!ctx) return PA_EINVAL;
+  ctx->stream = static_cast<cudaStream_t>(stream);
+  return PA_OK;
+}
+
+static cudaError_t eval_any(pa_ctx* ctx, const uint8_t* pop, int64_t n, void* fit) {
+  if (ctx->cfg.prec == PA_FP64)
+    return pa::launch_eval_f64(ctx, pop, n, static_cast<double*>(fit), ctx->stream);
+  return pa::launch_eval_f32(ctx, pop, n, static_cast<float*>(fit), ctx->stream);
+}
+
+pa_status pa_eval_population(pa_ctx* ctx, const uint8_t* pop_dev, int64_t n, void* fit_dev) {
+  if (!ctx) return PA_EINVAL;
+  if (n < 0) return fail(ctx, PA_EINVAL, "n must be >= 0");
+  if (n == 0) return PA_OK;
+  if (!pop_dev || !fit_dev) return fail(ctx, PA_EINVAL, "null buffer");
+  PA_TRY(ctx, eval_any(ctx, pop_dev, n, fit_dev), "eval kernel");
+  return PA_OK;
+}
+
+static pa_status ensure_stage(pa_ctx* ctx, int64_t n) {
+  if (n <= ctx->stage_cap) return PA_OK;
+  cudaFree(ctx->stage_pop);
+  cudaFree(ctx->stage_fit);
+  ctx->stage_pop = nullptr;
+  ctx->stage_fit = nullptr;
+  ctx->stage_cap = 0;
+  const int64_t LK = (int64_t)ctx->cfg.L * ctx->cfg.K;
+  const size_t fsz = ctx->cfg.prec == PA_FP64 ? 8 : 4;
+  PA_TRY(ctx, cudaMalloc(&ctx->stage_pop, (size_t)(n * LK)), "cudaMalloc staging");
+  PA_TRY(ctx, cudaMalloc(&ctx->stage_fit, fsz * (size_t)n), "cudaMalloc staging");
+  ctx->stage_cap = n;
+  return PA_OK;
+}
+
+pa_status pa_eval_population_host(pa_ctx* ctx, const uint8_t* pop_host, int64_t n,
+                                  void* fit_host) {
+  if (!ctx) return PA_EINVAL;
+  if (n < 0) return fail(ctx, PA_EINVAL, "n must be >= 0");
+  if (n == 0) return PA_OK;
+  if (!pop_host || !fit_host) return fail(ctx, PA_EINVAL, "null buffer");
+  pa_status st = ensure_stage(ctx, n);
+  if (st != PA_OK) return st;
+  const int64_t LK = (int64_t)ctx->cfg.L * ctx->cfg.K;
+  const size_t fsz = ctx->cfg.prec == PA_FP64 ? 8 : 4;
+  PA_TRY(ctx, cudaMemcpyAsync(ctx->stage_pop, pop_host, (size_t)(n * LK), cudaMemcpyHostToDevice,
+                              ctx->stream),
+         "copy population");
+  PA_TRY(ctx, eval_any(ctx, ctx->stage_pop, n, ctx->stage_fit), "eval kernel");
+  PA_TRY(ctx, cudaMemcpyAsync(fit_host, ctx->stage_fit, fsz * (size_t)n, cudaMemcpyDeviceToHost,
+                              ctx->stream),
+         "copy fitness");
+  PA_TRY(ctx, cudaStreamSynchronize(ctx->stream), "sync");
+  return PA_OK;
+}
+
+pa_status pa_ga_step(pa_ctx* ctx, const uint8_t* pop_dev, const void* fit_dev, int32_t generation,
+                     uint8_t* next_dev) {
+  if (!ctx) return PA_EINVAL;
+  if (!pop_dev || !fit_dev || !next_dev) return fail(ctx, PA_EINVAL, "null buffer");
+  if (generation < 0) return fail(ctx, PA_EINVAL, "generation must be >= 0");
+  const size_t bytes = (size_t)ctx->cfg.N * ctx->cfg.L * ctx->cfg.K;
+  const uint8_t* a0 = pop_dev;
+  const uint8_t* b0 = next_dev;
+  if (a0 < b0 + bytes && b0 < a0 + bytes) return fail(ctx, PA_EINVAL, "buffers overlap");
+  PA_TRY(ctx, pa::launch_ga_step(ctx, pop_dev, fit_dev, generation, next_dev, ctx->stream),
+         "ga kernel");
+  return PA_OK;
+}
+
+pa_status pa_kmeans_seed(pa_ctx* ctx, int32_t* labels_host, double* centroids_host) {
+  if (!ctx) return PA_EINVAL;
+  if ((labels_host || centroids_host) && !ctx->has_positions)
+    return fail(ctx, PA_EINVAL, "no positions: K-means outputs unavailable");
+  ctx->cur = 0;
+  ctx->generation = 0;
+  PA_TRY(ctx, pa::launch_seed(ctx, ctx->pop[0], ctx->stream), "seed kernel");
+  const int64_t LK = (int64_t)ctx->cfg.L * ctx->cfg.K;
+  if (labels_host)
+    PA_TRY(ctx, cudaMemcpyAsync(labels_host, ctx->labels, sizeof(int32_t) * LK,
+                                cudaMemcpyDeviceToHost, ctx->stream),
+           "copy labels");
+  if (centroids_host)
+    PA_TRY(ctx, cudaMemcpyAsync(centroids_host, ctx->centroids,
+                                sizeof(double) * 2 * ctx->cfg.kmeans_k, cudaMemcpyDeviceToHost,
+                                ctx->stream),
+           "copy centroids");
+  if (labels_host || centroids_host) PA_TRY(ctx, cudaStreamSynchronize(ctx->stream), "sync");
+  return PA_OK;
+}
+
+static pa_status run_generations(pa_ctx* ctx, int32_t generations) {
+  for (int32_t g = 0; g < generations; ++g) {
+    uint8_t* cur = ctx->pop[ctx->cur];
+    uint8_t* nxt = ctx->pop[ctx->cur ^ 1];
+    PA_TRY(ctx, eval_any(ctx, cur, ctx->cfg.N, ctx->fit), "eval kernel");
+    PA_TRY(ctx, pa::launch_ga_step(ctx, cur, ctx->fit, ctx->generation, nxt, ctx->stream),
+           "ga kernel");
+    ctx->cur ^= 1;
+    ctx->generation += 1;
+  }
+  return PA_OK;
+}
+
+pa_status pa_step(pa_ctx* ctx, int32_t generations) {
+  if (!ctx) return PA_EINVAL;
+  if (generations < 0) return fail(ctx, PA_EINVAL, "generations must be >= 0");
+  return run_generations(ctx, generations);
+}
+
+pa_status pa_solve(pa_ctx* ctx, int32_t generations, uint8_t* best_host, double* best_fit) {
+  if (!ctx) return PA_EINVAL;
+  if (generations < 0) return fail(ctx, PA_EINVAL, "generations must be >= 0");
+  pa_status st = pa_kmeans_seed(ctx, nullptr, nullptr);
+  if (st != PA_OK) return st;
+  st = run_generations(ctx, generations);
+  if (st != PA_OK) return st;
+  uint8_t* cur = ctx->pop[ctx->cur];
+  PA_TRY(ctx, eval_any(ctx, cur, ctx->cfg.N, ctx->fit), "eval kernel");
+  double* best_dev = reinterpret_cast<double*>(ctx->scratch_i64);
+  PA_TRY(ctx, pa::launch_argbest(ctx, ctx->fit, cur, ctx->best_row, best_dev, ctx->stream),
+         "argbest kernel");
+  const int64_t LK = (int64_t)ctx->cfg.L * ctx->cfg.K;
+  if (best_host)
+    PA_TRY(ctx, cudaMemcpyAsync(best_host, ctx->best_row, (size_t)LK, cudaMemcpyDeviceToHost,
+                                ctx->stream),
+           "copy best");
+  if (best_fit)
+    PA_TRY(ctx, cudaMemcpyAsync(best_fit, best_dev, sizeof(double), cudaMemcpyDeviceToHost,
+                                ctx->stream),
+           "copy best fit");
+  PA_TRY(ctx, cudaStreamSynchronize(ctx->stream), "sync");
+  return PA_OK;
+}
+
+pa_status pa_get_population(pa_ctx* ctx, uint8_t* pop_host, void* fit_host, int32_t* generation) {
+  if (!ctx) return PA_EINVAL;
+  const size_t bytes = (size_t)ctx->cfg.N * ctx->cfg.L * ctx->cfg.K;
+  uint8_t* cur = ctx->pop[ctx->cur];
+  if (pop_host)
+    PA_TRY(ctx, cudaMemcpyAsync(pop_host, cur, bytes, cudaMemcpyDeviceToHost, ctx->stream),
+           "copy population");
+  if (fit_host) {
+    PA_TRY(ctx, eval_any(ctx, cur, ctx->cfg.N, ctx->fit), "eval kernel");
+    const size_t fsz = ctx->cfg.prec == PA_FP64 ? 8 : 4;
+    PA_TRY(ctx, cudaMemcpyAsync(fit_host, ctx->fit, fsz * ctx->cfg.N, cudaMemcpyDeviceToHost,
+                                ctx->stream),
+           "copy fitness");
+  }
+  if (generation) *generation = ctx->generation;
+  PA_TRY(ctx, cudaStreamSynchronize(ctx->stream), "sync");
+  return PA_OK;
+}
+
+pa_status pa_validate_population(pa_ctx* ctx, const uint8_t* pop_dev, int64_t n,
+                                 int64_t* first_bad) {
+  if (!ctx || !first_bad) return PA_EINVAL;
+  if (n < 0) return fail(ctx, PA_EINVAL, "n must be >= 0");
+  *first_bad = -1;
+  if (n == 0) return PA_OK;
+  if (!pop_dev) return fail(ctx, PA_EINVAL, "null buffer");
+  int64_t* flag = ctx->scratch_i64 + 1;
+  PA_TRY(ctx, cudaMemsetAsync(flag, 0xFF, sizeof(int64_t), ctx->stream), "memset");
+  PA_TRY(ctx, pa::launch_validate(ctx, pop_dev, n, flag, ctx->stream), "validate kernel");
+  uint64_t h = 0;
+  PA_TRY(ctx, cudaMemcpyAsync(&h, flag, sizeof h, cudaMemcpyDeviceToHost, ctx->stream), "copy");
+  PA_TRY(ctx, cudaStreamSynchronize(ctx->stream), "sync");
+  *first_bad = (h == ~0ULL) ? -1 : (int64_t)h;
+  return PA_OK;
+}
+
+pa_status pa_set_population(pa_ctx* ctx, const uint8_t* pop_host, int32_t generation) {
+  if (!ctx || !pop_host) return PA_EINVAL;
+  if (generation < 0) return fail(ctx, PA_EINVAL, "generation must be >= 0");
+  const size_t bytes = (size_t)ctx->cfg.N * ctx->cfg.L * ctx->cfg.K;
+  uint8_t* dst = ctx->pop[ctx->cur ^ 1];
+  PA_TRY(ctx, cudaMemcpyAsync(dst, pop_host, bytes, cudaMemcpyHostToDevice, ctx->stream),
+         "copy population");
+  int64_t bad = -1;
+  pa_status st = pa_validate_population(ctx, dst, ctx->cfg.N, &bad);
+  if (st != PA_OK) return st;
+  if (bad >= 0) return fail(ctx, PA_EINVAL, "population row is not a permutation");
+  ctx->cur ^= 1;
+  ctx->generation = generation;
+  return PA_OK;
+}
+
+pa_status pa_population_device(pa_ctx* ctx, uint8_t** pop_dev, void** fit_dev) {
+  if (!ctx) return PA_EINVAL;
+  if (pop_dev) *pop_dev = ctx->pop[ctx->cur];
+  if (fit_dev) *fit_dev = ctx->fit;
+  return PA_OK;
+}
+
+}  // extern "C"

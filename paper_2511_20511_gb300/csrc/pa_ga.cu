@@ -1,0 +1,446 @@
+// pa_ga.cu -- GA generation step, K-means population seeding, best-member
+// selection and permutation validation (paper Alg. 1, Sec. 1 items 1-2).
+//
+// Every random decision comes from a Philox4x64-10 draw stream keyed by the
+// seed and addressed by (slot, generation, tag), so a child's draws do not
+// depend on which thread makes them and the generation is bit-reproducible.
+//
+// GA generation (one thread per child slot n):
+//   slots 0..E-1  the E best members by (fitness desc, index asc), unchanged
+//                 (elitism);
+//   slot n >= E   parent a = tournament over draws [0, t), parent b over
+//                 [t, 2t) (indices uniform with replacement, best fitness
+//                 wins, ties to the lower index); with draw 2t < pc_thresh a
+//                 cut c = 1 + below(draw 2t+1, L-1), rows < c from a and
+//                 rows >= c from b (row-wise one-cut crossover keeps every
+//                 row a permutation), else a copy of a; then for each row l,
+//                 with draw 2t+2+3l < pm_thresh, swap two distinct positions
+//                 chosen by draws 2t+3+3l and 2t+4+3l.
+// Seeding (single block):
+//   Lloyd's K-means on the users' positions relative to their own BS
+//   (integer mm; exact int64 centroid sums, one FP64 division; nearest
+//   centroid with ties to the lower index; an empty cluster keeps its
+//   centroid); initial centroids are k distinct users by a partial
+//   Fisher-Yates shuffle.  The assignment A*: in each cell, users in order of
+//   (distance to own centroid, index) take pilot = label when free, the rest
+//   take the free pilots in ascending order.  Member 0 = A*, members
+//   1..n_seeded-1 = A* with each row swapped with probability 1/2, the rest
+//   uniformly random rows (Fisher-Yates).
+#include <algorithm>
+
+#include "pa_internal.cuh"
+
+namespace pa {
+namespace {
+
+template <typename FT>
+__device__ __forceinline__ bool better(const FT* fit, int a, int b) {
+  const FT fa = fit[a], fb = fit[b];
+  if (fa > fb) return true;
+  if (fa < fb) return false;
+  return a < b;
+}
+
+// Block-wide best index by (fitness desc, index asc) among members not in
+// excluded[0..nex).  Result broadcast through *out.  All threads call it.
+template <typename FT>
+__device__ int block_best(const FT* fit, int N, const int* excluded, int nex, int* red_idx) {
+  int best = -1;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    bool skip = false;
+    for (int e = 0; e < nex; ++e) skip |= (excluded[e] == i);
+    if (skip) continue;
+    if (best < 0 || better(fit, i, best)) best = i;
+  }
+  // warp reduction
+  for (int off = 16; off > 0; off >>= 1) {
+    const int o = __shfl_down_sync(0xffffffffu, best, off);
+    if (o >= 0 && (best < 0 || better(fit, o, best))) best = o;
+  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __syncthreads();
+  if (lane == 0) red_idx[warp] = best;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int b = -1;
+    const int nw = (blockDim.x + 31) >> 5;
+    for (int w = 0; w < nw; ++w) {
+      const int o = red_idx[w];
+      if (o >= 0 && (b < 0 || better(fit, o, b))) b = o;
+    }
+    red_idx[32] = b;
+  }
+  __syncthreads();
+  const int r = red_idx[32];
+  __syncthreads();
+  return r;
+}
+
+__device__ __forceinline__ void swap_two(uint8_t* row, int K, uint32_t ui, uint32_t uj) {
+  if (K < 2) return;
+  const int i = (int)below(ui, (uint32_t)K);
+  const int jj = (int)below(uj, (uint32_t)(K - 1));
+  const int j = jj + (jj >= i ? 1 : 0);
+  const uint8_t t = row[i];
+  row[i] = row[j];
+  row[j] = t;
+}
+
+struct GaArgs {
+  const uint8_t* pop;
+  const void* fit;
+  uint8_t* next;
+  int N, L, K, E, tour;
+  uint64_t pc_thresh, pm_thresh, seed;
+  int gen;
+};
+
+template <typename FT>
+__device__ int tournament(const FT* fit, int N, int tour, DrawStream& ds, uint32_t first) {
+  int best = (int)below(ds.draw(first), (uint32_t)N);
+  for (int t = 1; t < tour; ++t) {
+    const int c = (int)below(ds.draw(first + t), (uint32_t)N);
+    if (better(fit, c, best)) best = c;
+  }
+  return best;
+}
+
+template <typename FT>
+__global__ void __launch_bounds__(256) k_ga_step(const GaArgs a) {
+  __shared__ int elites[64];
+  __shared__ int red[33];
+  const FT* fit = static_cast<const FT*>(a.fit);
+  const int64_t LK = (int64_t)a.L * a.K;
+  const int E = a.E;
+  // every block determines the elites (E is small) before writing children
+  for (int e = 0; e < E; ++e) {
+    const int b = block_best(fit, a.N, elites, e, red);
+    if (threadIdx.x == 0) elites[e] = b;
+    __syncthreads();
+  }
+  for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < a.N; n += gridDim.x * blockDim.x) {
+    uint8_t* child = a.next + n * LK;
+    if (n < E) {
+      const uint8_t* src = a.pop + (int64_t)elites[n] * LK;
+      for (int64_t i = 0; i < LK; ++i) child[i] = src[i];
+      continue;
+    }
+    DrawStream ds(a.seed, (uint64_t)n, (uint64_t)a.gen, kTagGa);
+    const int T = a.tour;
+    const int pa_ = tournament(fit, a.N, T, ds, 0);
+    const int pb_ = tournament(fit, a.N, T, ds, (uint32_t)T);
+    const uint32_t u_cross = ds.draw((uint32_t)(2 * T));
+    const uint32_t u_cut = ds.draw((uint32_t)(2 * T + 1));
+    int cut = a.L;
+    if ((uint64_t)u_cross < a.pc_thresh) cut = 1 + (int)below(u_cut, (uint32_t)(a.L - 1));
+    const uint8_t* A = a.pop + (int64_t)pa_ * LK;
+    const uint8_t* B = a.pop + (int64_t)pb_ * LK;
+    const int64_t split = (int64_t)cut * a.K;
+    for (int64_t i = 0; i < LK; ++i) child[i] = i < split ? A[i] : B[i];
+    for (int l = 0; l < a.L; ++l) {
+      const uint32_t base = (uint32_t)(2 * T + 2 + 3 * l);
+      const uint32_t u_mut = ds.draw(base);
+      const uint32_t ui = ds.draw(base + 1);
+      const uint32_t uj = ds.draw(base + 2);
+      if ((uint64_t)u_mut < a.pm_thresh) swap_two(child + (int64_t)l * a.K, a.K, ui, uj);
+    }
+  }
+}
+
+// ------------------------------------------------------------------ seeding
+struct SeedArgs {
+  const int32_t* user_xy;  // [U][2] or null
+  const int32_t* bs_xy;    // [L][2] or null
+  int L, K, kk, max_iter;
+  int N, n_seeded;
+  uint64_t seed;
+  uint8_t* pop;
+  int32_t* labels;      // [U] out (may be null when feat is null)
+  double* centroids;    // [kk][2] out
+};
+
+__device__ __forceinline__ double dist2(int32_t fx, int32_t fy, double cx, double cy) {
+  const double dx = __dsub_rn((double)fx, cx);
+  const double dy = __dsub_rn((double)fy, cy);
+  return __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
+}
+
+__device__ void random_row(uint8_t* row, int K, DrawStream& ds, uint32_t first) {
+  for (int k = 0; k < K; ++k) row[k] = (uint8_t)k;
+  for (int t = 0; t < K - 1; ++t) {
+    const int i = K - 1 - t;
+    const int j = (int)below(ds.draw(first + t), (uint32_t)(i + 1));
+    const uint8_t tmp = row[i];
+    row[i] = row[j];
+    row[j] = tmp;
+  }
+}
+
+constexpr int kSeedThreads = 1024;
+constexpr int kMaxU = 64 * 64;  // users handled by the single-block K-means
+
+__global__ void __launch_bounds__(kSeedThreads) k_seed(const SeedArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int L = a.L, K = a.K, U = L * K, kk = a.kk;
+  const int64_t LK = U;
+  double* cx = reinterpret_cast<double*>(smem);
+  double* cy = cx + kk;
+  unsigned long long* sx = reinterpret_cast<unsigned long long*>(cy + kk);
+  unsigned long long* sy = sx + kk;
+  int* cnt = reinterpret_cast<int*>(sy + kk);
+  int* label = cnt + kk;         // [U]
+  int* idx = label + U;          // [U] scratch for the initial shuffle
+  int32_t* feat = idx + U;       // [U][2] position relative to the own BS
+  uint8_t* astar = reinterpret_cast<uint8_t*>(feat + 2 * U);  // [U]
+  __shared__ int changed;
+  const bool kmeans = a.user_xy != nullptr && a.n_seeded > 0;
+
+  if (kmeans) {
+    for (int u = threadIdx.x; u < U; u += blockDim.x) {
+      idx[u] = u;
+      label[u] = -1;
+      const int l = u / K;
+      feat[2 * u] = a.user_xy[2 * u] - a.bs_xy[2 * l];
+      feat[2 * u + 1] = a.user_xy[2 * u + 1] - a.bs_xy[2 * l + 1];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      DrawStream ds(a.seed, 0, 0, kTagKmeans);
+      for (int i = 0; i < kk; ++i) {
+        const int j = i + (int)below(ds.draw((uint32_t)i), (uint32_t)(U - i));
+        const int t = idx[i];
+        idx[i] = idx[j];
+        idx[j] = t;
+        cx[i] = (double)feat[2 * idx[i]];
+        cy[i] = (double)feat[2 * idx[i] + 1];
+      }
+    }
+    __syncthreads();
+    for (int it = 0; it < a.max_iter; ++it) {
+      if (threadIdx.x == 0) changed = 0;
+      __syncthreads();
+      for (int u = threadIdx.x; u < U; u += blockDim.x) {
+        const int32_t fx = feat[2 * u], fy = feat[2 * u + 1];
+        int best = 0;
+        double bd = dist2(fx, fy, cx[0], cy[0]);
+        for (int c = 1; c < kk; ++c) {
+          const double d = dist2(fx, fy, cx[c], cy[c]);
+          if (d < bd) {
+            bd = d;
+            best = c;
+          }
+        }
+        if (label[u] != best) changed = 1;
+        label[u] = best;
+      }
+      __syncthreads();
+      if (changed == 0 || it == a.max_iter - 1) break;
+      for (int c = threadIdx.x; c < kk; c += blockDim.x) {
+        sx[c] = 0;
+        sy[c] = 0;
+        cnt[c] = 0;
+      }
+      __syncthreads();
+      for (int u = threadIdx.x; u < U; u += blockDim.x) {
+        const int c = label[u];
+        atomicAdd(&sx[c], (unsigned long long)(long long)feat[2 * u]);
+        atomicAdd(&sy[c], (unsigned long long)(long long)feat[2 * u + 1]);
+        atomicAdd(&cnt[c], 1);
+      }
+      __syncthreads();
+      for (int c = threadIdx.x; c < kk; c += blockDim.x) {
+        if (cnt[c] > 0) {
+          cx[c] = __ddiv_rn((double)(long long)sx[c], (double)cnt[c]);
+          cy[c] = __ddiv_rn((double)(long long)sy[c], (double)cnt[c]);
+        }
+      }
+      __syncthreads();
+    }
+    // A*: one thread per cell
+    for (int l = threadIdx.x; l < L; l += blockDim.x) {
+      int order[kMaxK];
+      double dist[kMaxK];
+      bool used[kMaxK];
+      int deferred[kMaxK];
+      for (int k = 0; k < K; ++k) {
+        const int u = l * K + k;
+        const int c = label[u];
+        dist[k] = dist2(feat[2 * u], feat[2 * u + 1], cx[c], cy[c]);
+        order[k] = k;
+        used[k] = false;
+      }
+      for (int i = 1; i < K; ++i) {
+        const int v = order[i];
+        int j = i - 1;
+        while (j >= 0 && (dist[order[j]] > dist[v] || (dist[order[j]] == dist[v] && order[j] > v))) {
+          order[j + 1] = order[j];
+          --j;
+        }
+        order[j + 1] = v;
+      }
+      int nd = 0;
+      for (int i = 0; i < K; ++i) {
+        const int k = order[i];
+        const int p = label[l * K + k];
+        if (!used[p]) {
+          used[p] = true;
+          astar[l * K + k] = (uint8_t)p;
+        } else {
+          deferred[nd++] = k;
+        }
+      }
+      int nf = 0;
+      for (int i = 0; i < nd; ++i) {
+        while (used[nf]) ++nf;
+        used[nf] = true;
+        astar[l * K + deferred[i]] = (uint8_t)nf;
+      }
+    }
+    __syncthreads();
+    for (int u = threadIdx.x; u < U; u += blockDim.x)
+      if (a.labels) a.labels[u] = label[u];
+    for (int c = threadIdx.x; c < kk; c += blockDim.x) {
+      a.centroids[2 * c] = cx[c];
+      a.centroids[2 * c + 1] = cy[c];
+    }
+  }
+  const int ns = kmeans ? a.n_seeded : 0;
+  for (int n = threadIdx.x; n < a.N; n += blockDim.x) {
+    uint8_t* X = a.pop + (int64_t)n * LK;
+    DrawStream ds(a.seed, (uint64_t)n, 0, kTagSeed);
+    if (n < ns) {
+      for (int i = 0; i < U; ++i) X[i] = astar[i];
+      if (n > 0) {
+        for (int l = 0; l < L; ++l) {
+          const uint32_t u_do = ds.draw((uint32_t)(3 * l));
+          const uint32_t ui = ds.draw((uint32_t)(3 * l + 1));
+          const uint32_t uj = ds.draw((uint32_t)(3 * l + 2));
+          if (u_do < 0x80000000u) swap_two(X + l * K, K, ui, uj);
+        }
+      }
+    } else {
+      for (int l = 0; l < L; ++l) random_row(X + l * K, K, ds, (uint32_t)(l * (K > 1 ? K - 1 : 0)));
+    }
+  }
+}
+
+// ------------------------------------------------------------------ best member
+template <typename FT>
+__global__ void __launch_bounds__(1024) k_argbest(const FT* fit, int N, const uint8_t* pop,
+                                                  int64_t LK, uint8_t* best_row,
+                                                  double* best_fit) {
+  __shared__ int red[33];
+  const int b = block_best(fit, N, nullptr, 0, red);
+  for (int64_t i = threadIdx.x; i < LK; i += blockDim.x) best_row[i] = pop[b * LK + i];
+  if (threadIdx.x == 0) *best_fit = (double)fit[b];
+}
+
+// ------------------------------------------------------------------ validation
+__global__ void k_validate(const uint8_t* pop, int64_t rows, int K, unsigned long long* first_bad,
+                           int L) {
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < rows;
+       r += (int64_t)gridDim.x * blockDim.x) {
+    const uint8_t* row = pop + r * K;
+    unsigned long long seen = 0;
+    bool ok = true;
+    for (int k = 0; k < K; ++k) {
+      const int p = row[k];
+      if (p >= K) {
+        ok = false;
+        break;
+      }
+      const unsigned long long bit = 1ULL << p;
+      if (seen & bit) {
+        ok = false;
+        break;
+      }
+      seen |= bit;
+    }
+    if (!ok) atomicMin(first_bad, (unsigned long long)(r / L));
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_ga_step(const pa_ctx* ctx, const uint8_t* pop, const void* fit, int32_t gen,
+                           uint8_t* next, cudaStream_t st) {
+  const pa_config& c = ctx->cfg;
+  GaArgs a;
+  a.pop = pop;
+  a.fit = fit;
+  a.next = next;
+  a.N = c.N;
+  a.L = c.L;
+  a.K = c.K;
+  a.E = c.E;
+  a.tour = c.tour;
+  a.pc_thresh = c.pc_thresh;
+  a.pm_thresh = c.pm_thresh;
+  a.seed = c.seed;
+  a.gen = gen;
+  const int threads = 256;
+  const int blocks = std::max(1, std::min((c.N + threads - 1) / threads, ctx->num_sms));
+  if (c.prec == PA_FP64)
+    k_ga_step<double><<<blocks, threads, 0, st>>>(a);
+  else
+    k_ga_step<float><<<blocks, threads, 0, st>>>(a);
+  count_launch();
+  return cudaGetLastError();
+}
+
+size_t seed_smem(int L, int K, int kk) {
+  const int U = L * K;
+  return (size_t)kk * (8 + 8 + 8 + 8 + 4) + (size_t)U * 4 * 4 + (size_t)U + 16;
+}
+
+cudaError_t launch_seed(pa_ctx* ctx, uint8_t* pop, cudaStream_t st) {
+  const pa_config& c = ctx->cfg;
+  SeedArgs a;
+  a.user_xy = ctx->has_positions ? ctx->user_xy : nullptr;
+  a.bs_xy = ctx->has_positions ? ctx->bs_xy : nullptr;
+  a.L = c.L;
+  a.K = c.K;
+  a.kk = c.kmeans_k;
+  a.max_iter = c.kmeans_max_iter;
+  a.N = c.N;
+  a.n_seeded = c.n_seeded;
+  a.seed = c.seed;
+  a.pop = pop;
+  a.labels = ctx->labels;
+  a.centroids = ctx->centroids;
+  const size_t smem = seed_smem(c.L, c.K, c.kmeans_k);
+  cudaError_t e =
+      cudaFuncSetAttribute(k_seed, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_seed<<<1, kSeedThreads, smem, st>>>(a);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_argbest(const pa_ctx* ctx, const void* fit, const uint8_t* pop,
+                           uint8_t* best_row, double* best_fit_dev, cudaStream_t st) {
+  const pa_config& c = ctx->cfg;
+  const int64_t LK = (int64_t)c.L * c.K;
+  if (c.prec == PA_FP64)
+    k_argbest<double><<<1, 1024, 0, st>>>(static_cast<const double*>(fit), c.N, pop, LK, best_row,
+                                          best_fit_dev);
+  else
+    k_argbest<float><<<1, 1024, 0, st>>>(static_cast<const float*>(fit), c.N, pop, LK, best_row,
+                                         best_fit_dev);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_validate(const pa_ctx* ctx, const uint8_t* pop, int64_t n, int64_t* first_bad,
+                            cudaStream_t st) {
+  const int64_t rows = n * ctx->cfg.L;
+  const int64_t blocks = std::min<int64_t>((rows + 255) / 256, (int64_t)ctx->num_sms * 16);
+  if (blocks <= 0) return cudaSuccess;
+  k_validate<<<(unsigned)blocks, 256, 0, st>>>(pop, rows, ctx->cfg.K,
+                                               reinterpret_cast<unsigned long long*>(first_bad),
+                                               ctx->cfg.L);
+  count_launch();
+  return cudaGetLastError();
+}
+
+}  // namespace pa

@@ -1,0 +1,157 @@
+// pa_internal.cuh -- internal declarations shared by the CUDA sources of
+// libpa.so (context layout, kernel launchers, device helpers).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/pa.h"
+
+namespace pa {
+
+// ----------------------------------------------------------------- limits
+constexpr int kMaxK = 64;            // pilots per cell (uint8 rows, smem rows)
+constexpr int kMaxL = 255;           // cells
+constexpr int kMaxNJ = 48;           // widest per-thread BS vector of the FP32 kernel
+constexpr int kSmemBudget = 227 * 1024;
+
+// Stream tags of the counter-based generator (counter word 3).
+enum : uint32_t { kTagSeed = 1, kTagKmeans = 2, kTagGa = 3 };
+
+// Prepared FP32 tables of one instance (device pointers, owned by ctx).
+struct F32Tables {
+  float* tab = nullptr;  // [L*K rows][RS]: row l*K+u, col j: beta[j][l][u]*2^s, 0 if j==l
+  float* own = nullptr;  // [L*K]: beta[l][l][u]*2^s
+  float* bn = nullptr;   // [L]: (B_j + sigma2/rho) * 2^s
+  int RS = 0;            // row stride (floats)
+  int NJ = 0;            // BS entries read per row (even, >= L)
+  int vec = 1;           // 2: float2 loads (K <= 16), 1: scalar loads
+  float M = 0.f;         // antennas
+  float pc = 0.f;        // sigma2/(tau_p rho) * 2^s
+  int scale_exp = 0;     // s
+  double scale = 1.0;    // 2^s
+};
+
+}  // namespace pa
+
+struct pa_ctx {
+  pa_config cfg{};
+  int device = 0;
+  int num_sms = 0;
+  cudaStream_t stream = nullptr;
+  double nc = 0.0;  // sigma2 / rho
+  double pc = 0.0;  // sigma2 / (tau_p rho)
+  // instance data (device)
+  double* beta64 = nullptr;   // [L][L][K] as given
+  double* bnc64 = nullptr;    // [L]: B_j + nc (FP64, oracle order)
+  pa::F32Tables t32;
+  int32_t* user_xy = nullptr; // [L*K][2] user positions (mm), or null
+  int32_t* bs_xy = nullptr;   // [L][2] BS positions (mm), or null
+  int32_t* labels = nullptr;  // [L*K]
+  double* centroids = nullptr;  // [kmeans_k][2]
+  int has_positions = 0;
+  // resident population (device)
+  uint8_t* pop[2] = {nullptr, nullptr};
+  int cur = 0;
+  void* fit = nullptr;         // [N] float or double
+  int32_t generation = 0;
+  // scratch
+  int64_t* scratch_i64 = nullptr;  // small device scratch (flags, argbest)
+  uint8_t* best_row = nullptr;     // [L*K]
+  // host staging for *_host calls
+  uint8_t* stage_pop = nullptr;
+  void* stage_fit = nullptr;
+  int64_t stage_cap = 0;
+  std::string err;
+};
+
+namespace pa {
+
+pa_status fail(pa_ctx* ctx, pa_status st, const std::string& msg);
+// process-wide count of kernels this library has launched
+void count_launch();
+pa_status cuda_check(pa_ctx* ctx, cudaError_t e, const char* what);
+
+// ----------------------------------------------------------------- launchers
+// pa_prep.cu
+cudaError_t launch_prep(pa_ctx* ctx);
+// host-side checks of one instance: beta finite and > 0 (returns the largest
+// value through bmax), relative positions within int32
+bool instance_ok(const pa_config& c, const double* beta, const int32_t* user_xy_mm,
+                 const int32_t* bs_xy_mm, double* bmax);
+// pa_fitness.cu
+cudaError_t launch_eval_f32(const pa_ctx* ctx, const uint8_t* pop, int64_t n, float* fit,
+                            cudaStream_t st);
+cudaError_t launch_eval_f64(const pa_ctx* ctx, const uint8_t* pop, int64_t n, double* fit,
+                            cudaStream_t st);
+bool f32_supported(int L, int K, size_t* smem_bytes);
+// pa_ga.cu
+cudaError_t launch_ga_step(const pa_ctx* ctx, const uint8_t* pop, const void* fit, int32_t gen,
+                           uint8_t* next, cudaStream_t st);
+cudaError_t launch_seed(pa_ctx* ctx, uint8_t* pop, cudaStream_t st);
+cudaError_t launch_argbest(const pa_ctx* ctx, const void* fit, const uint8_t* pop,
+                           uint8_t* best_row, double* best_fit_dev, cudaStream_t st);
+cudaError_t launch_validate(const pa_ctx* ctx, const uint8_t* pop, int64_t n, int64_t* first_bad,
+                            cudaStream_t st);
+
+// ----------------------------------------------------------------- device helpers
+// Philox4x64-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of the 4x64
+// S-box, Weyl key schedule.
+struct Philox4x64 {
+  uint64_t v[4];
+};
+
+__device__ __forceinline__ Philox4x64 philox4x64_10(uint64_t c0, uint64_t c1, uint64_t c2,
+                                                    uint64_t c3, uint64_t k0, uint64_t k1) {
+  const uint64_t M0 = 0xD2E7470EE14C6C93ULL, M1 = 0xCA5A826395121157ULL;
+  const uint64_t W0 = 0x9E3779B97F4A7C15ULL, W1 = 0xBB67AE8584CAA73BULL;
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r > 0) {
+      k0 += W0;
+      k1 += W1;
+    }
+    const uint64_t hi0 = __umul64hi(M0, c0), lo0 = M0 * c0;
+    const uint64_t hi1 = __umul64hi(M1, c2), lo1 = M1 * c2;
+    const uint64_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+    c0 = n0;
+    c1 = lo1;
+    c2 = n2;
+    c3 = lo0;
+  }
+  Philox4x64 o;
+  o.v[0] = c0;
+  o.v[1] = c1;
+  o.v[2] = c2;
+  o.v[3] = c3;
+  return o;
+}
+
+// Draw stream for one (seed, slot, generation, tag): 32-bit draw d is half
+// (d & 1) of 64-bit word (d >> 1) & 3 of block d >> 3.  Caches one block.
+struct DrawStream {
+  uint64_t seed, slot, gen, tag;
+  uint64_t cached_block;
+  Philox4x64 blk;
+  __device__ DrawStream(uint64_t seed_, uint64_t slot_, uint64_t gen_, uint64_t tag_)
+      : seed(seed_), slot(slot_), gen(gen_), tag(tag_), cached_block(~0ULL) {}
+  __device__ __forceinline__ uint32_t draw(uint32_t d) {
+    const uint64_t b = d >> 3;
+    if (b != cached_block) {
+      blk = philox4x64_10(b, slot, gen, tag, seed, 0);
+      cached_block = b;
+    }
+    const uint32_t i = (d >> 1) & 3u;
+    const uint64_t w = i == 0 ? blk.v[0] : i == 1 ? blk.v[1] : i == 2 ? blk.v[2] : blk.v[3];
+    return (d & 1u) ? (uint32_t)(w >> 32) : (uint32_t)(w & 0xFFFFFFFFu);
+  }
+};
+
+// Uniform integer in [0, n) from a 32-bit draw (multiply-shift).
+__device__ __forceinline__ uint32_t below(uint32_t u, uint32_t n) {
+  return (uint32_t)(((uint64_t)u * (uint64_t)n) >> 32);
+}
+
+}  // namespace pa
