@@ -237,6 +237,9 @@ def run_ours(args):
     def solve_step():
         ctx.solve(G_GEN)
 
+    if args.only == "eval":
+        return run_eval_only(args, B, inputs, ctx, stream, dev, rank)
+
     # ---- device-resident solves (value)
     for _ in range(args.warmup):
         solve_step()
@@ -341,6 +344,23 @@ def run_ours(args):
     return 0
 
 
+def run_eval_only(args, B, inputs, ctx, stream, dev, rank):
+    """Only the population evaluation of 2^20 chromosomes (for profilers)."""
+    import torch
+
+    nb = 1 << BATCH_LOG2
+    pop = inputs.random_population_torch(nb, L, K, seed=1000 + rank, device=dev)
+    fit = torch.empty(nb, dtype=torch.float32, device=dev)
+    torch.cuda.synchronize()
+    for _ in range(args.warmup + args.steps):
+        B.pa_eval_population(ctx.handle, pop, fit)
+    stream.synchronize()
+    print(json.dumps({"only": "eval", "launches": args.warmup + args.steps,
+                      "checksum": float(fit.double().sum().item())}))
+    ctx.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -349,6 +369,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--only", choices=["all", "eval"], default="all",
+                    help="eval: time only the 2^20-chromosome evaluation (profiling runs)")
     args = ap.parse_args()
     if args.warmup < 3:
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)

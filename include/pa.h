@@ -207,7 +207,8 @@ pa_status pa_validate_population(pa_ctx* ctx, const uint8_t* pop_dev, int64_t n,
 /* Static description of a status code. */
 const char* pa_status_str(pa_status s);
 
-/* Last error message of a context ("" if none). */
+/* Last error message of a context ("" if none).  With ctx == NULL: the
+ * reason for the calling thread's last failed pa_create. */
 const char* pa_last_error(const pa_ctx* ctx);
 
 /* Number of CUDA kernels this library has launched in this process (all

@@ -87,10 +87,9 @@ def exported_symbols():
 def _check(st, ctx=None):
     if st != PA_OK:
         msg = lib().pa_status_str(st).decode()
-        if ctx is not None:
-            detail = lib().pa_last_error(ctx).decode()
-            if detail:
-                msg = f"{msg}: {detail}"
+        detail = lib().pa_last_error(ctx).decode()  # ctx None: this thread's last create error
+        if detail:
+            msg = f"{msg}: {detail}"
         raise PaError(st, msg)
 
 
@@ -116,6 +115,8 @@ def pa_config_default(L, K, **overrides):
         if not hasattr(cfg, k):
             raise AttributeError(k)
         setattr(cfg, k, v)
+    if "N" in overrides and "n_seeded" not in overrides:
+        cfg.n_seeded = (cfg.N + 1) // 2
     return cfg
 
 
@@ -136,7 +137,7 @@ def pa_create(cfg, beta, user_xy_mm=None, bs_xy_mm=None, stream=None):
     out = C.c_void_p()
     st = lib().pa_create(C.byref(cfg), _host_ptr(beta), _host_ptr(u), _host_ptr(b),
                          _stream_handle(stream), C.byref(out))
-    _check(st)
+    _check(st, None)
     return out
 
 

@@ -14,6 +14,7 @@
 namespace pa {
 
 static std::atomic<uint64_t> g_launches{0};
+static thread_local std::string t_create_error;  // last pa_create failure of this thread
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 void f32_geometry(int L, int K, int* NJ, int* RS, int* vec);
@@ -112,7 +113,9 @@ const char* pa_status_str(pa_status s) {
   return "unknown status";
 }
 
-const char* pa_last_error(const pa_ctx* ctx) { return ctx ? ctx->err.c_str() : ""; }
+const char* pa_last_error(const pa_ctx* ctx) {
+  return ctx ? ctx->err.c_str() : pa::t_create_error.c_str();
+}
 
 uint64_t pa_kernel_launches(void) { return pa::g_launches.load(std::memory_order_relaxed); }
 
@@ -198,16 +201,24 @@ static void free_ctx(pa_ctx* c) {
 
 pa_status pa_create(const pa_config* cfg, const double* beta, const int32_t* user_xy_mm,
                     const int32_t* bs_xy_mm, void* stream, pa_ctx** out) {
-  if (!out) return PA_EINVAL;
+  std::string& why = pa::t_create_error;
+  why.clear();
+  auto reject = [&](pa_status s, const char* m) {
+    why = m;
+    return s;
+  };
+  if (!out) return reject(PA_EINVAL, "out is NULL");
   *out = nullptr;
-  if (!cfg || !beta) return PA_EINVAL;
-  if ((user_xy_mm == nullptr) != (bs_xy_mm == nullptr)) return PA_EINVAL;
-  std::string why;
+  if (!cfg || !beta) return reject(PA_EINVAL, "cfg and beta are required");
+  if ((user_xy_mm == nullptr) != (bs_xy_mm == nullptr))
+    return reject(PA_EINVAL, "user and BS positions must both be given or both be NULL");
   if (validate_config(cfg, &why) != PA_OK) return PA_EINVAL;
   double bmax = 0.0;
-  if (!pa::instance_ok(*cfg, beta, user_xy_mm, bs_xy_mm, &bmax)) return PA_EINVAL;
+  if (!pa::instance_ok(*cfg, beta, user_xy_mm, bs_xy_mm, &bmax))
+    return reject(PA_EINVAL, "beta must be finite and > 0; relative positions within int32");
   const int L = cfg->L, K = cfg->K;
-  if (cfg->prec == PA_FP32 && !pa::f32_supported(L, K, nullptr)) return PA_EUNSUPPORTED;
+  if (cfg->prec == PA_FP32 && !pa::f32_supported(L, K, nullptr))
+    return reject(PA_EUNSUPPORTED, "FP32 gain table of this (L, K) exceeds shared memory");
 
   pa_ctx* c = new (std::nothrow) pa_ctx();
   if (!c) return PA_ENOMEM;
@@ -255,6 +266,7 @@ pa_status pa_create(const pa_config* cfg, const double* beta, const int32_t* use
     if (!chk(cudaStreamSynchronize(c->stream), "prepare sync")) break;
   } while (0);
   if (st != PA_OK) {
+    why = c->err;
     free_ctx(c);
     return st;
   }

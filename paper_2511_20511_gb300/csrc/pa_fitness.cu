@@ -27,6 +27,7 @@
 // products (no FMA), log2 by the atanh series, per-cell partial sums added in
 // ascending j.
 #include <algorithm>
+#include <mutex>
 
 #include "pa_internal.cuh"
 
@@ -288,14 +289,45 @@ F32Launch f32_shape(int L, int K, int RS) {
   return s;
 }
 
+// Resident blocks per SM of a kernel at a launch shape.  The attribute and
+// occupancy queries cost host time, so results are cached per (kernel,
+// device, threads, shared memory).
+struct OccKey {
+  const void* fn;
+  int dev, threads;
+  size_t smem;
+};
+static int cached_occupancy(const void* fn, int threads, size_t smem, cudaError_t* err) {
+  static OccKey keys[64];
+  static int vals[64];
+  static int used = 0;
+  static std::mutex mu;
+  std::lock_guard<std::mutex> lock(mu);
+  int dev = 0;
+  *err = cudaGetDevice(&dev);
+  if (*err != cudaSuccess) return 0;
+  for (int i = 0; i < used; ++i)
+    if (keys[i].fn == fn && keys[i].dev == dev && keys[i].threads == threads &&
+        keys[i].smem == smem)
+      return vals[i];
+  *err = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (*err != cudaSuccess) return 0;
+  int per_sm = 0;
+  *err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, smem);
+  if (*err != cudaSuccess) return 0;
+  if (used < 64) {
+    keys[used] = OccKey{fn, dev, threads, smem};
+    vals[used] = per_sm;
+    ++used;
+  }
+  return per_sm;
+}
+
 template <int NJ, int VEC, bool FIN>
 cudaError_t run_f32(const F32Args& a, const F32Launch& s, int num_sms, cudaStream_t st) {
   auto kern = k_eval_f32<NJ, VEC, FIN>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)s.smem);
-  if (e != cudaSuccess) return e;
-  int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, s.threads, s.smem);
+  cudaError_t e = cudaSuccess;
+  const int per_sm = cached_occupancy((const void*)kern, s.threads, s.smem, &e);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   const int64_t tiles = (a.n + a.NT - 1) / a.NT;
@@ -387,10 +419,10 @@ cudaError_t launch_eval_f64(const pa_ctx* ctx, const uint8_t* pop, int64_t n, do
   a.pc = ctx->pc;
   const int LK = a.L * a.K;
   const size_t smem = (size_t)LK * 8 + 2 * (size_t)LK;
-  cudaError_t e = cudaFuncSetAttribute(k_eval_f64, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
-  if (e != cudaSuccess) return e;
   const int threads = LK >= 256 ? 256 : ((LK + 31) / 32) * 32;
+  cudaError_t e = cudaSuccess;
+  cached_occupancy((const void*)k_eval_f64, threads, smem, &e);
+  if (e != cudaSuccess) return e;
   const int64_t grid = std::min<int64_t>(n, (int64_t)ctx->num_sms * 8);
   k_eval_f64<<<(unsigned)grid, threads, smem, st>>>(a);
   count_launch();
