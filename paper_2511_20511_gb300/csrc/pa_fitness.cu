@@ -289,8 +289,10 @@ F32Launch f32_shape(int L, int K, int RS) {
   return s;
 }
 
-// Resident blocks per SM of a kernel at a launch shape.  The attribute and
-// occupancy queries cost host time, so results are cached per (kernel,
+// Resident blocks per SM of a kernel at a launch shape.  The first query of
+// a kernel on a device raises its dynamic shared-memory cap to the device's
+// opt-in maximum (a cap sized to one launch would reject a later, larger
+// one); the queries cost host time, so results are cached per (kernel,
 // device, threads, shared memory).
 struct OccKey {
   const void* fn;
@@ -298,9 +300,12 @@ struct OccKey {
   size_t smem;
 };
 static int cached_occupancy(const void* fn, int threads, size_t smem, cudaError_t* err) {
-  static OccKey keys[64];
-  static int vals[64];
+  static OccKey keys[256];
+  static int vals[256];
   static int used = 0;
+  static const void* capped_fn[64];
+  static int capped_dev[64];
+  static int ncapped = 0;
   static std::mutex mu;
   std::lock_guard<std::mutex> lock(mu);
   int dev = 0;
@@ -310,12 +315,24 @@ static int cached_occupancy(const void* fn, int threads, size_t smem, cudaError_
     if (keys[i].fn == fn && keys[i].dev == dev && keys[i].threads == threads &&
         keys[i].smem == smem)
       return vals[i];
-  *err = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (*err != cudaSuccess) return 0;
+  bool capped = false;
+  for (int i = 0; i < ncapped; ++i) capped |= (capped_fn[i] == fn && capped_dev[i] == dev);
+  if (!capped) {
+    int optin = 0;
+    *err = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (*err != cudaSuccess) return 0;
+    *err = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+    if (*err != cudaSuccess) return 0;
+    if (ncapped < 64) {
+      capped_fn[ncapped] = fn;
+      capped_dev[ncapped] = dev;
+      ++ncapped;
+    }
+  }
   int per_sm = 0;
   *err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, smem);
   if (*err != cudaSuccess) return 0;
-  if (used < 64) {
+  if (used < 256) {
     keys[used] = OccKey{fn, dev, threads, smem};
     vals[used] = per_sm;
     ++used;

@@ -95,16 +95,27 @@ struct GaArgs {
   int gen;
 };
 
+// Tournament of size T over draws [first, first + T): lane t < T draws one
+// candidate; the winner is the best by (fitness desc, index asc), which does
+// not depend on the order the candidates are compared in.
 template <typename FT>
-__device__ int tournament(const FT* fit, int N, int tour, DrawStream& ds, uint32_t first) {
-  int best = (int)below(ds.draw(first), (uint32_t)N);
-  for (int t = 1; t < tour; ++t) {
-    const int c = (int)below(ds.draw(first + t), (uint32_t)N);
-    if (better(fit, c, best)) best = c;
+__device__ __forceinline__ int warp_tournament(const FT* fit, int N, int T, DrawStream& ds,
+                                               uint32_t first, int lane) {
+  int best = -1;
+  for (int t = lane; t < T; t += 32) {
+    const int c = (int)below(ds.draw(first + (uint32_t)t), (uint32_t)N);
+    if (best < 0 || better(fit, c, best)) best = c;
+  }
+  for (int off = 16; off > 0; off >>= 1) {
+    const int o = __shfl_xor_sync(0xffffffffu, best, off);
+    if (o >= 0 && (best < 0 || better(fit, o, best))) best = o;
   }
   return best;
 }
 
+// One warp per child slot.  Lanes draw the tournament candidates in
+// parallel, copy the parents' rows with coalesced byte streams, then apply
+// the per-row swap mutation with one lane per row.
 template <typename FT>
 __global__ void __launch_bounds__(256) k_ga_step(const GaArgs a) {
   __shared__ int elites[64];
@@ -112,38 +123,41 @@ __global__ void __launch_bounds__(256) k_ga_step(const GaArgs a) {
   const FT* fit = static_cast<const FT*>(a.fit);
   const int64_t LK = (int64_t)a.L * a.K;
   const int E = a.E;
-  // every block determines the elites (E is small) before writing children
   for (int e = 0; e < E; ++e) {
     const int b = block_best(fit, a.N, elites, e, red);
     if (threadIdx.x == 0) elites[e] = b;
     __syncthreads();
   }
-  for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < a.N; n += gridDim.x * blockDim.x) {
-    uint8_t* child = a.next + n * LK;
+  const int lane = threadIdx.x & 31;
+  const int warps = blockDim.x >> 5;
+  const int T = a.tour;
+  for (int n = blockIdx.x * warps + (threadIdx.x >> 5); n < a.N; n += gridDim.x * warps) {
+    uint8_t* __restrict__ child = a.next + n * LK;
     if (n < E) {
-      const uint8_t* src = a.pop + (int64_t)elites[n] * LK;
-      for (int64_t i = 0; i < LK; ++i) child[i] = src[i];
+      const uint8_t* __restrict__ src = a.pop + (int64_t)elites[n] * LK;
+      for (int64_t i = lane; i < LK; i += 32) child[i] = src[i];
       continue;
     }
     DrawStream ds(a.seed, (uint64_t)n, (uint64_t)a.gen, kTagGa);
-    const int T = a.tour;
-    const int pa_ = tournament(fit, a.N, T, ds, 0);
-    const int pb_ = tournament(fit, a.N, T, ds, (uint32_t)T);
+    const int pa_ = warp_tournament(fit, a.N, T, ds, 0, lane);
+    const int pb_ = warp_tournament(fit, a.N, T, ds, (uint32_t)T, lane);
     const uint32_t u_cross = ds.draw((uint32_t)(2 * T));
     const uint32_t u_cut = ds.draw((uint32_t)(2 * T + 1));
     int cut = a.L;
     if ((uint64_t)u_cross < a.pc_thresh) cut = 1 + (int)below(u_cut, (uint32_t)(a.L - 1));
-    const uint8_t* A = a.pop + (int64_t)pa_ * LK;
-    const uint8_t* B = a.pop + (int64_t)pb_ * LK;
+    const uint8_t* __restrict__ A = a.pop + (int64_t)pa_ * LK;
+    const uint8_t* __restrict__ B = a.pop + (int64_t)pb_ * LK;
     const int64_t split = (int64_t)cut * a.K;
-    for (int64_t i = 0; i < LK; ++i) child[i] = i < split ? A[i] : B[i];
-    for (int l = 0; l < a.L; ++l) {
+    for (int64_t i = lane; i < LK; i += 32) child[i] = i < split ? A[i] : B[i];
+    __syncwarp();
+    for (int l = lane; l < a.L; l += 32) {
       const uint32_t base = (uint32_t)(2 * T + 2 + 3 * l);
       const uint32_t u_mut = ds.draw(base);
       const uint32_t ui = ds.draw(base + 1);
       const uint32_t uj = ds.draw(base + 2);
       if ((uint64_t)u_mut < a.pm_thresh) swap_two(child + (int64_t)l * a.K, a.K, ui, uj);
     }
+    __syncwarp();
   }
 }
 
@@ -304,23 +318,28 @@ __global__ void __launch_bounds__(kSeedThreads) k_seed(const SeedArgs a) {
       a.centroids[2 * c + 1] = cy[c];
     }
   }
+  // Members: one thread per (member n, cell l) row, built in a per-thread
+  // shared-memory row and written out as K contiguous bytes.
+  __syncthreads();
   const int ns = kmeans ? a.n_seeded : 0;
-  for (int n = threadIdx.x; n < a.N; n += blockDim.x) {
-    uint8_t* X = a.pop + (int64_t)n * LK;
+  uint8_t* row = astar + ((U + 15) & ~15) + threadIdx.x * K;
+  const int64_t rows = (int64_t)a.N * L;
+  for (int64_t r = threadIdx.x; r < rows; r += blockDim.x) {
+    const int n = (int)(r / L), l = (int)(r - (int64_t)n * L);
     DrawStream ds(a.seed, (uint64_t)n, 0, kTagSeed);
     if (n < ns) {
-      for (int i = 0; i < U; ++i) X[i] = astar[i];
+      for (int k = 0; k < K; ++k) row[k] = astar[l * K + k];
       if (n > 0) {
-        for (int l = 0; l < L; ++l) {
-          const uint32_t u_do = ds.draw((uint32_t)(3 * l));
-          const uint32_t ui = ds.draw((uint32_t)(3 * l + 1));
-          const uint32_t uj = ds.draw((uint32_t)(3 * l + 2));
-          if (u_do < 0x80000000u) swap_two(X + l * K, K, ui, uj);
-        }
+        const uint32_t u_do = ds.draw((uint32_t)(3 * l));
+        const uint32_t ui = ds.draw((uint32_t)(3 * l + 1));
+        const uint32_t uj = ds.draw((uint32_t)(3 * l + 2));
+        if (u_do < 0x80000000u) swap_two(row, K, ui, uj);
       }
     } else {
-      for (int l = 0; l < L; ++l) random_row(X + l * K, K, ds, (uint32_t)(l * (K > 1 ? K - 1 : 0)));
+      random_row(row, K, ds, (uint32_t)(l * (K > 1 ? K - 1 : 0)));
     }
+    uint8_t* dst = a.pop + r * K;
+    for (int k = 0; k < K; ++k) dst[k] = row[k];
   }
 }
 
@@ -378,8 +397,8 @@ cudaError_t launch_ga_step(const pa_ctx* ctx, const uint8_t* pop, const void* fi
   a.pm_thresh = c.pm_thresh;
   a.seed = c.seed;
   a.gen = gen;
-  const int threads = 256;
-  const int blocks = std::max(1, std::min((c.N + threads - 1) / threads, ctx->num_sms));
+  const int threads = 256;  // 8 children (one per warp) per block
+  const int blocks = std::max(1, std::min((c.N + 7) / 8, ctx->num_sms * 4));
   if (c.prec == PA_FP64)
     k_ga_step<double><<<blocks, threads, 0, st>>>(a);
   else
@@ -390,7 +409,8 @@ cudaError_t launch_ga_step(const pa_ctx* ctx, const uint8_t* pop, const void* fi
 
 size_t seed_smem(int L, int K, int kk) {
   const int U = L * K;
-  return (size_t)kk * (8 + 8 + 8 + 8 + 4) + (size_t)U * 4 * 4 + (size_t)U + 16;
+  return (size_t)kk * (8 + 8 + 8 + 8 + 4) + (size_t)U * 4 * 4 + (size_t)((U + 15) & ~15) +
+         (size_t)kSeedThreads * K + 16;
 }
 
 cudaError_t launch_seed(pa_ctx* ctx, uint8_t* pop, cudaStream_t st) {
@@ -409,9 +429,16 @@ cudaError_t launch_seed(pa_ctx* ctx, uint8_t* pop, cudaStream_t st) {
   a.labels = ctx->labels;
   a.centroids = ctx->centroids;
   const size_t smem = seed_smem(c.L, c.K, c.kmeans_k);
-  cudaError_t e =
-      cudaFuncSetAttribute(k_seed, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
+  static int capped_dev = -1;  // the seed kernel's cap is raised once per device
+  if (capped_dev != ctx->device) {
+    int optin = 0;
+    cudaError_t e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin,
+                                           ctx->device);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_seed, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+    if (e != cudaSuccess) return e;
+    capped_dev = ctx->device;
+  }
   k_seed<<<1, kSeedThreads, smem, st>>>(a);
   count_launch();
   return cudaGetLastError();

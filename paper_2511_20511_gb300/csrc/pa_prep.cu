@@ -12,16 +12,25 @@
 namespace pa {
 namespace {
 
-__global__ void k_prep_sums(const double* __restrict__ beta, int L, int K, double nc,
-                            double scale, double* __restrict__ bnc, float* __restrict__ bn) {
-  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < L; j += gridDim.x * blockDim.x) {
-    double b = 0.0;
-    const double* row = beta + (size_t)j * L * K;
-    for (int l = 0; l < L; ++l)
-      for (int k = 0; k < K; ++k) b = __dadd_rn(b, row[l * K + k]);
-    const double v = __dadd_rn(b, nc);
-    bnc[j] = v;
-    if (bn) bn[j] = __double2float_rn(__dmul_rn(v, scale));
+// One block per BS j: the row beta[j][.][.] is staged in shared memory with
+// coalesced loads, then one thread adds it up in the fixed (l, k) order.
+__global__ void __launch_bounds__(256) k_prep_sums(const double* __restrict__ beta, int L, int K,
+                                                   double nc, double scale,
+                                                   double* __restrict__ bnc,
+                                                   float* __restrict__ bn) {
+  extern __shared__ double row[];
+  const int LK = L * K;
+  for (int j = blockIdx.x; j < L; j += gridDim.x) {
+    __syncthreads();
+    for (int i = threadIdx.x; i < LK; i += blockDim.x) row[i] = beta[(size_t)j * LK + i];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double b = 0.0;
+      for (int i = 0; i < LK; ++i) b = __dadd_rn(b, row[i]);
+      const double v = __dadd_rn(b, nc);
+      bnc[j] = v;
+      if (bn) bn[j] = __double2float_rn(__dmul_rn(v, scale));
+    }
   }
 }
 
@@ -47,8 +56,8 @@ __global__ void k_prep_table(const double* __restrict__ beta, int L, int K, int 
 cudaError_t launch_prep(pa_ctx* ctx) {
   const int L = ctx->cfg.L, K = ctx->cfg.K;
   const bool f32 = ctx->cfg.prec == PA_FP32;
-  k_prep_sums<<<(L + 127) / 128, 128, 0, ctx->stream>>>(ctx->beta64, L, K, ctx->nc, ctx->t32.scale,
-                                                        ctx->bnc64, f32 ? ctx->t32.bn : nullptr);
+  k_prep_sums<<<L, 256, sizeof(double) * L * K, ctx->stream>>>(
+      ctx->beta64, L, K, ctx->nc, ctx->t32.scale, ctx->bnc64, f32 ? ctx->t32.bn : nullptr);
   count_launch();
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || !f32) return e;
