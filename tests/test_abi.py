@@ -88,7 +88,11 @@ def test_create_rejects_bad_beta_and_positions(B):
     assert _create_status(B, fm, beta) == B.PA_EINVAL
 
 
-def test_status_strings(B):
+def test_status_strings_and_create_reason(B):
     for s in range(7):
         assert B.lib().pa_status_str(s)
-    assert B.lib().pa_last_error(None) == b""
+    cfg = B.pa_config_default(7, 4, E=300)
+    assert _create_status(B, cfg, np.ones((7, 7, 4))) == B.PA_EINVAL
+    assert b"E must be" in B.lib().pa_last_error(None)
+    with pytest.raises(B.PaError, match="E must be"):
+        B.pa_create(cfg, np.ones((7, 7, 4)))
