@@ -318,10 +318,7 @@ static int cached_occupancy(const void* fn, int threads, size_t smem, cudaError_
   bool capped = false;
   for (int i = 0; i < ncapped; ++i) capped |= (capped_fn[i] == fn && capped_dev[i] == dev);
   if (!capped) {
-    int optin = 0;
-    *err = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    if (*err != cudaSuccess) return 0;
-    *err = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+    *err = raise_smem_cap(fn, dev);
     if (*err != cudaSuccess) return 0;
     if (ncapped < 64) {
       capped_fn[ncapped] = fn;
@@ -349,6 +346,7 @@ cudaError_t run_f32(const F32Args& a, const F32Launch& s, int num_sms, cudaStrea
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   const int64_t tiles = (a.n + a.NT - 1) / a.NT;
   const int64_t grid = std::min<int64_t>(tiles, (int64_t)per_sm * num_sms);
+  (void)cudaGetLastError();  // drop a stale error of an earlier call
   kern<<<(unsigned)grid, s.threads, s.smem, st>>>(a);
   count_launch();
   return cudaGetLastError();
@@ -441,6 +439,7 @@ cudaError_t launch_eval_f64(const pa_ctx* ctx, const uint8_t* pop, int64_t n, do
   cached_occupancy((const void*)k_eval_f64, threads, smem, &e);
   if (e != cudaSuccess) return e;
   const int64_t grid = std::min<int64_t>(n, (int64_t)ctx->num_sms * 8);
+  (void)cudaGetLastError();  // drop a stale error of an earlier call
   k_eval_f64<<<(unsigned)grid, threads, smem, st>>>(a);
   count_launch();
   return cudaGetLastError();

@@ -27,6 +27,7 @@
 //   1..n_seeded-1 = A* with each row swapped with probability 1/2, the rest
 //   uniformly random rows (Fisher-Yates).
 #include <algorithm>
+#include <atomic>
 
 #include "pa_internal.cuh"
 
@@ -399,6 +400,7 @@ cudaError_t launch_ga_step(const pa_ctx* ctx, const uint8_t* pop, const void* fi
   a.gen = gen;
   const int threads = 256;  // 8 children (one per warp) per block
   const int blocks = std::max(1, std::min((c.N + 7) / 8, ctx->num_sms * 4));
+  (void)cudaGetLastError();  // drop a stale error of an earlier call
   if (c.prec == PA_FP64)
     k_ga_step<double><<<blocks, threads, 0, st>>>(a);
   else
@@ -429,16 +431,14 @@ cudaError_t launch_seed(pa_ctx* ctx, uint8_t* pop, cudaStream_t st) {
   a.labels = ctx->labels;
   a.centroids = ctx->centroids;
   const size_t smem = seed_smem(c.L, c.K, c.kmeans_k);
-  static int capped_dev = -1;  // the seed kernel's cap is raised once per device
-  if (capped_dev != ctx->device) {
-    int optin = 0;
-    cudaError_t e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin,
-                                           ctx->device);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_seed, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+  static std::atomic<uint64_t> capped{0};  // devices whose cap is raised (bit per device)
+  const uint64_t bit = 1ULL << (ctx->device & 63);
+  if (!(capped.load() & bit)) {
+    cudaError_t e = raise_smem_cap((const void*)k_seed, ctx->device);
     if (e != cudaSuccess) return e;
-    capped_dev = ctx->device;
+    capped.fetch_or(bit);
   }
+  (void)cudaGetLastError();  // drop a stale error of an earlier call
   k_seed<<<1, kSeedThreads, smem, st>>>(a);
   count_launch();
   return cudaGetLastError();
@@ -448,6 +448,7 @@ cudaError_t launch_argbest(const pa_ctx* ctx, const void* fit, const uint8_t* po
                            uint8_t* best_row, double* best_fit_dev, cudaStream_t st) {
   const pa_config& c = ctx->cfg;
   const int64_t LK = (int64_t)c.L * c.K;
+  (void)cudaGetLastError();  // drop a stale error of an earlier call
   if (c.prec == PA_FP64)
     k_argbest<double><<<1, 1024, 0, st>>>(static_cast<const double*>(fit), c.N, pop, LK, best_row,
                                           best_fit_dev);
@@ -463,6 +464,7 @@ cudaError_t launch_validate(const pa_ctx* ctx, const uint8_t* pop, int64_t n, in
   const int64_t rows = n * ctx->cfg.L;
   const int64_t blocks = std::min<int64_t>((rows + 255) / 256, (int64_t)ctx->num_sms * 16);
   if (blocks <= 0) return cudaSuccess;
+  (void)cudaGetLastError();  // drop a stale error of an earlier call
   k_validate<<<(unsigned)blocks, 256, 0, st>>>(pop, rows, ctx->cfg.K,
                                                reinterpret_cast<unsigned long long*>(first_bad),
                                                ctx->cfg.L);

@@ -96,6 +96,19 @@ cudaError_t launch_argbest(const pa_ctx* ctx, const void* fit, const uint8_t* po
 cudaError_t launch_validate(const pa_ctx* ctx, const uint8_t* pop, int64_t n, int64_t* first_bad,
                             cudaStream_t st);
 
+// Raise a kernel's dynamic shared-memory cap to what the device allows
+// beside the kernel's static shared memory (call once per kernel and device).
+inline cudaError_t raise_smem_cap(const void* fn, int dev) {
+  int optin = 0;
+  cudaError_t e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e != cudaSuccess) return e;
+  cudaFuncAttributes fa;
+  e = cudaFuncGetAttributes(&fa, fn);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              optin - (int)fa.sharedSizeBytes);
+}
+
 // ----------------------------------------------------------------- device helpers
 // Philox4x64-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of the 4x64
 // S-box, Weyl key schedule.

@@ -56,6 +56,7 @@ __global__ void k_prep_table(const double* __restrict__ beta, int L, int K, int 
 cudaError_t launch_prep(pa_ctx* ctx) {
   const int L = ctx->cfg.L, K = ctx->cfg.K;
   const bool f32 = ctx->cfg.prec == PA_FP32;
+  (void)cudaGetLastError();  // drop a stale error of an earlier call
   k_prep_sums<<<L, 256, sizeof(double) * L * K, ctx->stream>>>(
       ctx->beta64, L, K, ctx->nc, ctx->t32.scale, ctx->bnc64, f32 ? ctx->t32.bn : nullptr);
   count_launch();
@@ -65,6 +66,7 @@ cudaError_t launch_prep(pa_ctx* ctx) {
   // table storage is padded to a multiple of 4 floats; pad rows are zero
   const int64_t total = ((rows * ctx->t32.RS + 3) / 4) * 4;
   const int64_t blocks = (total + 255) / 256;
+  (void)cudaGetLastError();  // drop a stale error of an earlier call
   k_prep_table<<<(unsigned)(blocks < 4096 ? blocks : 4096), 256, 0, ctx->stream>>>(
       ctx->beta64, L, K, ctx->t32.RS, ctx->t32.scale, total, ctx->t32.tab, ctx->t32.own);
   count_launch();
