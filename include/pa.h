@@ -204,6 +204,40 @@ pa_status pa_population_device(pa_ctx* ctx, uint8_t** pop_dev, void** fit_dev);
 pa_status pa_validate_population(pa_ctx* ctx, const uint8_t* pop_dev, int64_t n,
                                  int64_t* first_bad);
 
+/*
+ * Size of the device array behind pa_eval_population_noalloc (bytes).
+ */
+#define PA_NOALLOC_SCRATCH_BYTES (256u * 1024u)
+
+/*
+ * Fitness evaluation that allocates nothing.  The paper has no counterpart:
+ * this entry point exists for callers that cannot allocate device memory --
+ * a real-time scheduling loop that must not take cudaMalloc's implicit
+ * synchronisation, a framework that hands out all device memory from its own
+ * pool, or code running while a stream is captured.  It computes exactly what
+ * pa_create + pa_eval_population + pa_destroy compute for the same cfg and
+ * beta, without a context: the instance copy and the prepared tables go to a
+ * file-scope device array of PA_NOALLOC_SCRATCH_BYTES bytes that every GPU
+ * holds from library load to process exit.
+ *   cfg      configuration (as for pa_create; only the instance and SINR
+ *            fields matter; prec selects the fitness type)
+ *   beta     host, L*L*K float64 gains (as for pa_create)
+ *   pop_dev  device, n*L*K bytes;  fit_dev  device, n float32 / float64
+ *   stream   cudaStream_t or NULL
+ * Instances needing more scratch than the array holds (gains + prepared
+ * tables) return PA_EUNSUPPORTED; pa_last_error(NULL) says how much was
+ * needed.  Invalid arguments return PA_EINVAL.  The first call on a device
+ * looks up the array's device address (cudaGetSymbolAddress) for that device;
+ * make that first call before any stream capture.  All calls share the array
+ * and leave their data in it; each call rewrites what it reads, but calls
+ * whose GPU work overlaps (unordered streams, concurrent host threads on one
+ * device) race and give undefined results.  Synchronises the stream before
+ * returning (the host beta is copied asynchronously).
+ */
+pa_status pa_eval_population_noalloc(const pa_config* cfg, const double* beta,
+                                     const uint8_t* pop_dev, int64_t n, void* fit_dev,
+                                     void* stream);
+
 /* Static description of a status code. */
 const char* pa_status_str(pa_status s);
 

@@ -61,6 +61,8 @@ _SIGS = {
     "pa_status_str": (C.c_char_p, [C.c_int]),
     "pa_last_error": (C.c_char_p, [C.c_void_p]),
     "pa_kernel_launches": (C.c_uint64, []),
+    "pa_eval_population_noalloc": (C.c_int, [C.POINTER(pa_config), C.c_void_p, C.c_void_p,
+                                             C.c_int64, C.c_void_p, C.c_void_p]),
 }
 
 
@@ -155,6 +157,16 @@ def pa_load_instance(ctx, beta, user_xy_mm=None, bs_xy_mm=None):
     b = None if bs_xy_mm is None else np.ascontiguousarray(bs_xy_mm, dtype=np.int32)
     _check(lib().pa_load_instance(ctx, _host_ptr(beta), _host_ptr(u), _host_ptr(b)), ctx)
     return beta, u, b  # keep the arrays alive until the stream has consumed them
+
+
+def pa_eval_population_noalloc(cfg, beta, pop, fit, stream=None):
+    """Evaluation without any device allocation (see include/pa.h)."""
+    beta = np.ascontiguousarray(beta, dtype=np.float64)
+    if beta.shape != (cfg.L, cfg.L, cfg.K):
+        raise ValueError(f"beta must be (L, L, K) = {(cfg.L, cfg.L, cfg.K)}, got {beta.shape}")
+    _check(lib().pa_eval_population_noalloc(C.byref(cfg), _host_ptr(beta), _dev_ptr(pop),
+                                            int(pop.shape[0]), _dev_ptr(fit),
+                                            _stream_handle(stream)), None)
 
 
 def pa_kernel_launches():

@@ -492,3 +492,10 @@ pa_status pa_population_device(pa_ctx* ctx, uint8_t** pop_dev, void** fit_dev) {
 }
 
 }  // extern "C"
+
+namespace pa {
+// Configuration check and per-thread error text for entry points that run
+// without a context.
+bool config_ok(const pa_config* c, std::string* why) { return validate_config(c, why) == PA_OK; }
+void set_thread_error(const std::string& msg) { t_create_error = msg; }
+}  // namespace pa
