@@ -388,7 +388,25 @@ pa_status pa_kmeans_seed(pa_ctx* ctx, int32_t* labels_host, double* centroids_ho
   return PA_OK;
 }
 
-static pa_status run_generations(pa_ctx* ctx, int32_t generations) {
+// G generations on the resident population.  One fused cluster launch
+// (pa_solve.cu) when the instance fits; otherwise one evaluation and one GA
+// launch per generation.  Either way the fitness buffer ends up holding the
+// fitness of the population it left behind only in the fused case.
+static pa_status run_generations(pa_ctx* ctx, int32_t generations, bool* final_evaluated) {
+  *final_evaluated = false;
+  if (generations == 0) return PA_OK;
+  {
+    cudaError_t e = pa::launch_solve(ctx, ctx->pop[ctx->cur], ctx->pop[ctx->cur ^ 1],
+                                     ctx->generation, generations, ctx->fit, nullptr, nullptr,
+                                     ctx->stream);
+    if (e == cudaSuccess) {
+      ctx->cur ^= 1;
+      ctx->generation += generations;
+      *final_evaluated = true;
+      return PA_OK;
+    }
+    if (e != cudaErrorNotSupported) return cuda_check(ctx, e, "solve kernel");
+  }
   for (int32_t g = 0; g < generations; ++g) {
     uint8_t* cur = ctx->pop[ctx->cur];
     uint8_t* nxt = ctx->pop[ctx->cur ^ 1];
@@ -404,7 +422,8 @@ static pa_status run_generations(pa_ctx* ctx, int32_t generations) {
 pa_status pa_step(pa_ctx* ctx, int32_t generations) {
   if (!ctx) return PA_EINVAL;
   if (generations < 0) return fail(ctx, PA_EINVAL, "generations must be >= 0");
-  return run_generations(ctx, generations);
+  bool evaluated = false;
+  return run_generations(ctx, generations, &evaluated);
 }
 
 pa_status pa_solve(pa_ctx* ctx, int32_t generations, uint8_t* best_host, double* best_fit) {
@@ -412,13 +431,25 @@ pa_status pa_solve(pa_ctx* ctx, int32_t generations, uint8_t* best_host, double*
   if (generations < 0) return fail(ctx, PA_EINVAL, "generations must be >= 0");
   pa_status st = pa_kmeans_seed(ctx, nullptr, nullptr);
   if (st != PA_OK) return st;
-  st = run_generations(ctx, generations);
-  if (st != PA_OK) return st;
-  uint8_t* cur = ctx->pop[ctx->cur];
-  PA_TRY(ctx, eval_any(ctx, cur, ctx->cfg.N, ctx->fit), "eval kernel");
   double* best_dev = reinterpret_cast<double*>(ctx->scratch_i64);
-  PA_TRY(ctx, pa::launch_argbest(ctx, ctx->fit, cur, ctx->best_row, best_dev, ctx->stream),
-         "argbest kernel");
+  // fused path: all generations, the final evaluation and the best member
+  // in one cluster launch
+  cudaError_t e = pa::launch_solve(ctx, ctx->pop[0], ctx->pop[1], 0, generations, ctx->fit,
+                                   ctx->best_row, best_dev, ctx->stream);
+  if (e == cudaSuccess) {
+    ctx->cur = 1;
+    ctx->generation = generations;
+  } else if (e == cudaErrorNotSupported) {
+    bool evaluated = false;
+    st = run_generations(ctx, generations, &evaluated);
+    if (st != PA_OK) return st;
+    uint8_t* cur = ctx->pop[ctx->cur];
+    PA_TRY(ctx, eval_any(ctx, cur, ctx->cfg.N, ctx->fit), "eval kernel");
+    PA_TRY(ctx, pa::launch_argbest(ctx, ctx->fit, cur, ctx->best_row, best_dev, ctx->stream),
+           "argbest kernel");
+  } else {
+    return cuda_check(ctx, e, "solve kernel");
+  }
   const int64_t LK = (int64_t)ctx->cfg.L * ctx->cfg.K;
   if (best_host)
     PA_TRY(ctx, cudaMemcpyAsync(best_host, ctx->best_row, (size_t)LK, cudaMemcpyDeviceToHost,

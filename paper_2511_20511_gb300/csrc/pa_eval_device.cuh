@@ -1,0 +1,203 @@
+// pa_eval_device.cuh -- device-side pieces of the fitness evaluation
+// (paper Sec. 3.2, Eq. 3-6) shared by the population kernels of
+// pa_fitness.cu and the fused solve kernel of pa_solve.cu.
+#pragma once
+
+#include "pa_internal.cuh"
+
+namespace pa {
+
+// ----------------------------------------------------------------- decode
+// Pilot -> user maps of NT members: INV[(l*NT + c)*K + p] = k where member c
+// gives pilot p to user k of cell l.  Member c's row l starts at
+// src + c*member_stride + l*K (generic pointer: global or shared memory).
+// Members c >= nvalid get the identity.  Consecutive threads take
+// consecutive members of one cell, so their K-byte targets are adjacent.
+// Out-of-range pilots are skipped: INV only ever holds values < K provided
+// it was initialised (e.g. zeroed) once.
+__device__ __forceinline__ void decode_members(const uint8_t* src, int64_t member_stride,
+                                               int nvalid, int NT, int L, int K,
+                                               uint8_t* INV) {
+  for (int idx = threadIdx.x; idx < NT * L; idx += blockDim.x) {
+    const int l = idx / NT;
+    const int c = idx - l * NT;
+    uint8_t* dst = INV + idx * K;
+    if (c < nvalid) {
+      const uint8_t* row = src + c * member_stride + (int64_t)l * K;
+      for (int k = 0; k < K; ++k) {
+        const int p = row[k];
+        if (p < K) dst[p] = (uint8_t)k;
+      }
+    } else {
+      for (int k = 0; k < K; ++k) dst[k] = (uint8_t)k;
+    }
+  }
+}
+
+// ----------------------------------------------------------------- FP32
+// Packed two-lane FP32 arithmetic (f32x2): one instruction, two independent
+// IEEE single-precision operations, each rounded exactly as the scalar one.
+__device__ __forceinline__ unsigned long long ffma2(unsigned long long a, unsigned long long b,
+                                                    unsigned long long c) {
+  unsigned long long d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+__device__ __forceinline__ unsigned long long fadd2(unsigned long long a, unsigned long long b) {
+  unsigned long long d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ unsigned long long pack2(float lo, float hi) {
+  unsigned long long d;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(d) : "f"(lo), "f"(hi));
+  return d;
+}
+__device__ __forceinline__ void unpack2(unsigned long long v, float& lo, float& hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+
+// Read-only view of the FP32 tables staged in shared memory.
+struct F32Smem {
+  const float* T;    // [L*K rows][RS], own-cell entry zero
+  const float* OWN;  // [L*K]
+  const float* BN;   // [L]
+  int L, K, RS;
+  float M, pc;
+};
+
+// Sum over BSs j of SE for the users holding pilot p in one member, where
+// invp[l*NTK] is the user of cell l holding p.  Accumulates the member's
+// per-pilot interference for all BSs at once: for each cell l, the row of
+// user inv_l(p) (its gains at every BS) is added into NJ accumulators,
+// squared for S2 and plain for S1 (FINITE_M).
+template <int NJ, int VEC, bool FIN>
+__device__ __forceinline__ float eval_pilot_f32(const F32Smem& s, const uint8_t* invp, int NTK) {
+  static_assert(NJ % 2 == 0, "NJ must be even");
+  constexpr int NP = NJ / 2;
+  unsigned long long acc2[NP];
+  unsigned long long acc1[FIN ? NP : 1];
+#pragma unroll
+  for (int c = 0; c < NP; ++c) {
+    acc2[c] = 0ULL;
+    if (FIN) acc1[c] = 0ULL;
+  }
+  const int L = s.L, K = s.K, RS = s.RS;
+  const float* Tl = s.T;
+  for (int l = 0; l < L; ++l, Tl += K * RS) {
+    const int u = invp[l * NTK];
+    const float* row = Tl + u * RS;
+#pragma unroll
+    for (int c = 0; c < NP; ++c) {
+      unsigned long long v;
+      if (VEC == 2)
+        v = reinterpret_cast<const unsigned long long*>(row)[c];
+      else
+        v = pack2(row[2 * c], row[2 * c + 1]);
+      acc2[c] = ffma2(v, v, acc2[c]);
+      if (FIN) acc1[c] = fadd2(acc1[c], v);
+    }
+  }
+  float se = 0.f;
+#pragma unroll
+  for (int c = 0; c < NP; ++c) {
+    float s2[2], s1[2] = {0.f, 0.f};
+    unpack2(acc2[c], s2[0], s2[1]);
+    if (FIN) unpack2(acc1[c], s1[0], s1[1]);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int j = 2 * c + h;
+      if (j < L) {
+        const int u = invp[j * NTK];
+        const float b = s.OWN[j * K + u];
+        const float b2 = b * b;
+        float num, den;
+        if (FIN) {
+          num = s.M * b2;
+          den = fmaf(s.M, s2[h], s.BN[j] * (s1[h] + b + s.pc));
+        } else {
+          num = b2;
+          den = s2[h];
+        }
+        se += __log2f(1.f + __fdividef(num, den));
+      }
+    }
+  }
+  return se;
+}
+
+// ----------------------------------------------------------------- FP64
+// log2 by the atanh series ln m = 2 sum_{n>=0} s^(2n+1)/(2n+1), s = (m-1)/(m+1)
+// (Abramowitz & Stegun 4.1.27) after x = m 2^e, m in [sqrt(1/2), sqrt(2));
+// every operation separately rounded so that the result is reproducible.
+__device__ __forceinline__ double log2_series(double x) {
+  if (isinf(x)) return x;
+  const long long bits = __double_as_longlong(x);
+  const int E = (int)((bits >> 52) & 0x7ff) - 1022;  // x = f 2^E, f in [0.5, 1)
+  const double f = __longlong_as_double((bits & 0x800FFFFFFFFFFFFFLL) | 0x3FE0000000000000LL);
+  double m;
+  int e;
+  if (f < 0.70710678118654752440) {
+    m = __dmul_rn(f, 2.0);
+    e = E - 1;
+  } else {
+    m = f;
+    e = E;
+  }
+  const double s = __ddiv_rn(__dsub_rn(m, 1.0), __dadd_rn(m, 1.0));
+  const double t = __dmul_rn(s, s);
+  double p = 1.0 / 23.0;
+  p = __dadd_rn(__dmul_rn(p, t), 1.0 / 21.0);
+  p = __dadd_rn(__dmul_rn(p, t), 1.0 / 19.0);
+  p = __dadd_rn(__dmul_rn(p, t), 1.0 / 17.0);
+  p = __dadd_rn(__dmul_rn(p, t), 1.0 / 15.0);
+  p = __dadd_rn(__dmul_rn(p, t), 1.0 / 13.0);
+  p = __dadd_rn(__dmul_rn(p, t), 1.0 / 11.0);
+  p = __dadd_rn(__dmul_rn(p, t), 1.0 / 9.0);
+  p = __dadd_rn(__dmul_rn(p, t), 1.0 / 7.0);
+  p = __dadd_rn(__dmul_rn(p, t), 1.0 / 5.0);
+  p = __dadd_rn(__dmul_rn(p, t), 1.0 / 3.0);
+  p = __dadd_rn(__dmul_rn(p, t), 1.0);
+  const double ln_m = __dmul_rn(__dmul_rn(2.0, s), p);
+  return __dadd_rn((double)e, __dmul_rn(ln_m, 1.44269504088896340736));
+}
+
+// SE of user k of cell j with pilot p in one member (FP64, the oracle's
+// operation order): inv[l*K + q] = user of cell l holding pilot q.
+__device__ __forceinline__ double se_user_f64(const double* __restrict__ beta,
+                                              const double* __restrict__ bnc, const uint8_t* inv,
+                                              int L, int K, int j, int k, int p, int fin,
+                                              double M, double pc) {
+  const double* bj = beta + (size_t)j * L * K;
+  double s2 = 0.0, s1 = 0.0;
+  for (int l = 0; l < L; ++l) {
+    const double b = __ldg(bj + l * K + inv[l * K + p]);
+    if (fin) s1 = __dadd_rn(s1, b);
+    if (l != j) s2 = __dadd_rn(s2, __dmul_rn(b, b));
+  }
+  const double own = __ldg(bj + j * K + k);
+  const double own2 = __dmul_rn(own, own);
+  double sinr;
+  if (fin) {
+    const double num = __dmul_rn(M, own2);
+    const double den = __dadd_rn(__dmul_rn(M, s2), __dmul_rn(__ldg(bnc + j), __dadd_rn(s1, pc)));
+    sinr = __ddiv_rn(num, den);
+  } else {
+    sinr = __ddiv_rn(own2, s2);
+  }
+  return log2_series(__dadd_rn(1.0, sinr));
+}
+
+// Eq. 6 sum of one member's per-user SE (se[j*K + k]) in the oracle's order:
+// per cell over k, then over cells.
+__device__ __forceinline__ double sum_se_f64(const double* se, int L, int K) {
+  double fitness = 0.0;
+  for (int j = 0; j < L; ++j) {
+    double cell = 0.0;
+    for (int k = 0; k < K; ++k) cell = __dadd_rn(cell, se[j * K + k]);
+    fitness = __dadd_rn(fitness, cell);
+  }
+  return fitness;
+}
+
+}  // namespace pa

@@ -29,7 +29,7 @@
 #include <algorithm>
 #include <mutex>
 
-#include "pa_internal.cuh"
+#include "pa_eval_device.cuh"
 
 namespace pa {
 namespace {
@@ -46,30 +46,6 @@ struct F32Args {
   float M, pc;
 };
 
-// Decode the pilots of NT chromosomes starting at n0 into
-// inv[(l*NT + c)*K + p] = user of cell l holding pilot p in chromosome c.
-// Out-of-range pilots are skipped (entries stay in range: the buffer is
-// zeroed at kernel start and only ever receives values < K).
-__device__ __forceinline__ void decode_tile(const F32Args& a, int64_t n0, uint8_t* inv) {
-  const int L = a.L, K = a.K, NT = a.NT;
-  const int64_t LK = (int64_t)L * K;
-  for (int idx = threadIdx.x; idx < NT * L; idx += blockDim.x) {
-    const int c = idx / L;
-    const int l = idx - c * L;
-    uint8_t* dst = inv + (l * NT + c) * K;
-    const int64_t n = n0 + c;
-    if (n < a.n) {
-      const uint8_t* row = a.pop + n * LK + (int64_t)l * K;
-      for (int k = 0; k < K; ++k) {
-        const int p = __ldg(row + k);
-        if (p < K) dst[p] = (uint8_t)k;
-      }
-    } else {
-      for (int k = 0; k < K; ++k) dst[k] = (uint8_t)k;
-    }
-  }
-}
-
 template <int NJ, int VEC, bool FIN>
 __global__ void __launch_bounds__(512) k_eval_f32(const F32Args a) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -79,7 +55,8 @@ __global__ void __launch_bounds__(512) k_eval_f32(const F32Args a) {
   float* PART = BN + ((a.L + 3) & ~3);
   uint8_t* INV = reinterpret_cast<uint8_t*>(PART + ((a.NTK + 3) & ~3));
   const int tid = threadIdx.x;
-  const int L = a.L, K = a.K, NT = a.NT, NTK = a.NTK, RS = a.RS;
+  const int L = a.L, K = a.K, NT = a.NT, NTK = a.NTK;
+  const int64_t LK = (int64_t)L * K;
 
   // Stage the instance tables once per block.
   {
@@ -92,69 +69,19 @@ __global__ void __launch_bounds__(512) k_eval_f32(const F32Args a) {
     for (int i = tid; i < L * NTK; i += blockDim.x) INV[i] = 0;
   }
   __syncthreads();
+  const F32Smem sm{T, OWN, BN, L, K, a.RS, a.M, a.pc};
 
   const int64_t tiles = (a.n + NT - 1) / NT;
   const bool active = tid < NTK;
   const uint8_t* invp = INV + tid;  // (l*NT + c)*K + p == l*NTK + tid
   for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
     const int64_t n0 = tile * NT;
-    decode_tile(a, n0, INV);
+    const int nvalid = (int)((a.n - n0) < NT ? (a.n - n0) : NT);
+    decode_members(a.pop + n0 * LK, LK, nvalid, NT, L, K, INV);
     __syncthreads();
-    if (active) {
-      float acc2[NJ];
-      float acc1[FIN ? NJ : 1];
-#pragma unroll
-      for (int j = 0; j < NJ; ++j) {
-        acc2[j] = 0.f;
-        if (FIN) acc1[j] = 0.f;
-      }
-      const float* Tl = T;
-      for (int l = 0; l < L; ++l, Tl += K * RS) {
-        const int u = invp[l * NTK];
-        const float* row = Tl + u * RS;
-        if (VEC == 2) {
-          const float2* row2 = reinterpret_cast<const float2*>(row);
-#pragma unroll
-          for (int c = 0; c < NJ / 2; ++c) {
-            const float2 t = row2[c];
-            acc2[2 * c] = fmaf(t.x, t.x, acc2[2 * c]);
-            acc2[2 * c + 1] = fmaf(t.y, t.y, acc2[2 * c + 1]);
-            if (FIN) {
-              acc1[2 * c] += t.x;
-              acc1[2 * c + 1] += t.y;
-            }
-          }
-        } else {
-#pragma unroll
-          for (int c = 0; c < NJ; ++c) {
-            const float t = row[c];
-            acc2[c] = fmaf(t, t, acc2[c]);
-            if (FIN) acc1[c] += t;
-          }
-        }
-      }
-      float se = 0.f;
-#pragma unroll
-      for (int j = 0; j < NJ; ++j) {
-        if (j < L) {
-          const int u = invp[j * NTK];
-          const float b = OWN[j * K + u];
-          const float b2 = b * b;
-          float num, den;
-          if (FIN) {
-            num = a.M * b2;
-            den = fmaf(a.M, acc2[j], BN[j] * (acc1[j] + b + a.pc));
-          } else {
-            num = b2;
-            den = acc2[j];
-          }
-          se += __log2f(1.f + __fdividef(num, den));
-        }
-      }
-      PART[tid] = se;
-    }
+    if (active) PART[tid] = eval_pilot_f32<NJ, VEC, FIN>(sm, invp, NTK);
     __syncthreads();
-    if (tid < NT && n0 + tid < a.n) {
+    if (tid < nvalid) {
       float s = 0.f;
       for (int p = 0; p < K; ++p) s += PART[tid * K + p];
       a.fit[n0 + tid] = s;
@@ -163,41 +90,6 @@ __global__ void __launch_bounds__(512) k_eval_f32(const F32Args a) {
 }
 
 // --------------------------------------------------------------------- FP64
-// log2 by the atanh series ln m = 2 sum_{n>=0} s^(2n+1)/(2n+1), s = (m-1)/(m+1)
-// (Abramowitz & Stegun 4.1.27) after x = m 2^e, m in [sqrt(1/2), sqrt(2));
-// every operation separately rounded so that the result is reproducible.
-__device__ __forceinline__ double log2_series(double x) {
-  if (isinf(x)) return x;
-  const long long bits = __double_as_longlong(x);
-  const int E = (int)((bits >> 52) & 0x7ff) - 1022;  // x = f 2^E, f in [0.5, 1)
-  const double f = __longlong_as_double((bits & 0x800FFFFFFFFFFFFFLL) | 0x3FE0000000000000LL);
-  double m;
-  int e;
-  if (f < 0.70710678118654752440) {
-    m = __dmul_rn(f, 2.0);
-    e = E - 1;
-  } else {
-    m = f;
-    e = E;
-  }
-  const double s = __ddiv_rn(__dsub_rn(m, 1.0), __dadd_rn(m, 1.0));
-  const double t = __dmul_rn(s, s);
-  double p = 1.0 / 23.0;
-  p = __dadd_rn(__dmul_rn(p, t), 1.0 / 21.0);
-  p = __dadd_rn(__dmul_rn(p, t), 1.0 / 19.0);
-  p = __dadd_rn(__dmul_rn(p, t), 1.0 / 17.0);
-  p = __dadd_rn(__dmul_rn(p, t), 1.0 / 15.0);
-  p = __dadd_rn(__dmul_rn(p, t), 1.0 / 13.0);
-  p = __dadd_rn(__dmul_rn(p, t), 1.0 / 11.0);
-  p = __dadd_rn(__dmul_rn(p, t), 1.0 / 9.0);
-  p = __dadd_rn(__dmul_rn(p, t), 1.0 / 7.0);
-  p = __dadd_rn(__dmul_rn(p, t), 1.0 / 5.0);
-  p = __dadd_rn(__dmul_rn(p, t), 1.0 / 3.0);
-  p = __dadd_rn(__dmul_rn(p, t), 1.0);
-  const double ln_m = __dmul_rn(__dmul_rn(2.0, s), p);
-  return __dadd_rn((double)e, __dmul_rn(ln_m, 1.44269504088896340736));
-}
-
 struct F64Args {
   const uint8_t* pop;
   int64_t n;
@@ -229,37 +121,10 @@ __global__ void __launch_bounds__(256) k_eval_f64(const F64Args a) {
     __syncthreads();
     for (int r = threadIdx.x; r < LK; r += blockDim.x) {
       const int j = r / K, k = r - j * K;
-      const int p = X[r];
-      const double* bj = a.beta + (size_t)j * LK;
-      double s2 = 0.0, s1 = 0.0;
-      for (int l = 0; l < L; ++l) {
-        const double b = __ldg(bj + l * K + INV[l * K + p]);
-        if (a.fin) s1 = __dadd_rn(s1, b);
-        if (l != j) s2 = __dadd_rn(s2, __dmul_rn(b, b));
-      }
-      const double own = __ldg(bj + j * K + k);
-      const double own2 = __dmul_rn(own, own);
-      double sinr;
-      if (a.fin) {
-        const double num = __dmul_rn(a.M, own2);
-        const double den =
-            __dadd_rn(__dmul_rn(a.M, s2), __dmul_rn(__ldg(a.bnc + j), __dadd_rn(s1, a.pc)));
-        sinr = __ddiv_rn(num, den);
-      } else {
-        sinr = __ddiv_rn(own2, s2);
-      }
-      SE[r] = log2_series(__dadd_rn(1.0, sinr));
+      SE[r] = se_user_f64(a.beta, a.bnc, INV, L, K, j, k, X[r], a.fin, a.M, a.pc);
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-      double fitness = 0.0;
-      for (int j = 0; j < L; ++j) {
-        double cell = 0.0;
-        for (int k = 0; k < K; ++k) cell = __dadd_rn(cell, SE[j * K + k]);
-        fitness = __dadd_rn(fitness, cell);
-      }
-      a.fit[n] = fitness;
-    }
+    if (threadIdx.x == 0) a.fit[n] = sum_se_f64(SE, L, K);
   }
 }
 

@@ -57,6 +57,7 @@ struct pa_ctx {
   int cur = 0;
   void* fit = nullptr;         // [N] float or double
   int32_t generation = 0;
+  int solve_C = -1;            // cluster size of the fused solve kernel (-1: not chosen, 0: none)
   // scratch
   int64_t* scratch_i64 = nullptr;  // small device scratch (flags, argbest)
   uint8_t* best_row = nullptr;     // [L*K]
@@ -93,6 +94,9 @@ cudaError_t launch_ga_step(const pa_ctx* ctx, const uint8_t* pop, const void* fi
 cudaError_t launch_seed(pa_ctx* ctx, uint8_t* pop, cudaStream_t st);
 cudaError_t launch_argbest(const pa_ctx* ctx, const void* fit, const uint8_t* pop,
                            uint8_t* best_row, double* best_fit_dev, cudaStream_t st);
+// pa_solve.cu
+cudaError_t launch_solve(pa_ctx* ctx, const uint8_t* pop_in, uint8_t* pop_out, int gen0, int G,
+                         void* fit_out, uint8_t* best_row, double* best_fit, cudaStream_t st);
 cudaError_t launch_validate(const pa_ctx* ctx, const uint8_t* pop, int64_t n, int64_t* first_bad,
                             cudaStream_t st);
 

@@ -1,0 +1,479 @@
+// pa_solve.cu -- whole GA runs (Alg. 1 loop) in one launch of one
+// thread-block cluster per instance.
+//
+// Each of the C CTAs of the cluster owns NT consecutive members of the
+// population in its shared memory, next to its own copy of the instance
+// tables.  One generation:
+//   1. every CTA evaluates its members (Eq. 3-6) and writes their fitness
+//      into every CTA's copy of the fitness vector (distributed shared
+//      memory stores);
+//   2. one cluster barrier (release/acquire): all fitness values and all
+//      members of this generation are visible cluster-wide;
+//   3. every CTA builds its own child slots (one warp per child): elites by
+//      (fitness desc, index asc), tournaments over the local fitness copy,
+//      parent rows read from their owners' shared memory, row-wise one-cut
+//      crossover, per-row swap mutation -- the same draws as k_ga_step.
+// Populations and fitness vectors are double-buffered, so one barrier per
+// generation suffices: a buffer is rewritten one generation after it was
+// read, and every CTA finished that read before arriving at the barrier the
+// writer has passed.  The barrier is the hardware cluster barrier (no
+// software spin).  After G generations the final population is evaluated,
+// written to global memory with its fitness, and CTA 0 selects the best
+// member.
+#include <cooperative_groups.h>
+
+#include <algorithm>
+#include <atomic>
+#include <mutex>
+
+#include "pa_eval_device.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace pa {
+namespace {
+
+constexpr int kSolveThreads = 256;
+
+struct SolveArgs {
+  const uint8_t* pop_in;  // N*LK, starting population
+  uint8_t* pop_out;       // N*LK, final population
+  void* fit_out;          // N fitness values of the final population
+  uint8_t* best_row;      // LK, or null
+  double* best_fit;       // 1, or null
+  int N, L, K, E, tour;
+  uint64_t pc_thresh, pm_thresh, seed;
+  int gen0, G;
+  int NT;    // members per CTA
+  int MS;    // member stride in shared memory (bytes, multiple of 16, >= L*K)
+  int NTT;   // members per evaluation pass
+  // FP32 tables
+  const float* tab;
+  const float* own;
+  const float* bn;
+  int RS;
+  int64_t tab_floats;
+  float M32, pc32;
+  // FP64 data
+  const double* beta;
+  const double* bnc;
+  double M64, pc64;
+  int fin;
+};
+
+template <typename FT>
+__device__ __forceinline__ bool better_s(const FT* fit, int a, int b) {
+  const FT fa = fit[a], fb = fit[b];
+  if (fa > fb) return true;
+  if (fa < fb) return false;
+  return a < b;
+}
+
+// Block-wide best member by (fitness desc, index asc), skipping excluded[0..nex).
+template <typename FT>
+__device__ int block_best_s(const FT* fit, int N, const int* excluded, int nex, int* red) {
+  int best = -1;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    bool skip = false;
+    for (int e = 0; e < nex; ++e) skip |= (excluded[e] == i);
+    if (skip) continue;
+    if (best < 0 || better_s(fit, i, best)) best = i;
+  }
+  for (int off = 16; off > 0; off >>= 1) {
+    const int o = __shfl_down_sync(0xffffffffu, best, off);
+    if (o >= 0 && (best < 0 || better_s(fit, o, best))) best = o;
+  }
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = best;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int b = -1;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      const int o = red[w];
+      if (o >= 0 && (b < 0 || better_s(fit, o, b))) b = o;
+    }
+    red[32] = b;
+  }
+  __syncthreads();
+  const int r = red[32];
+  __syncthreads();
+  return r;
+}
+
+__device__ __forceinline__ void swap2(uint8_t* row, int K, uint32_t ui, uint32_t uj) {
+  if (K < 2) return;
+  const int i = (int)below(ui, (uint32_t)K);
+  const int jj = (int)below(uj, (uint32_t)(K - 1));
+  const int j = jj + (jj >= i ? 1 : 0);
+  const uint8_t t = row[i];
+  row[i] = row[j];
+  row[j] = t;
+}
+
+// 32-bit word w of a child: bytes below `split` from parent A, the rest from
+// parent B (row-wise crossover cut at a byte offset).
+__device__ __forceinline__ uint32_t merge_word(uint32_t a, uint32_t b, int w, int64_t split) {
+  const int64_t lo = 4 * (int64_t)w;
+  if (lo + 4 <= split) return a;
+  if (lo >= split) return b;
+  const int na = (int)(split - lo);  // 1..3 bytes from A
+  const uint32_t mask = (1u << (8 * na)) - 1u;
+  return (a & mask) | (b & ~mask);
+}
+
+template <typename FT, int NJ, int VEC, bool FIN>
+__global__ void __launch_bounds__(kSolveThreads) k_solve(const SolveArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ int elites[64];
+  __shared__ int red[33];
+  cg::cluster_group cluster = cg::this_cluster();
+  const int rank = (int)cluster.block_rank();
+  const int C = (int)cluster.num_blocks();
+  const int tid = threadIdx.x;
+  const int L = a.L, K = a.K, N = a.N, NT = a.NT, MS = a.MS, NTT = a.NTT;
+  const int LK = L * K;
+  constexpr bool F64 = sizeof(FT) == 8;
+
+  // ---- carve shared memory
+  unsigned char* p = smem;
+  float* T = nullptr;
+  float* OWN = nullptr;
+  float* BN = nullptr;
+  if (!F64) {
+    T = reinterpret_cast<float*>(p);
+    p += 4 * a.tab_floats;
+    OWN = reinterpret_cast<float*>(p);
+    p += 4 * ((LK + 3) & ~3);
+    BN = reinterpret_cast<float*>(p);
+    p += 4 * ((L + 3) & ~3);
+  }
+  FT* FIT[2];
+  FIT[0] = reinterpret_cast<FT*>(p);
+  p += sizeof(FT) * ((N + 1) & ~1);
+  FIT[1] = reinterpret_cast<FT*>(p);
+  p += sizeof(FT) * ((N + 1) & ~1);
+  double* SE = reinterpret_cast<double*>(p);  // FP64: NTT*LK per-user SE
+  float* PART = reinterpret_cast<float*>(p);  // FP32: NTT*K per-pilot sums
+  p += F64 ? 8 * (size_t)NTT * LK : 4 * (size_t)((NTT * K + 3) & ~3);
+  uint8_t* POP[2];
+  POP[0] = p;
+  p += (size_t)NT * MS;
+  POP[1] = p;
+  p += (size_t)NT * MS;
+  uint8_t* INV = p;  // FP32: [L][NTT][K]; FP64: [NTT][L][K]
+
+  const int base_n = rank * NT;
+  const int nvalid = max(0, min(NT, N - base_n));
+
+  // ---- stage tables and own members
+  if (!F64) {
+    const float4* s4 = reinterpret_cast<const float4*>(a.tab);
+    float4* d4 = reinterpret_cast<float4*>(T);
+    for (int64_t i = tid; i < a.tab_floats / 4; i += blockDim.x) d4[i] = __ldg(s4 + i);
+    for (int i = tid; i < LK; i += blockDim.x) OWN[i] = __ldg(a.own + i);
+    if (FIN)
+      for (int i = tid; i < L; i += blockDim.x) BN[i] = __ldg(a.bn + i);
+  }
+  for (int i = tid; i < NTT * LK; i += blockDim.x) INV[i] = 0;
+  for (int c = 0; c < nvalid; ++c) {
+    const uint8_t* src = a.pop_in + (int64_t)(base_n + c) * LK;
+    for (int r = tid; r < LK; r += blockDim.x) POP[0][c * MS + r] = src[r];
+  }
+  __syncthreads();
+  const F32Smem sm{T, OWN, BN, L, K, a.RS, a.M32, a.pc32};
+
+  int cur = 0;
+  const int lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+  for (int g = 0;; ++g) {
+    FT* fit = FIT[g & 1];
+    const uint8_t* popc = POP[cur];
+    // ---- 1. evaluate own members, broadcast their fitness
+    for (int c0 = 0; c0 < nvalid; c0 += NTT) {
+      const int nv = min(NTT, nvalid - c0);
+      if (!F64) {
+        decode_members(popc + c0 * MS, MS, nv, NTT, L, K, INV);
+        __syncthreads();
+        if (tid < NTT * K) PART[tid] = eval_pilot_f32<NJ, VEC, FIN>(sm, INV + tid, NTT * K);
+        __syncthreads();
+        if (tid < nv) {
+          float s = 0.f;
+          for (int q = 0; q < K; ++q) s += PART[tid * K + q];
+          const int n = base_n + c0 + tid;
+          for (int r = 0; r < C; ++r) cluster.map_shared_rank(fit, r)[n] = (FT)s;
+        }
+      } else {
+        for (int i = tid; i < nv * LK; i += blockDim.x) {
+          const int c = i / LK, u = i - c * LK, l = u / K, k = u - l * K;
+          int q = popc[(c0 + c) * MS + u];
+          q = q < K ? q : K - 1;
+          INV[c * LK + l * K + q] = (uint8_t)k;
+        }
+        __syncthreads();
+        for (int i = tid; i < nv * LK; i += blockDim.x) {
+          const int c = i / LK, u = i - c * LK, j = u / K, k = u - j * K;
+          int q = popc[(c0 + c) * MS + u];
+          q = q < K ? q : K - 1;
+          SE[i] = se_user_f64(a.beta, a.bnc, INV + c * LK, L, K, j, k, q, a.fin, a.M64, a.pc64);
+        }
+        __syncthreads();
+        if (tid < nv) {
+          const double s = sum_se_f64(SE + tid * LK, L, K);
+          const int n = base_n + c0 + tid;
+          for (int r = 0; r < C; ++r) cluster.map_shared_rank(fit, r)[n] = (FT)s;
+        }
+      }
+      __syncthreads();
+    }
+    // ---- 2. all fitness values and members of generation g are visible
+    cluster.sync();
+    if (g == a.G) break;
+    // ---- 3. children of this CTA's slots
+    const int E = a.E;
+    if (base_n < E) {
+      for (int e = 0; e < E; ++e) {
+        const int b = block_best_s(fit, N, elites, e, red);
+        if (tid == 0) elites[e] = b;
+        __syncthreads();
+      }
+    }
+    uint8_t* popn = POP[cur ^ 1];
+    const int T_ = a.tour;
+    const int nwords = (LK + 3) >> 2;
+    for (int i = warp; i < nvalid; i += nwarps) {
+      const int n = base_n + i;
+      uint32_t* child = reinterpret_cast<uint32_t*>(popn + i * MS);
+      int pa_, pb_;
+      int64_t split;
+      DrawStream ds(a.seed, (uint64_t)n, (uint64_t)(a.gen0 + g), kTagGa);
+      if (n < E) {
+        pa_ = pb_ = elites[n];
+        split = LK;
+      } else {
+        int best = -1;
+        for (int t = lane; t < T_; t += 32) {
+          const int c = (int)below(ds.draw((uint32_t)t), (uint32_t)N);
+          if (best < 0 || better_s(fit, c, best)) best = c;
+        }
+        for (int off = 16; off > 0; off >>= 1) {
+          const int o = __shfl_xor_sync(0xffffffffu, best, off);
+          if (o >= 0 && (best < 0 || better_s(fit, o, best))) best = o;
+        }
+        pa_ = best;
+        best = -1;
+        for (int t = lane; t < T_; t += 32) {
+          const int c = (int)below(ds.draw((uint32_t)(T_ + t)), (uint32_t)N);
+          if (best < 0 || better_s(fit, c, best)) best = c;
+        }
+        for (int off = 16; off > 0; off >>= 1) {
+          const int o = __shfl_xor_sync(0xffffffffu, best, off);
+          if (o >= 0 && (best < 0 || better_s(fit, o, best))) best = o;
+        }
+        pb_ = best;
+        const uint32_t u_cross = ds.draw((uint32_t)(2 * T_));
+        const uint32_t u_cut = ds.draw((uint32_t)(2 * T_ + 1));
+        int cut = L;
+        if ((uint64_t)u_cross < a.pc_thresh) cut = 1 + (int)below(u_cut, (uint32_t)(L - 1));
+        split = (int64_t)cut * K;
+      }
+      const uint32_t* A = reinterpret_cast<const uint32_t*>(
+          cluster.map_shared_rank(POP[cur], pa_ / NT) + (pa_ % NT) * MS);
+      const uint32_t* B = reinterpret_cast<const uint32_t*>(
+          cluster.map_shared_rank(POP[cur], pb_ / NT) + (pb_ % NT) * MS);
+      for (int w = lane; w < nwords; w += 32) child[w] = merge_word(A[w], B[w], w, split);
+      __syncwarp();
+      if (n >= E) {
+        uint8_t* cb = reinterpret_cast<uint8_t*>(child);
+        for (int l = lane; l < L; l += 32) {
+          const uint32_t base = (uint32_t)(2 * T_ + 2 + 3 * l);
+          const uint32_t u_mut = ds.draw(base);
+          const uint32_t ui = ds.draw(base + 1);
+          const uint32_t uj = ds.draw(base + 2);
+          if ((uint64_t)u_mut < a.pm_thresh) swap2(cb + l * K, K, ui, uj);
+        }
+      }
+      __syncwarp();
+    }
+    cur ^= 1;
+    __syncthreads();
+  }
+
+  // ---- outputs: final population and fitness, best member
+  const FT* fit = FIT[a.G & 1];
+  for (int c = 0; c < nvalid; ++c) {
+    uint8_t* dst = a.pop_out + (int64_t)(base_n + c) * LK;
+    for (int r = tid; r < LK; r += blockDim.x) dst[r] = POP[cur][c * MS + r];
+  }
+  FT* fo = static_cast<FT*>(a.fit_out);
+  for (int c = tid; c < nvalid; c += blockDim.x) fo[base_n + c] = fit[base_n + c];
+  if (rank == 0 && a.best_row) {
+    const int b = block_best_s(fit, N, elites, 0, red);
+    const uint8_t* src = cluster.map_shared_rank(POP[cur], b / NT) + (b % NT) * MS;
+    for (int r = tid; r < LK; r += blockDim.x) a.best_row[r] = src[r];
+    if (tid == 0) *a.best_fit = (double)fit[b];
+  }
+  cluster.sync();  // keep this CTA's shared memory alive for remote readers
+}
+
+// ------------------------------------------------------------------ launch
+struct SolveShape {
+  int C, NT, MS, NTT;
+  size_t smem;
+};
+
+SolveShape solve_shape(const pa_ctx* ctx, int C) {
+  const pa_config& c = ctx->cfg;
+  const bool f64 = c.prec == PA_FP64;
+  const int LK = c.L * c.K;
+  SolveShape s{};
+  s.C = C;
+  s.NT = (c.N + C - 1) / C;
+  s.MS = ((LK + 15) / 16) * 16;
+  if (f64) {
+    s.NTT = std::max(1, std::min(s.NT, 2048 / std::max(1, LK)));
+  } else {
+    s.NTT = std::max(1, std::min(s.NT, kSolveThreads / c.K));
+  }
+  size_t b = 0;
+  if (!f64) {
+    const size_t tab = (((size_t)LK * ctx->t32.RS + 3) / 4) * 4;
+    b += 4 * tab + 4 * (size_t)((LK + 3) & ~3) + 4 * (size_t)((c.L + 3) & ~3);
+  }
+  const size_t fsz = f64 ? 8 : 4;
+  b += 2 * fsz * (size_t)((c.N + 1) & ~1);
+  b += f64 ? 8 * (size_t)s.NTT * LK : 4 * (size_t)((s.NTT * c.K + 3) & ~3);
+  b += 2 * (size_t)s.NT * s.MS;
+  b += f64 ? (size_t)s.NTT * LK : (size_t)c.L * s.NTT * c.K;
+  s.smem = (b + 15) & ~size_t(15);
+  return s;
+}
+
+template <typename FT, int NJ, int VEC, bool FIN>
+cudaError_t run_solve(const SolveArgs& a, const SolveShape& s, bool check_fit, cudaStream_t st) {
+  auto kern = k_solve<FT, NJ, VEC, FIN>;
+  static std::atomic<uint64_t> prepared{0};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const uint64_t bit = 1ULL << (dev & 63);
+  if (!(prepared.load() & bit)) {
+    e = raise_smem_cap((const void*)kern, dev);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess) return e;
+    prepared.fetch_or(bit);
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(s.C, 1, 1);
+  cfg.blockDim = dim3(kSolveThreads, 1, 1);
+  cfg.dynamicSmemBytes = s.smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = s.C;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  if (check_fit) {
+    int nclusters = 0;
+    e = cudaOccupancyMaxActiveClusters(&nclusters, kern, &cfg);
+    if (e != cudaSuccess || nclusters < 1) {
+      (void)cudaGetLastError();
+      return cudaErrorNotSupported;  // this cluster shape cannot be resident
+    }
+  }
+  (void)cudaGetLastError();  // drop a stale error of an earlier call
+  e = cudaLaunchKernelEx(&cfg, kern, a);
+  count_launch();
+  return e;
+}
+
+template <typename FT, int VEC, bool FIN>
+cudaError_t pick_solve(int NJ, const SolveArgs& a, const SolveShape& s, bool chk, cudaStream_t st) {
+  switch (NJ) {
+    case 4: return run_solve<FT, 4, VEC, FIN>(a, s, chk, st);
+    case 8: return run_solve<FT, 8, VEC, FIN>(a, s, chk, st);
+    case 12: return run_solve<FT, 12, VEC, FIN>(a, s, chk, st);
+    case 16: return run_solve<FT, 16, VEC, FIN>(a, s, chk, st);
+    case 20: return run_solve<FT, 20, VEC, FIN>(a, s, chk, st);
+    case 24: return run_solve<FT, 24, VEC, FIN>(a, s, chk, st);
+    case 28: return run_solve<FT, 28, VEC, FIN>(a, s, chk, st);
+    case 32: return run_solve<FT, 32, VEC, FIN>(a, s, chk, st);
+    case 36: return run_solve<FT, 36, VEC, FIN>(a, s, chk, st);
+    case 40: return run_solve<FT, 40, VEC, FIN>(a, s, chk, st);
+    case 44: return run_solve<FT, 44, VEC, FIN>(a, s, chk, st);
+    case 48: return run_solve<FT, 48, VEC, FIN>(a, s, chk, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace
+
+// Run G generations from pop_in into pop_out (fitness of the final
+// population to fit_out; best member to best_row/best_fit when given) in
+// one cluster launch.  The cluster size is the largest of 16 (non-portable),
+// 8, 4, 2, 1 CTAs that can be resident with this shared memory, never more
+// CTAs than members; it is found on the first call and kept in the context.
+// Returns cudaErrorNotSupported when no shape fits (the caller then runs
+// the per-generation kernels).
+cudaError_t launch_solve(pa_ctx* ctx, const uint8_t* pop_in, uint8_t* pop_out, int gen0, int G,
+                         void* fit_out, uint8_t* best_row, double* best_fit, cudaStream_t st) {
+  if (ctx->solve_C == 0) return cudaErrorNotSupported;
+  const pa_config& c = ctx->cfg;
+  static const int sizes[] = {16, 8, 4, 2, 1};
+  for (int C : sizes) {
+    if (ctx->solve_C > 0 && C != ctx->solve_C) continue;
+    if (C > c.N) continue;
+    const SolveShape s = solve_shape(ctx, C);
+    if (s.smem + (64 + 33) * 4 > (size_t)kSmemBudget) continue;
+    SolveArgs a{};
+    a.pop_in = pop_in;
+    a.pop_out = pop_out;
+    a.fit_out = fit_out;
+    a.best_row = best_row;
+    a.best_fit = best_fit;
+    a.N = c.N;
+    a.L = c.L;
+    a.K = c.K;
+    a.E = c.E;
+    a.tour = c.tour;
+    a.pc_thresh = c.pc_thresh;
+    a.pm_thresh = c.pm_thresh;
+    a.seed = c.seed;
+    a.gen0 = gen0;
+    a.G = G;
+    a.NT = s.NT;
+    a.MS = s.MS;
+    a.NTT = s.NTT;
+    a.tab = ctx->t32.tab;
+    a.own = ctx->t32.own;
+    a.bn = ctx->t32.bn;
+    a.RS = ctx->t32.RS;
+    a.tab_floats = (((int64_t)c.L * c.K * ctx->t32.RS + 3) / 4) * 4;
+    a.M32 = ctx->t32.M;
+    a.pc32 = ctx->t32.pc;
+    a.beta = ctx->beta64;
+    a.bnc = ctx->bnc64;
+    a.M64 = c.M;
+    a.pc64 = ctx->pc;
+    a.fin = c.mode == PA_SINR_FINITE_M;
+    const bool fin = a.fin;
+    const bool chk = ctx->solve_C < 0;
+    cudaError_t e;
+    if (c.prec == PA_FP64)
+      e = run_solve<double, 4, 2, false>(a, s, chk, st);
+    else if (ctx->t32.vec == 2)
+      e = fin ? pick_solve<float, 2, true>(ctx->t32.NJ, a, s, chk, st)
+              : pick_solve<float, 2, false>(ctx->t32.NJ, a, s, chk, st);
+    else
+      e = fin ? pick_solve<float, 1, true>(ctx->t32.NJ, a, s, chk, st)
+              : pick_solve<float, 1, false>(ctx->t32.NJ, a, s, chk, st);
+    if (e == cudaErrorNotSupported) continue;
+    if (e == cudaSuccess) ctx->solve_C = C;
+    return e;
+  }
+  ctx->solve_C = 0;
+  return cudaErrorNotSupported;
+}
+
+}  // namespace pa

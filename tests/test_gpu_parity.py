@@ -282,3 +282,35 @@ def test_checkpoint_resume_bit_exact(B):
         c.set_population(bad, 0)
     for x in (a, b, c):
         x.close()
+
+
+@pytest.mark.parametrize("L,K,N,E,mode", [(19, 10, 256, 2, 1), (7, 4, 32, 2, 0), (37, 16, 130, 5, 1),
+                                          (19, 17, 100, 3, 0), (7, 1, 9, 0, 1)])
+def test_fused_generations_equal_per_generation_kernels(B, L, K, N, E, mode):
+    """pa_step runs all generations in one cluster launch; the same
+    generations driven one kernel pair at a time through pa_eval_population
+    and pa_ga_step must give the identical population and fitness (FP32: the
+    arithmetic per member is the same in both kernels)."""
+    inst = inputs.instance(L, K, seed=21, dtype=np.float32)
+    cfg = _cfg(B, L, K, B.PA_FP32, mode, N=N, E=E, seed=77, pm_thresh=B.pa_prob_to_thresh(0.2))
+    ctx = B.Context(cfg, inst["beta"], inst["user_xy_mm"], inst["bs_xy_mm"])
+    try:
+        ctx.kmeans_seed()
+        start, _, _ = ctx.get_population(with_fitness=False)
+        G = 25
+        ctx.step(G)
+        fused, ffit, g = ctx.get_population()
+        assert g == G
+        pop = torch.from_numpy(start).cuda()
+        fit = torch.empty(N, dtype=torch.float32, device="cuda")
+        nxt = torch.empty_like(pop)
+        for gen in range(G):
+            B.pa_eval_population(ctx.handle, pop, fit)
+            B.pa_ga_step(ctx.handle, pop, fit, gen, nxt)
+            pop, nxt = nxt, pop
+        B.pa_eval_population(ctx.handle, pop, fit)
+        torch.cuda.synchronize()
+        assert (pop.cpu().numpy() == fused).all()
+        assert (fit.cpu().numpy() == ffit).all()
+    finally:
+        ctx.close()
