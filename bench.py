@@ -239,6 +239,12 @@ def run_ours(args):
 
     if args.only == "eval":
         return run_eval_only(args, B, inputs, ctx, stream, dev, rank)
+    if args.only == "solve":
+        for _ in range(args.warmup + args.steps):
+            ctx.solve(G_GEN)
+        print(json.dumps({"only": "solve", "solves": args.warmup + args.steps}))
+        ctx.close()
+        return 0
 
     # ---- device-resident solves (value)
     for _ in range(args.warmup):
@@ -369,8 +375,9 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
-    ap.add_argument("--only", choices=["all", "eval"], default="all",
-                    help="eval: time only the 2^20-chromosome evaluation (profiling runs)")
+    ap.add_argument("--only", choices=["all", "eval", "solve"], default="all",
+                    help="eval / solve: run only the 2^20-chromosome evaluation or only the "
+                         "solves, untimed (for profilers)")
     args = ap.parse_args()
     if args.warmup < 3:
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)

@@ -96,15 +96,15 @@ struct GaArgs {
   int gen;
 };
 
-// Tournament of size T over draws [first, first + T): lane t < T draws one
-// candidate; the winner is the best by (fitness desc, index asc), which does
-// not depend on the order the candidates are compared in.
+// Best of the candidates drawn by draws dr[0 .. T) (indices uniform with
+// replacement), by (fitness desc, index asc): the winner does not depend on
+// the order the candidates are compared in, so lanes split the work.
 template <typename FT>
-__device__ __forceinline__ int warp_tournament(const FT* fit, int N, int T, DrawStream& ds,
-                                               uint32_t first, int lane) {
+__device__ __forceinline__ int warp_tournament(const FT* fit, int N, int T, const uint32_t* dr,
+                                               int lane) {
   int best = -1;
   for (int t = lane; t < T; t += 32) {
-    const int c = (int)below(ds.draw(first + (uint32_t)t), (uint32_t)N);
+    const int c = (int)below(dr[t], (uint32_t)N);
     if (best < 0 || better(fit, c, best)) best = c;
   }
   for (int off = 16; off > 0; off >>= 1) {
@@ -114,51 +114,59 @@ __device__ __forceinline__ int warp_tournament(const FT* fit, int N, int T, Draw
   return best;
 }
 
-// One warp per child slot.  Lanes draw the tournament candidates in
-// parallel, copy the parents' rows with coalesced byte streams, then apply
-// the per-row swap mutation with one lane per row.
+constexpr int kGaThreads = 256;
+constexpr int kGaChildren = 8;  // child slots per block (one warp each)
+
+// One block per 8 consecutive child slots.  The block first generates all
+// their draws (one Philox block per thread) into shared memory, then each
+// warp builds one child: tournaments in parallel lanes, the parents' rows
+// copied with coalesced byte streams, the per-row swap mutation with one
+// lane per row.
 template <typename FT>
-__global__ void __launch_bounds__(256) k_ga_step(const GaArgs a) {
+__global__ void __launch_bounds__(kGaThreads) k_ga_step(const GaArgs a) {
+  extern __shared__ uint32_t DR[];  // [kGaChildren][nblk*8]
   __shared__ int elites[64];
   __shared__ int red[33];
   const FT* fit = static_cast<const FT*>(a.fit);
   const int64_t LK = (int64_t)a.L * a.K;
-  const int E = a.E;
-  for (int e = 0; e < E; ++e) {
-    const int b = block_best(fit, a.N, elites, e, red);
-    if (threadIdx.x == 0) elites[e] = b;
+  const int E = a.E, T = a.tour;
+  const int nblk = (2 * T + 2 + 3 * a.L + 7) / 8;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int n0 = blockIdx.x * kGaChildren; n0 < a.N; n0 += gridDim.x * kGaChildren) {
+    const int nc = min(kGaChildren, a.N - n0);
+    if (n0 < E) {
+      for (int e = 0; e < E; ++e) {
+        const int b = block_best(fit, a.N, elites, e, red);
+        if (threadIdx.x == 0) elites[e] = b;
+        __syncthreads();
+      }
+    }
+    gen_child_draws(DR, n0, nc, nblk, a.seed, (uint64_t)a.gen, E);
     __syncthreads();
-  }
-  const int lane = threadIdx.x & 31;
-  const int warps = blockDim.x >> 5;
-  const int T = a.tour;
-  for (int n = blockIdx.x * warps + (threadIdx.x >> 5); n < a.N; n += gridDim.x * warps) {
-    uint8_t* __restrict__ child = a.next + n * LK;
-    if (n < E) {
-      const uint8_t* __restrict__ src = a.pop + (int64_t)elites[n] * LK;
-      for (int64_t i = lane; i < LK; i += 32) child[i] = src[i];
-      continue;
+    if (warp < nc) {
+      const int n = n0 + warp;
+      uint8_t* __restrict__ child = a.next + n * LK;
+      if (n < E) {
+        const uint8_t* __restrict__ src = a.pop + (int64_t)elites[n] * LK;
+        for (int64_t i = lane; i < LK; i += 32) child[i] = src[i];
+      } else {
+        const uint32_t* dr = DR + (size_t)warp * nblk * 8;
+        const int pa_ = warp_tournament(fit, a.N, T, dr, lane);
+        const int pb_ = warp_tournament(fit, a.N, T, dr + T, lane);
+        int cut = a.L;
+        if ((uint64_t)dr[2 * T] < a.pc_thresh) cut = 1 + (int)below(dr[2 * T + 1], (uint32_t)(a.L - 1));
+        const uint8_t* __restrict__ A = a.pop + (int64_t)pa_ * LK;
+        const uint8_t* __restrict__ B = a.pop + (int64_t)pb_ * LK;
+        const int64_t split = (int64_t)cut * a.K;
+        for (int64_t i = lane; i < LK; i += 32) child[i] = i < split ? A[i] : B[i];
+        __syncwarp();
+        for (int l = lane; l < a.L; l += 32) {
+          const int base = 2 * T + 2 + 3 * l;
+          if ((uint64_t)dr[base] < a.pm_thresh) swap_two(child + (int64_t)l * a.K, a.K, dr[base + 1], dr[base + 2]);
+        }
+      }
     }
-    DrawStream ds(a.seed, (uint64_t)n, (uint64_t)a.gen, kTagGa);
-    const int pa_ = warp_tournament(fit, a.N, T, ds, 0, lane);
-    const int pb_ = warp_tournament(fit, a.N, T, ds, (uint32_t)T, lane);
-    const uint32_t u_cross = ds.draw((uint32_t)(2 * T));
-    const uint32_t u_cut = ds.draw((uint32_t)(2 * T + 1));
-    int cut = a.L;
-    if ((uint64_t)u_cross < a.pc_thresh) cut = 1 + (int)below(u_cut, (uint32_t)(a.L - 1));
-    const uint8_t* __restrict__ A = a.pop + (int64_t)pa_ * LK;
-    const uint8_t* __restrict__ B = a.pop + (int64_t)pb_ * LK;
-    const int64_t split = (int64_t)cut * a.K;
-    for (int64_t i = lane; i < LK; i += 32) child[i] = i < split ? A[i] : B[i];
-    __syncwarp();
-    for (int l = lane; l < a.L; l += 32) {
-      const uint32_t base = (uint32_t)(2 * T + 2 + 3 * l);
-      const uint32_t u_mut = ds.draw(base);
-      const uint32_t ui = ds.draw(base + 1);
-      const uint32_t uj = ds.draw(base + 2);
-      if ((uint64_t)u_mut < a.pm_thresh) swap_two(child + (int64_t)l * a.K, a.K, ui, uj);
-    }
-    __syncwarp();
+    __syncthreads();
   }
 }
 
@@ -398,13 +406,15 @@ cudaError_t launch_ga_step(const pa_ctx* ctx, const uint8_t* pop, const void* fi
   a.pm_thresh = c.pm_thresh;
   a.seed = c.seed;
   a.gen = gen;
-  const int threads = 256;  // 8 children (one per warp) per block
-  const int blocks = std::max(1, std::min((c.N + 7) / 8, ctx->num_sms * 4));
+  const int blocks = std::max(1, std::min((c.N + kGaChildren - 1) / kGaChildren,
+                                          ctx->num_sms * 8));
+  const int nblk = (2 * c.tour + 2 + 3 * c.L + 7) / 8;
+  const size_t smem = (size_t)kGaChildren * nblk * 32;
   (void)cudaGetLastError();  // drop a stale error of an earlier call
   if (c.prec == PA_FP64)
-    k_ga_step<double><<<blocks, threads, 0, st>>>(a);
+    k_ga_step<double><<<blocks, kGaThreads, smem, st>>>(a);
   else
-    k_ga_step<float><<<blocks, threads, 0, st>>>(a);
+    k_ga_step<float><<<blocks, kGaThreads, smem, st>>>(a);
   count_launch();
   return cudaGetLastError();
 }

@@ -166,6 +166,26 @@ struct DrawStream {
   }
 };
 
+// Draws of a GA generation for nc consecutive child slots n0 .. n0+nc-1:
+// DR[c*nblk*8 + d] = draw d of slot n0+c (the same values DrawStream gives),
+// one Philox block per thread.  Slots below E (elites) take no draws and
+// are skipped.
+__device__ __forceinline__ void gen_child_draws(uint32_t* DR, int n0, int nc, int nblk,
+                                                uint64_t seed, uint64_t gen, int E) {
+  for (int t = threadIdx.x; t < nc * nblk; t += blockDim.x) {
+    const int c = t / nblk, b = t - c * nblk;
+    const int n = n0 + c;
+    if (n < E) continue;
+    const Philox4x64 r = philox4x64_10((uint64_t)b, (uint64_t)n, gen, kTagGa, seed, 0);
+    uint32_t* o = DR + (size_t)c * nblk * 8 + b * 8;
+#pragma unroll
+    for (int w = 0; w < 4; ++w) {
+      o[2 * w] = (uint32_t)(r.v[w] & 0xFFFFFFFFu);
+      o[2 * w + 1] = (uint32_t)(r.v[w] >> 32);
+    }
+  }
+}
+
 // Uniform integer in [0, n) from a 32-bit draw (multiply-shift).
 __device__ __forceinline__ uint32_t below(uint32_t u, uint32_t n) {
   return (uint32_t)(((uint64_t)u * (uint64_t)n) >> 32);

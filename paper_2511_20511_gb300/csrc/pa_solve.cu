@@ -47,6 +47,8 @@ struct SolveArgs {
   int NT;    // members per CTA
   int MS;    // member stride in shared memory (bytes, multiple of 16, >= L*K)
   int NTT;   // members per evaluation pass
+  int nblk;  // Philox blocks of draws per child
+  int CH;    // children whose draws are staged at once
   // FP32 tables
   const float* tab;
   const float* own;
@@ -161,6 +163,8 @@ __global__ void __launch_bounds__(kSolveThreads) k_solve(const SolveArgs a) {
   POP[1] = p;
   p += (size_t)NT * MS;
   uint8_t* INV = p;  // FP32: [L][NTT][K]; FP64: [NTT][L][K]
+  p += (size_t)((NTT * LK + 15) & ~15);
+  uint32_t* DR = reinterpret_cast<uint32_t*>(p);  // [CH][nblk*8] draws of staged children
 
   const int base_n = rank * NT;
   const int nvalid = max(0, min(NT, N - base_n));
@@ -239,59 +243,61 @@ __global__ void __launch_bounds__(kSolveThreads) k_solve(const SolveArgs a) {
     uint8_t* popn = POP[cur ^ 1];
     const int T_ = a.tour;
     const int nwords = (LK + 3) >> 2;
-    for (int i = warp; i < nvalid; i += nwarps) {
-      const int n = base_n + i;
-      uint32_t* child = reinterpret_cast<uint32_t*>(popn + i * MS);
-      int pa_, pb_;
-      int64_t split;
-      DrawStream ds(a.seed, (uint64_t)n, (uint64_t)(a.gen0 + g), kTagGa);
-      if (n < E) {
-        pa_ = pb_ = elites[n];
-        split = LK;
-      } else {
-        int best = -1;
-        for (int t = lane; t < T_; t += 32) {
-          const int c = (int)below(ds.draw((uint32_t)t), (uint32_t)N);
-          if (best < 0 || better_s(fit, c, best)) best = c;
+    const int nblk = a.nblk;
+    for (int c0 = 0; c0 < nvalid; c0 += a.CH) {
+      const int nc = min(a.CH, nvalid - c0);
+      gen_child_draws(DR, base_n + c0, nc, nblk, a.seed, (uint64_t)(a.gen0 + g), E);
+      __syncthreads();
+      for (int i = warp; i < nc; i += nwarps) {
+        const int n = base_n + c0 + i;
+        const uint32_t* dr = DR + (size_t)i * nblk * 8;
+        uint32_t* child = reinterpret_cast<uint32_t*>(popn + (c0 + i) * MS);
+        int pa_, pb_;
+        int64_t split;
+        if (n < E) {
+          pa_ = pb_ = elites[n];
+          split = LK;
+        } else {
+          int best = -1;
+          for (int t = lane; t < T_; t += 32) {
+            const int c = (int)below(dr[t], (uint32_t)N);
+            if (best < 0 || better_s(fit, c, best)) best = c;
+          }
+          for (int off = 16; off > 0; off >>= 1) {
+            const int o = __shfl_xor_sync(0xffffffffu, best, off);
+            if (o >= 0 && (best < 0 || better_s(fit, o, best))) best = o;
+          }
+          pa_ = best;
+          best = -1;
+          for (int t = lane; t < T_; t += 32) {
+            const int c = (int)below(dr[T_ + t], (uint32_t)N);
+            if (best < 0 || better_s(fit, c, best)) best = c;
+          }
+          for (int off = 16; off > 0; off >>= 1) {
+            const int o = __shfl_xor_sync(0xffffffffu, best, off);
+            if (o >= 0 && (best < 0 || better_s(fit, o, best))) best = o;
+          }
+          pb_ = best;
+          int cut = L;
+          if ((uint64_t)dr[2 * T_] < a.pc_thresh) cut = 1 + (int)below(dr[2 * T_ + 1], (uint32_t)(L - 1));
+          split = (int64_t)cut * K;
         }
-        for (int off = 16; off > 0; off >>= 1) {
-          const int o = __shfl_xor_sync(0xffffffffu, best, off);
-          if (o >= 0 && (best < 0 || better_s(fit, o, best))) best = o;
+        const uint32_t* A = reinterpret_cast<const uint32_t*>(
+            cluster.map_shared_rank(POP[cur], pa_ / NT) + (pa_ % NT) * MS);
+        const uint32_t* B = reinterpret_cast<const uint32_t*>(
+            cluster.map_shared_rank(POP[cur], pb_ / NT) + (pb_ % NT) * MS);
+        for (int w = lane; w < nwords; w += 32) child[w] = merge_word(A[w], B[w], w, split);
+        __syncwarp();
+        if (n >= E) {
+          uint8_t* cb = reinterpret_cast<uint8_t*>(child);
+          for (int l = lane; l < L; l += 32) {
+            const int base = 2 * T_ + 2 + 3 * l;
+            if ((uint64_t)dr[base] < a.pm_thresh) swap2(cb + l * K, K, dr[base + 1], dr[base + 2]);
+          }
         }
-        pa_ = best;
-        best = -1;
-        for (int t = lane; t < T_; t += 32) {
-          const int c = (int)below(ds.draw((uint32_t)(T_ + t)), (uint32_t)N);
-          if (best < 0 || better_s(fit, c, best)) best = c;
-        }
-        for (int off = 16; off > 0; off >>= 1) {
-          const int o = __shfl_xor_sync(0xffffffffu, best, off);
-          if (o >= 0 && (best < 0 || better_s(fit, o, best))) best = o;
-        }
-        pb_ = best;
-        const uint32_t u_cross = ds.draw((uint32_t)(2 * T_));
-        const uint32_t u_cut = ds.draw((uint32_t)(2 * T_ + 1));
-        int cut = L;
-        if ((uint64_t)u_cross < a.pc_thresh) cut = 1 + (int)below(u_cut, (uint32_t)(L - 1));
-        split = (int64_t)cut * K;
+        __syncwarp();
       }
-      const uint32_t* A = reinterpret_cast<const uint32_t*>(
-          cluster.map_shared_rank(POP[cur], pa_ / NT) + (pa_ % NT) * MS);
-      const uint32_t* B = reinterpret_cast<const uint32_t*>(
-          cluster.map_shared_rank(POP[cur], pb_ / NT) + (pb_ % NT) * MS);
-      for (int w = lane; w < nwords; w += 32) child[w] = merge_word(A[w], B[w], w, split);
-      __syncwarp();
-      if (n >= E) {
-        uint8_t* cb = reinterpret_cast<uint8_t*>(child);
-        for (int l = lane; l < L; l += 32) {
-          const uint32_t base = (uint32_t)(2 * T_ + 2 + 3 * l);
-          const uint32_t u_mut = ds.draw(base);
-          const uint32_t ui = ds.draw(base + 1);
-          const uint32_t uj = ds.draw(base + 2);
-          if ((uint64_t)u_mut < a.pm_thresh) swap2(cb + l * K, K, ui, uj);
-        }
-      }
-      __syncwarp();
+      __syncthreads();
     }
     cur ^= 1;
     __syncthreads();
@@ -316,7 +322,7 @@ __global__ void __launch_bounds__(kSolveThreads) k_solve(const SolveArgs a) {
 
 // ------------------------------------------------------------------ launch
 struct SolveShape {
-  int C, NT, MS, NTT;
+  int C, NT, MS, NTT, nblk, CH;
   size_t smem;
 };
 
@@ -325,8 +331,10 @@ SolveShape solve_shape(const pa_ctx* ctx, int C) {
   const bool f64 = c.prec == PA_FP64;
   const int LK = c.L * c.K;
   SolveShape s{};
+  s.nblk = (2 * c.tour + 2 + 3 * c.L + 7) / 8;
   s.C = C;
   s.NT = (c.N + C - 1) / C;
+  s.CH = std::max(1, std::min(s.NT, 16384 / (s.nblk * 32)));
   s.MS = ((LK + 15) / 16) * 16;
   if (f64) {
     s.NTT = std::max(1, std::min(s.NT, 2048 / std::max(1, LK)));
@@ -342,7 +350,8 @@ SolveShape solve_shape(const pa_ctx* ctx, int C) {
   b += 2 * fsz * (size_t)((c.N + 1) & ~1);
   b += f64 ? 8 * (size_t)s.NTT * LK : 4 * (size_t)((s.NTT * c.K + 3) & ~3);
   b += 2 * (size_t)s.NT * s.MS;
-  b += f64 ? (size_t)s.NTT * LK : (size_t)c.L * s.NTT * c.K;
+  b += ((size_t)s.NTT * LK + 15) & ~size_t(15);
+  b += (size_t)s.CH * s.nblk * 32;
   s.smem = (b + 15) & ~size_t(15);
   return s;
 }
@@ -445,6 +454,8 @@ cudaError_t launch_solve(pa_ctx* ctx, const uint8_t* pop_in, uint8_t* pop_out, i
     a.NT = s.NT;
     a.MS = s.MS;
     a.NTT = s.NTT;
+    a.nblk = s.nblk;
+    a.CH = s.CH;
     a.tab = ctx->t32.tab;
     a.own = ctx->t32.own;
     a.bn = ctx->t32.bn;
