@@ -66,15 +66,24 @@ struct F32Smem {
   float M, pc;
 };
 
-// Sum over BSs j of SE for the users holding pilot p in one member, where
-// invp[l*NTK] is the user of cell l holding p.  Accumulates the member's
-// per-pilot interference for all BSs at once: for each cell l, the row of
-// user inv_l(p) (its gains at every BS) is added into NJ accumulators,
-// squared for S2 and plain for S1 (FINITE_M).
-template <int NJ, int VEC, bool FIN>
-__device__ __forceinline__ float eval_pilot_f32(const F32Smem& s, const uint8_t* invp, int NTK) {
-  static_assert(NJ % 2 == 0, "NJ must be even");
-  constexpr int NP = NJ / 2;
+// Threads per (member, pilot) of the FP32 evaluation: two for float2 tables
+// with at least 8 BS columns (each takes half of the columns), else one.
+template <int NJ, int VEC>
+struct PilotSplit {
+  static constexpr int JS = (VEC == 2 && NJ >= 8) ? 2 : 1;
+};
+
+// Sum of SE over the BSs j of this thread's column share for the users
+// holding pilot p in one member, where invp[l*stride] is the user of cell l
+// holding p.  Accumulates the member's per-pilot interference for all BSs of
+// the share at once: for each cell l, the row of user inv_l(p) (its gains at
+// every BS) is added into the accumulators, squared for S2 and plain for S1
+// (FINITE_M).  Share h of JS covers column pairs [h*NJ/(2 JS), (h+1)*NJ/(2 JS)).
+template <int NJ, int VEC, bool FIN, int JS>
+__device__ __forceinline__ float eval_pilot_f32(const F32Smem& s, const uint8_t* invp, int stride,
+                                                int h) {
+  static_assert(NJ % (2 * JS) == 0, "NJ must split into JS shares of column pairs");
+  constexpr int NP = NJ / 2 / JS;
   unsigned long long acc2[NP];
   unsigned long long acc1[FIN ? NP : 1];
 #pragma unroll
@@ -83,9 +92,10 @@ __device__ __forceinline__ float eval_pilot_f32(const F32Smem& s, const uint8_t*
     if (FIN) acc1[c] = 0ULL;
   }
   const int L = s.L, K = s.K, RS = s.RS;
-  const float* Tl = s.T;
+  const int c0 = h * NP;
+  const float* Tl = s.T + 2 * c0;
   for (int l = 0; l < L; ++l, Tl += K * RS) {
-    const int u = invp[l * NTK];
+    const int u = invp[l * stride];
     const float* row = Tl + u * RS;
 #pragma unroll
     for (int c = 0; c < NP; ++c) {
@@ -105,19 +115,19 @@ __device__ __forceinline__ float eval_pilot_f32(const F32Smem& s, const uint8_t*
     unpack2(acc2[c], s2[0], s2[1]);
     if (FIN) unpack2(acc1[c], s1[0], s1[1]);
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int j = 2 * c + h;
+    for (int hh = 0; hh < 2; ++hh) {
+      const int j = 2 * (c0 + c) + hh;
       if (j < L) {
-        const int u = invp[j * NTK];
+        const int u = invp[j * stride];
         const float b = s.OWN[j * K + u];
         const float b2 = b * b;
         float num, den;
         if (FIN) {
           num = s.M * b2;
-          den = fmaf(s.M, s2[h], s.BN[j] * (s1[h] + b + s.pc));
+          den = fmaf(s.M, s2[hh], s.BN[j] * (s1[hh] + b + s.pc));
         } else {
           num = b2;
-          den = s2[h];
+          den = s2[hh];
         }
         se += __log2f(1.f + __fdividef(num, den));
       }

@@ -53,7 +53,7 @@ __global__ void __launch_bounds__(512) k_eval_f32(const F32Args a) {
   float* OWN = T + a.tab_floats;
   float* BN = OWN + ((a.L * a.K + 3) & ~3);
   float* PART = BN + ((a.L + 3) & ~3);
-  uint8_t* INV = reinterpret_cast<uint8_t*>(PART + ((a.NTK + 3) & ~3));
+  uint8_t* INV = reinterpret_cast<uint8_t*>(PART + ((2 * a.NTK + 3) & ~3));
   const int tid = threadIdx.x;
   const int L = a.L, K = a.K, NT = a.NT, NTK = a.NTK;
   const int64_t LK = (int64_t)L * K;
@@ -71,19 +71,26 @@ __global__ void __launch_bounds__(512) k_eval_f32(const F32Args a) {
   __syncthreads();
   const F32Smem sm{T, OWN, BN, L, K, a.RS, a.M, a.pc};
 
+  // thread -> (member c, pilot p) index q = c*K + p and column share h; with
+  // two shares, the lower and upper half-warps take shares 0 and 1 of the
+  // same 16 q's, so each half-warp's float2 loads stay conflict-free
+  constexpr int JS = PilotSplit<NJ, VEC>::JS;
+  const int lane = tid & 31;
+  const int h = JS == 2 ? (lane >> 4) : 0;
+  const int q = JS == 2 ? ((tid >> 5) << 4) + (lane & 15) : tid;
   const int64_t tiles = (a.n + NT - 1) / NT;
-  const bool active = tid < NTK;
-  const uint8_t* invp = INV + tid;  // (l*NT + c)*K + p == l*NTK + tid
+  const bool active = q < NTK;
+  const uint8_t* invp = INV + q;  // (l*NT + c)*K + p == l*NTK + q
   for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
     const int64_t n0 = tile * NT;
     const int nvalid = (int)((a.n - n0) < NT ? (a.n - n0) : NT);
     decode_members(a.pop + n0 * LK, LK, nvalid, NT, L, K, INV);
     __syncthreads();
-    if (active) PART[tid] = eval_pilot_f32<NJ, VEC, FIN>(sm, invp, NTK);
+    if (active) PART[q * JS + h] = eval_pilot_f32<NJ, VEC, FIN, JS>(sm, invp, NTK, h);
     __syncthreads();
     if (tid < nvalid) {
       float s = 0.f;
-      for (int p = 0; p < K; ++p) s += PART[tid * K + p];
+      for (int i = 0; i < K * JS; ++i) s += PART[tid * K * JS + i];
       a.fit[n0 + tid] = s;
     }
   }
@@ -134,23 +141,28 @@ struct F32Launch {
   size_t smem;
 };
 
-F32Launch f32_shape(int L, int K, int RS) {
+// Block shape of k_eval_f32: NT members of K pilots, one thread per (member,
+// pilot) and column share (two shares for float2 tables with NJ >= 8).
+F32Launch f32_shape(int L, int K, int RS, int NJ) {
   F32Launch s{};
+  const int JS = (K <= 16 && NJ >= 8) ? 2 : 1;
+  int NTK;
   if (K <= 16) {
     int base = 32;
     while (base % K) base += 32;  // lcm(K, 32)
     const int m = std::max(1, 256 / base);
-    s.threads = base * m;
-    s.NT = s.threads / K;
+    NTK = base * m;
+    s.NT = NTK / K;
+    s.threads = NTK * JS;
   } else {
     s.NT = std::max(1, 256 / K);
-    s.threads = ((s.NT * K + 31) / 32) * 32;
+    NTK = s.NT * K;
+    s.threads = ((NTK + 31) / 32) * 32;
   }
   const size_t LK = (size_t)L * K;
   const size_t tab = ((LK * RS + 3) / 4) * 4;
-  const size_t NTK = (size_t)s.NT * K;
-  s.smem = 4 * (tab + ((LK + 3) & ~size_t(3)) + ((L + 3) & ~3) + ((NTK + 3) & ~size_t(3))) +
-           ((L * NTK + 15) & ~size_t(15));
+  s.smem = 4 * (tab + ((LK + 3) & ~size_t(3)) + ((L + 3) & ~3) + ((2 * (size_t)NTK + 3) & ~size_t(3))) +
+           (((size_t)L * NTK + 15) & ~size_t(15));
   return s;
 }
 
@@ -249,7 +261,7 @@ bool f32_supported(int L, int K, size_t* smem_bytes) {
   int NJ, RS, vec;
   f32_geometry(L, K, &NJ, &RS, &vec);
   if (NJ > kMaxNJ || K > kMaxK) return false;
-  const F32Launch s = f32_shape(L, K, RS);
+  const F32Launch s = f32_shape(L, K, RS, NJ);
   if (smem_bytes) *smem_bytes = s.smem;
   return s.smem <= (size_t)kSmemBudget;
 }
@@ -259,7 +271,7 @@ cudaError_t launch_eval_f32(const pa_ctx* ctx, const uint8_t* pop, int64_t n, fl
   if (n <= 0) return cudaSuccess;
   const pa::F32Tables& t = ctx->t32;
   const int L = ctx->cfg.L, K = ctx->cfg.K;
-  const F32Launch s = f32_shape(L, K, t.RS);
+  const F32Launch s = f32_shape(L, K, t.RS, t.NJ);
   F32Args a;
   a.pop = pop;
   a.n = n;

@@ -33,7 +33,7 @@ namespace cg = cooperative_groups;
 namespace pa {
 namespace {
 
-constexpr int kSolveThreads = 256;
+constexpr int kSolveThreads = 512;
 
 struct SolveArgs {
   const uint8_t* pop_in;  // N*LK, starting population
@@ -45,7 +45,8 @@ struct SolveArgs {
   uint64_t pc_thresh, pm_thresh, seed;
   int gen0, G;
   int NT;    // members per CTA
-  int MS;    // member stride in shared memory (bytes, multiple of 16, >= L*K)
+  int MS;    // member record size in shared memory (bytes): X, then INV at XO
+  int XO;    // offset of the inverse permutation inside a record
   int NTT;   // members per evaluation pass
   int nblk;  // Philox blocks of draws per child
   int CH;    // children whose draws are staged at once
@@ -123,18 +124,35 @@ __device__ __forceinline__ uint32_t merge_word(uint32_t a, uint32_t b, int w, in
   return (a & mask) | (b & ~mask);
 }
 
+// Remote 32-bit load from another CTA's shared memory (distributed shared
+// memory): `addr` is a shared::cluster address from mapa.
+__device__ __forceinline__ uint32_t ld_dsmem(uint32_t addr) {
+  uint32_t v;
+  asm volatile("ld.shared::cluster.u32 %0, [%1];" : "=r"(v) : "r"(addr));
+  return v;
+}
+__device__ __forceinline__ uint32_t dsmem_addr(const void* local, int rank) {
+  uint32_t a = (uint32_t)__cvta_generic_to_shared(local), r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+  return r;
+}
+
+// Member record in shared memory (MS bytes): the chromosome X (L*K bytes,
+// pilot of each user) at offset 0 and its inverse INV (L*K bytes, user of
+// each pilot, row by row) at offset XO.  Crossover takes whole rows, so the
+// child's INV rows are its parents' INV rows; a swap mutation updates both.
 template <typename FT, int NJ, int VEC, bool FIN>
 __global__ void __launch_bounds__(kSolveThreads) k_solve(const SolveArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int elites[64];
-  __shared__ int red[33];
   cg::cluster_group cluster = cg::this_cluster();
   const int rank = (int)cluster.block_rank();
   const int C = (int)cluster.num_blocks();
   const int tid = threadIdx.x;
-  const int L = a.L, K = a.K, N = a.N, NT = a.NT, MS = a.MS, NTT = a.NTT;
+  const int L = a.L, K = a.K, N = a.N, NT = a.NT, MS = a.MS, XO = a.XO;
   const int LK = L * K;
   constexpr bool F64 = sizeof(FT) == 8;
+  constexpr int JS = F64 ? 1 : PilotSplit<NJ, VEC>::JS;
 
   // ---- carve shared memory
   unsigned char* p = smem;
@@ -155,21 +173,19 @@ __global__ void __launch_bounds__(kSolveThreads) k_solve(const SolveArgs a) {
   FIT[1] = reinterpret_cast<FT*>(p);
   p += sizeof(FT) * ((N + 1) & ~1);
   double* SE = reinterpret_cast<double*>(p);  // FP64: NTT*LK per-user SE
-  float* PART = reinterpret_cast<float*>(p);  // FP32: NTT*K per-pilot sums
-  p += F64 ? 8 * (size_t)NTT * LK : 4 * (size_t)((NTT * K + 3) & ~3);
-  uint8_t* POP[2];
+  float* PART = reinterpret_cast<float*>(p);  // FP32: NTT*K*JS per-share sums
+  p += F64 ? 8 * (size_t)a.NTT * LK : 4 * (size_t)((a.NTT * K * JS + 3) & ~3);
+  unsigned char* POP[2];
   POP[0] = p;
   p += (size_t)NT * MS;
   POP[1] = p;
   p += (size_t)NT * MS;
-  uint8_t* INV = p;  // FP32: [L][NTT][K]; FP64: [NTT][L][K]
-  p += (size_t)((NTT * LK + 15) & ~15);
   uint32_t* DR = reinterpret_cast<uint32_t*>(p);  // [CH][nblk*8] draws of staged children
 
   const int base_n = rank * NT;
   const int nvalid = max(0, min(NT, N - base_n));
 
-  // ---- stage tables and own members
+  // ---- stage tables and own members (X and its inverse)
   if (!F64) {
     const float4* s4 = reinterpret_cast<const float4*>(a.tab);
     float4* d4 = reinterpret_cast<float4*>(T);
@@ -178,46 +194,58 @@ __global__ void __launch_bounds__(kSolveThreads) k_solve(const SolveArgs a) {
     if (FIN)
       for (int i = tid; i < L; i += blockDim.x) BN[i] = __ldg(a.bn + i);
   }
-  for (int i = tid; i < NTT * LK; i += blockDim.x) INV[i] = 0;
-  for (int c = 0; c < nvalid; ++c) {
-    const uint8_t* src = a.pop_in + (int64_t)(base_n + c) * LK;
-    for (int r = tid; r < LK; r += blockDim.x) POP[0][c * MS + r] = src[r];
+  for (int i = tid; i < NT * MS; i += blockDim.x) POP[0][i] = 0;
+  __syncthreads();
+  for (int i = tid; i < nvalid * LK; i += blockDim.x) {
+    const int c = i / LK, r = i - c * LK;
+    POP[0][c * MS + r] = a.pop_in[(int64_t)base_n * LK + i];
+  }
+  __syncthreads();
+  for (int i = tid; i < nvalid * L; i += blockDim.x) {
+    const int c = i / L, l = i - c * L;
+    const uint8_t* x = POP[0] + c * MS + l * K;
+    uint8_t* inv = POP[0] + c * MS + XO + l * K;
+    for (int k = 0; k < K; ++k) {
+      const int q = x[k];
+      if (q < K) inv[q] = (uint8_t)k;
+    }
   }
   __syncthreads();
   const F32Smem sm{T, OWN, BN, L, K, a.RS, a.M32, a.pc32};
 
   int cur = 0;
   const int lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+  const int T_ = a.tour, nblk = a.nblk, E = a.E;
+  const int nwords = MS >> 2;
+  // FP32 evaluation thread roles: q = member*K + pilot, column share h
+  const int h = JS == 2 ? (lane >> 4) : 0;
+  const int q = JS == 2 ? (warp << 4) + (lane & 15) : tid;
   for (int g = 0;; ++g) {
     FT* fit = FIT[g & 1];
-    const uint8_t* popc = POP[cur];
+    const unsigned char* popc = POP[cur];
     // ---- 1. evaluate own members, broadcast their fitness
-    for (int c0 = 0; c0 < nvalid; c0 += NTT) {
-      const int nv = min(NTT, nvalid - c0);
+    for (int c0 = 0; c0 < nvalid; c0 += a.NTT) {
+      const int nv = min(a.NTT, nvalid - c0);
       if (!F64) {
-        decode_members(popc + c0 * MS, MS, nv, NTT, L, K, INV);
-        __syncthreads();
-        if (tid < NTT * K) PART[tid] = eval_pilot_f32<NJ, VEC, FIN>(sm, INV + tid, NTT * K);
+        if (q < nv * K) {
+          const int c = q / K, pp = q - c * K;
+          PART[q * JS + h] =
+              eval_pilot_f32<NJ, VEC, FIN, JS>(sm, popc + (c0 + c) * MS + XO + pp, K, h);
+        }
         __syncthreads();
         if (tid < nv) {
           float s = 0.f;
-          for (int q = 0; q < K; ++q) s += PART[tid * K + q];
+          for (int i = 0; i < K * JS; ++i) s += PART[tid * K * JS + i];
           const int n = base_n + c0 + tid;
           for (int r = 0; r < C; ++r) cluster.map_shared_rank(fit, r)[n] = (FT)s;
         }
       } else {
         for (int i = tid; i < nv * LK; i += blockDim.x) {
-          const int c = i / LK, u = i - c * LK, l = u / K, k = u - l * K;
-          int q = popc[(c0 + c) * MS + u];
-          q = q < K ? q : K - 1;
-          INV[c * LK + l * K + q] = (uint8_t)k;
-        }
-        __syncthreads();
-        for (int i = tid; i < nv * LK; i += blockDim.x) {
           const int c = i / LK, u = i - c * LK, j = u / K, k = u - j * K;
-          int q = popc[(c0 + c) * MS + u];
-          q = q < K ? q : K - 1;
-          SE[i] = se_user_f64(a.beta, a.bnc, INV + c * LK, L, K, j, k, q, a.fin, a.M64, a.pc64);
+          const unsigned char* rec = popc + (c0 + c) * MS;
+          int qq = rec[u];
+          qq = qq < K ? qq : K - 1;
+          SE[i] = se_user_f64(a.beta, a.bnc, rec + XO, L, K, j, k, qq, a.fin, a.M64, a.pc64);
         }
         __syncthreads();
         if (tid < nv) {
@@ -232,21 +260,45 @@ __global__ void __launch_bounds__(kSolveThreads) k_solve(const SolveArgs a) {
     cluster.sync();
     if (g == a.G) break;
     // ---- 3. children of this CTA's slots
-    const int E = a.E;
-    if (base_n < E) {
-      for (int e = 0; e < E; ++e) {
-        const int b = block_best_s(fit, N, elites, e, red);
-        if (tid == 0) elites[e] = b;
-        __syncthreads();
-      }
-    }
-    uint8_t* popn = POP[cur ^ 1];
-    const int T_ = a.tour;
-    const int nwords = (LK + 3) >> 2;
-    const int nblk = a.nblk;
+    unsigned char* popn = POP[cur ^ 1];
     for (int c0 = 0; c0 < nvalid; c0 += a.CH) {
       const int nc = min(a.CH, nvalid - c0);
-      gen_child_draws(DR, base_n + c0, nc, nblk, a.seed, (uint64_t)(a.gen0 + g), E);
+      if (c0 == 0 && base_n < E) {
+        // warp 0: the E elites, one warp-wide argmax per elite, while the
+        // other warps generate the children's draws
+        if (warp == 0) {
+          for (int e = 0; e < E; ++e) {
+            int best = -1;
+            for (int i = lane; i < N; i += 32) {
+              bool taken = false;
+              for (int f = 0; f < e; ++f) taken |= (elites[f] == i);
+              if (!taken && (best < 0 || better_s(fit, i, best))) best = i;
+            }
+            for (int off = 16; off > 0; off >>= 1) {
+              const int o = __shfl_xor_sync(0xffffffffu, best, off);
+              if (o >= 0 && (best < 0 || better_s(fit, o, best))) best = o;
+            }
+            if (lane == 0) elites[e] = best;
+            __syncwarp();
+          }
+        } else {
+          for (int t = tid - 32; t < nc * nblk; t += blockDim.x - 32) {
+            const int c = t / nblk, b = t - c * nblk;
+            const int n = base_n + c0 + c;
+            if (n < E) continue;
+            const Philox4x64 r =
+                philox4x64_10((uint64_t)b, (uint64_t)n, (uint64_t)(a.gen0 + g), kTagGa, a.seed, 0);
+            uint32_t* o = DR + (size_t)c * nblk * 8 + b * 8;
+#pragma unroll
+            for (int w = 0; w < 4; ++w) {
+              o[2 * w] = (uint32_t)(r.v[w] & 0xFFFFFFFFu);
+              o[2 * w + 1] = (uint32_t)(r.v[w] >> 32);
+            }
+          }
+        }
+      } else {
+        gen_child_draws(DR, base_n + c0, nc, nblk, a.seed, (uint64_t)(a.gen0 + g), E);
+      }
       __syncthreads();
       for (int i = warp; i < nc; i += nwarps) {
         const int n = base_n + c0 + i;
@@ -282,17 +334,48 @@ __global__ void __launch_bounds__(kSolveThreads) k_solve(const SolveArgs a) {
           if ((uint64_t)dr[2 * T_] < a.pc_thresh) cut = 1 + (int)below(dr[2 * T_ + 1], (uint32_t)(L - 1));
           split = (int64_t)cut * K;
         }
-        const uint32_t* A = reinterpret_cast<const uint32_t*>(
-            cluster.map_shared_rank(POP[cur], pa_ / NT) + (pa_ % NT) * MS);
-        const uint32_t* B = reinterpret_cast<const uint32_t*>(
-            cluster.map_shared_rank(POP[cur], pb_ / NT) + (pb_ % NT) * MS);
-        for (int w = lane; w < nwords; w += 32) child[w] = merge_word(A[w], B[w], w, split);
+        // parents' records from their owners: all remote loads issued first
+        const uint32_t ra = dsmem_addr(POP[cur] + (pa_ % NT) * MS, pa_ / NT);
+        const uint32_t rb = dsmem_addr(POP[cur] + (pb_ % NT) * MS, pb_ / NT);
+        constexpr int kMaxW = 4;  // words per lane held at once (records <= 512 bytes)
+        uint32_t wa[kMaxW], wb[kMaxW];
+#pragma unroll
+        for (int r = 0; r < kMaxW; ++r) {
+          const int w = lane + 32 * r;
+          if (w < nwords) {
+            wa[r] = ld_dsmem(ra + 4 * w);
+            wb[r] = ld_dsmem(rb + 4 * w);
+          }
+        }
+        for (int w = lane + 32 * kMaxW; w < nwords; w += 32) {  // longer records
+          const int64_t off = 4 * (int64_t)w >= XO ? XO : 0;
+          child[w] = merge_word(ld_dsmem(ra + 4 * w), ld_dsmem(rb + 4 * w), w, split + off);
+        }
+#pragma unroll
+        for (int r = 0; r < kMaxW; ++r) {
+          const int w = lane + 32 * r;
+          if (w < nwords) {
+            const int64_t off = 4 * (int64_t)w >= XO ? XO : 0;
+            child[w] = merge_word(wa[r], wb[r], w, split + off);
+          }
+        }
         __syncwarp();
         if (n >= E) {
-          uint8_t* cb = reinterpret_cast<uint8_t*>(child);
+          uint8_t* cx = reinterpret_cast<uint8_t*>(child);
           for (int l = lane; l < L; l += 32) {
             const int base = 2 * T_ + 2 + 3 * l;
-            if ((uint64_t)dr[base] < a.pm_thresh) swap2(cb + l * K, K, dr[base + 1], dr[base + 2]);
+            if ((uint64_t)dr[base] < a.pm_thresh && K >= 2) {
+              const int i1 = (int)below(dr[base + 1], (uint32_t)K);
+              const int jj = (int)below(dr[base + 2], (uint32_t)(K - 1));
+              const int i2 = jj + (jj >= i1 ? 1 : 0);
+              uint8_t* xr = cx + l * K;
+              uint8_t* ir = cx + XO + l * K;
+              const uint8_t p1 = xr[i1], p2 = xr[i2];
+              xr[i1] = p2;
+              xr[i2] = p1;
+              if (p1 < K) ir[p1] = (uint8_t)i2;
+              if (p2 < K) ir[p2] = (uint8_t)i1;
+            }
           }
         }
         __syncwarp();
@@ -300,29 +383,34 @@ __global__ void __launch_bounds__(kSolveThreads) k_solve(const SolveArgs a) {
       __syncthreads();
     }
     cur ^= 1;
-    __syncthreads();
   }
 
   // ---- outputs: final population and fitness, best member
   const FT* fit = FIT[a.G & 1];
-  for (int c = 0; c < nvalid; ++c) {
-    uint8_t* dst = a.pop_out + (int64_t)(base_n + c) * LK;
-    for (int r = tid; r < LK; r += blockDim.x) dst[r] = POP[cur][c * MS + r];
+  for (int i = tid; i < nvalid * LK; i += blockDim.x) {
+    const int c = i / LK, r = i - c * LK;
+    a.pop_out[(int64_t)base_n * LK + i] = POP[cur][c * MS + r];
   }
   FT* fo = static_cast<FT*>(a.fit_out);
   for (int c = tid; c < nvalid; c += blockDim.x) fo[base_n + c] = fit[base_n + c];
-  if (rank == 0 && a.best_row) {
-    const int b = block_best_s(fit, N, elites, 0, red);
-    const uint8_t* src = cluster.map_shared_rank(POP[cur], b / NT) + (b % NT) * MS;
-    for (int r = tid; r < LK; r += blockDim.x) a.best_row[r] = src[r];
-    if (tid == 0) *a.best_fit = (double)fit[b];
+  if (rank == 0 && a.best_row && warp == 0) {
+    int best = -1;
+    for (int i = lane; i < N; i += 32)
+      if (best < 0 || better_s(fit, i, best)) best = i;
+    for (int off = 16; off > 0; off >>= 1) {
+      const int o = __shfl_xor_sync(0xffffffffu, best, off);
+      if (o >= 0 && (best < 0 || better_s(fit, o, best))) best = o;
+    }
+    const uint8_t* src = cluster.map_shared_rank(POP[cur], best / NT) + (best % NT) * MS;
+    for (int r = lane; r < LK; r += 32) a.best_row[r] = src[r];
+    if (lane == 0) *a.best_fit = (double)fit[best];
   }
   cluster.sync();  // keep this CTA's shared memory alive for remote readers
 }
 
 // ------------------------------------------------------------------ launch
 struct SolveShape {
-  int C, NT, MS, NTT, nblk, CH;
+  int C, NT, MS, XO, NTT, nblk, CH;
   size_t smem;
 };
 
@@ -335,9 +423,16 @@ SolveShape solve_shape(const pa_ctx* ctx, int C) {
   s.C = C;
   s.NT = (c.N + C - 1) / C;
   s.CH = std::max(1, std::min(s.NT, 16384 / (s.nblk * 32)));
-  s.MS = ((LK + 15) / 16) * 16;
+  // record = X | INV, 4-byte aligned halves; an odd number of words per
+  // record keeps the per-member inverse reads of one warp in distinct banks
+  s.XO = ((LK + 3) / 4) * 4;
+  s.MS = 2 * s.XO;
+  if ((s.MS / 4) % 2 == 0) s.MS += 4;
+  const int JS = (!f64 && ctx->t32.vec == 2 && ctx->t32.NJ >= 8) ? 2 : 1;
   if (f64) {
     s.NTT = std::max(1, std::min(s.NT, 2048 / std::max(1, LK)));
+  } else if (JS == 2) {
+    s.NTT = std::max(1, std::min(s.NT, (kSolveThreads / 2) / c.K));
   } else {
     s.NTT = std::max(1, std::min(s.NT, kSolveThreads / c.K));
   }
@@ -348,9 +443,8 @@ SolveShape solve_shape(const pa_ctx* ctx, int C) {
   }
   const size_t fsz = f64 ? 8 : 4;
   b += 2 * fsz * (size_t)((c.N + 1) & ~1);
-  b += f64 ? 8 * (size_t)s.NTT * LK : 4 * (size_t)((s.NTT * c.K + 3) & ~3);
+  b += f64 ? 8 * (size_t)s.NTT * LK : 4 * (size_t)((s.NTT * c.K * JS + 3) & ~3);
   b += 2 * (size_t)s.NT * s.MS;
-  b += ((size_t)s.NTT * LK + 15) & ~size_t(15);
   b += (size_t)s.CH * s.nblk * 32;
   s.smem = (b + 15) & ~size_t(15);
   return s;
@@ -434,7 +528,7 @@ cudaError_t launch_solve(pa_ctx* ctx, const uint8_t* pop_in, uint8_t* pop_out, i
     if (ctx->solve_C > 0 && C != ctx->solve_C) continue;
     if (C > c.N) continue;
     const SolveShape s = solve_shape(ctx, C);
-    if (s.smem + (64 + 33) * 4 > (size_t)kSmemBudget) continue;
+    if (s.smem + 64 * 4 > (size_t)kSmemBudget) continue;
     SolveArgs a{};
     a.pop_in = pop_in;
     a.pop_out = pop_out;
@@ -453,6 +547,7 @@ cudaError_t launch_solve(pa_ctx* ctx, const uint8_t* pop_in, uint8_t* pop_out, i
     a.G = G;
     a.NT = s.NT;
     a.MS = s.MS;
+    a.XO = s.XO;
     a.NTT = s.NTT;
     a.nblk = s.nblk;
     a.CH = s.CH;
