@@ -147,13 +147,11 @@ F32Launch f32_shape(int L, int K, int RS, int NJ) {
   F32Launch s{};
   const int JS = (K <= 16 && NJ >= 8) ? 2 : 1;
   int NTK;
-  if (K <= 16) {
-    int base = 32;
-    while (base % K) base += 32;  // lcm(K, 32)
-    const int m = std::max(1, 256 / base);
-    NTK = base * m;
-    s.NT = NTK / K;
-    s.threads = NTK * JS;
+  if (JS == 2) {
+    // up to 128 (member, pilot) pairs; 16 pairs per warp (one per column share)
+    s.NT = std::max(1, 128 / K);
+    NTK = s.NT * K;
+    s.threads = 32 * ((NTK + 15) / 16);
   } else {
     s.NT = std::max(1, 256 / K);
     NTK = s.NT * K;
