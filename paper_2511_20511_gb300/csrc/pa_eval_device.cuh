@@ -136,6 +136,17 @@ __device__ __forceinline__ float eval_pilot_f32(const F32Smem& s, const uint8_t*
   return se;
 }
 
+// Fitness of one member from its n per-(pilot, share) partial SE sums, by
+// one warp: lane i takes partials i, i+32, ...; then a fixed xor-shuffle
+// tree.  The same tree in every kernel keeps their results identical.
+__device__ __forceinline__ float member_sum(const float* part, int n, int lane) {
+  float s = 0.f;
+  for (int i = lane; i < n; i += 32) s += part[i];
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+  return s;
+}
+
 // ----------------------------------------------------------------- FP64
 // log2 by the atanh series ln m = 2 sum_{n>=0} s^(2n+1)/(2n+1), s = (m-1)/(m+1)
 // (Abramowitz & Stegun 4.1.27) after x = m 2^e, m in [sqrt(1/2), sqrt(2));

@@ -88,10 +88,9 @@ __global__ void __launch_bounds__(512) k_eval_f32(const F32Args a) {
     __syncthreads();
     if (active) PART[q * JS + h] = eval_pilot_f32<NJ, VEC, FIN, JS>(sm, invp, NTK, h);
     __syncthreads();
-    if (tid < nvalid) {
-      float s = 0.f;
-      for (int i = 0; i < K * JS; ++i) s += PART[tid * K * JS + i];
-      a.fit[n0 + tid] = s;
+    for (int c = tid >> 5; c < nvalid; c += blockDim.x >> 5) {
+      const float f = member_sum(PART + c * K * JS, K * JS, lane);
+      if (lane == 0) a.fit[n0 + c] = f;
     }
   }
 }

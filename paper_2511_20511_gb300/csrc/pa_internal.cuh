@@ -168,11 +168,12 @@ struct DrawStream {
 
 // Draws of a GA generation for nc consecutive child slots n0 .. n0+nc-1:
 // DR[c*nblk*8 + d] = draw d of slot n0+c (the same values DrawStream gives),
-// one Philox block per thread.  Slots below E (elites) take no draws and
-// are skipped.
-__device__ __forceinline__ void gen_child_draws(uint32_t* DR, int n0, int nc, int nblk,
-                                                uint64_t seed, uint64_t gen, int E) {
-  for (int t = threadIdx.x; t < nc * nblk; t += blockDim.x) {
+// one Philox block per thread (threads t0, t0 + tstride, ...).  Slots below
+// E (elites) take no draws and are skipped.
+__device__ __forceinline__ void gen_child_draws_from(uint32_t* DR, int n0, int nc, int nblk,
+                                                     uint64_t seed, uint64_t gen, int E, int t0,
+                                                     int tstride) {
+  for (int t = t0; t < nc * nblk; t += tstride) {
     const int c = t / nblk, b = t - c * nblk;
     const int n = n0 + c;
     if (n < E) continue;
@@ -184,6 +185,11 @@ __device__ __forceinline__ void gen_child_draws(uint32_t* DR, int n0, int nc, in
       o[2 * w + 1] = (uint32_t)(r.v[w] >> 32);
     }
   }
+}
+
+__device__ __forceinline__ void gen_child_draws(uint32_t* DR, int n0, int nc, int nblk,
+                                                uint64_t seed, uint64_t gen, int E) {
+  gen_child_draws_from(DR, n0, nc, nblk, seed, gen, E, threadIdx.x, blockDim.x);
 }
 
 // Uniform integer in [0, n) from a 32-bit draw (multiply-shift).

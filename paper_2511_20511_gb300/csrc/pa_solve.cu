@@ -72,6 +72,38 @@ __device__ __forceinline__ bool better_s(const FT* fit, int a, int b) {
   return a < b;
 }
 
+// "member i with fitness v is better than member b with fitness bv": higher
+// fitness, or not lower (equal or unordered) and a lower index.
+template <typename FT>
+__device__ __forceinline__ bool better_v(FT v, int i, FT bv, int b) {
+  if (v > bv) return true;
+  if (v < bv) return false;
+  return i < b;
+}
+__device__ __forceinline__ float shfl_xor_ft(float v, int off) {
+  return __shfl_xor_sync(0xffffffffu, v, off);
+}
+__device__ __forceinline__ double shfl_xor_ft(double v, int off) {
+  return __shfl_xor_sync(0xffffffffu, v, off);
+}
+
+// Tournament over draws dr[0 .. T): candidates uniform with replacement,
+// the best by (fitness desc, index asc) wins.  Every lane computes it.
+template <typename FT>
+__device__ __forceinline__ int tournament_lane(const FT* fit, int N, int T, const uint32_t* dr) {
+  int best = (int)below(dr[0], (uint32_t)N);
+  FT bv = fit[best];
+  for (int t = 1; t < T; ++t) {
+    const int c = (int)below(dr[t], (uint32_t)N);
+    const FT cv = fit[c];
+    if (better_v(cv, c, bv, best)) {
+      best = c;
+      bv = cv;
+    }
+  }
+  return best;
+}
+
 // Block-wide best member by (fitness desc, index asc), skipping excluded[0..nex).
 template <typename FT>
 __device__ int block_best_s(const FT* fit, int N, const int* excluded, int nex, int* red) {
@@ -223,21 +255,30 @@ __global__ void __launch_bounds__(kSolveThreads) k_solve(const SolveArgs a) {
   for (int g = 0;; ++g) {
     FT* fit = FIT[g & 1];
     const unsigned char* popc = POP[cur];
-    // ---- 1. evaluate own members, broadcast their fitness
+    // ---- 1. evaluate own members, broadcast their fitness.  When all
+    //         children fit in one draw chunk, the warps the evaluation leaves
+    //         idle generate this generation's draws meanwhile (draws do not
+    //         depend on fitness).
+    const bool one_chunk = nvalid <= a.CH;
+    bool drawn = false;
     for (int c0 = 0; c0 < nvalid; c0 += a.NTT) {
       const int nv = min(a.NTT, nvalid - c0);
       if (!F64) {
+        const int eval_warps = JS == 2 ? (nv * K + 15) / 16 : (nv * K + 31) / 32;
         if (q < nv * K) {
           const int c = q / K, pp = q - c * K;
           PART[q * JS + h] =
               eval_pilot_f32<NJ, VEC, FIN, JS>(sm, popc + (c0 + c) * MS + XO + pp, K, h);
+        } else if (c0 == 0 && one_chunk && g < a.G && eval_warps < nwarps && warp >= eval_warps) {
+          gen_child_draws_from(DR, base_n, nvalid, nblk, a.seed, (uint64_t)(a.gen0 + g), E,
+                               tid - eval_warps * 32, blockDim.x - eval_warps * 32);
         }
+        if (c0 == 0 && one_chunk && eval_warps < nwarps) drawn = true;
         __syncthreads();
-        if (tid < nv) {
-          float s = 0.f;
-          for (int i = 0; i < K * JS; ++i) s += PART[tid * K * JS + i];
-          const int n = base_n + c0 + tid;
-          for (int r = 0; r < C; ++r) cluster.map_shared_rank(fit, r)[n] = (FT)s;
+        for (int c = warp; c < nv; c += nwarps) {
+          const float f = member_sum(PART + c * K * JS, K * JS, lane);
+          const int n = base_n + c0 + c;
+          if (lane < C) cluster.map_shared_rank(fit, lane)[n] = (FT)f;
         }
       } else {
         for (int i = tid; i < nv * LK; i += blockDim.x) {
@@ -259,77 +300,67 @@ __global__ void __launch_bounds__(kSolveThreads) k_solve(const SolveArgs a) {
     // ---- 2. all fitness values and members of generation g are visible
     cluster.sync();
     if (g == a.G) break;
-    // ---- 3. children of this CTA's slots
+    // ---- 3. children of this CTA's slots.  Elite slots (n < E) go to warp
+    //         0, which first finds the elites; the other slots are spread
+    //         over the remaining warps (all warps when this CTA has no
+    //         elite slot).
     unsigned char* popn = POP[cur ^ 1];
+    const int n_elite_here = max(0, min(E - base_n, nvalid));
     for (int c0 = 0; c0 < nvalid; c0 += a.CH) {
       const int nc = min(a.CH, nvalid - c0);
-      if (c0 == 0 && base_n < E) {
-        // warp 0: the E elites, one warp-wide argmax per elite, while the
-        // other warps generate the children's draws
-        if (warp == 0) {
-          for (int e = 0; e < E; ++e) {
-            int best = -1;
-            for (int i = lane; i < N; i += 32) {
-              bool taken = false;
-              for (int f = 0; f < e; ++f) taken |= (elites[f] == i);
-              if (!taken && (best < 0 || better_s(fit, i, best))) best = i;
-            }
-            for (int off = 16; off > 0; off >>= 1) {
-              const int o = __shfl_xor_sync(0xffffffffu, best, off);
-              if (o >= 0 && (best < 0 || better_s(fit, o, best))) best = o;
-            }
-            if (lane == 0) elites[e] = best;
-            __syncwarp();
-          }
-        } else {
-          for (int t = tid - 32; t < nc * nblk; t += blockDim.x - 32) {
-            const int c = t / nblk, b = t - c * nblk;
-            const int n = base_n + c0 + c;
-            if (n < E) continue;
-            const Philox4x64 r =
-                philox4x64_10((uint64_t)b, (uint64_t)n, (uint64_t)(a.gen0 + g), kTagGa, a.seed, 0);
-            uint32_t* o = DR + (size_t)c * nblk * 8 + b * 8;
-#pragma unroll
-            for (int w = 0; w < 4; ++w) {
-              o[2 * w] = (uint32_t)(r.v[w] & 0xFFFFFFFFu);
-              o[2 * w + 1] = (uint32_t)(r.v[w] >> 32);
-            }
-          }
-        }
-      } else {
+      if (!(drawn && c0 == 0)) {
         gen_child_draws(DR, base_n + c0, nc, nblk, a.seed, (uint64_t)(a.gen0 + g), E);
+        __syncthreads();
       }
-      __syncthreads();
-      for (int i = warp; i < nc; i += nwarps) {
-        const int n = base_n + c0 + i;
+      if (c0 == 0 && n_elite_here > 0 && warp == 0) {
+        for (int e = 0; e < E; ++e) {
+          int best = -1;
+          FT bv = (FT)0;
+          for (int i = lane; i < N; i += 32) {
+            bool taken = false;
+            for (int f = 0; f < e; ++f) taken |= (elites[f] == i);
+            if (taken) continue;
+            const FT v = fit[i];
+            if (best < 0 || better_v(v, i, bv, best)) {
+              best = i;
+              bv = v;
+            }
+          }
+          for (int off = 16; off > 0; off >>= 1) {
+            const int o = __shfl_xor_sync(0xffffffffu, best, off);
+            const FT ov = shfl_xor_ft(bv, off);
+            if (o >= 0 && (best < 0 || better_v(ov, o, bv, best))) {
+              best = o;
+              bv = ov;
+            }
+          }
+          if (lane == 0) elites[e] = best;
+          __syncwarp();
+        }
+      }
+      // slot order within the chunk: elite slots by warp 0, others round robin
+      const int first_w = (c0 == 0 && n_elite_here > 0) ? 1 : 0;
+      const int span = nwarps - first_w;
+      for (int i = 0; i < nc; ++i) {
+        const int slot = c0 + i;
+        const bool elite_slot = slot < n_elite_here;
+        int owner;
+        if (elite_slot) owner = 0;
+        else owner = first_w + (span > 0 ? (slot - (c0 == 0 ? n_elite_here : 0)) % span : 0);
+        if (span <= 0) owner = 0;
+        if (warp != owner) continue;
+        const int n = base_n + slot;
         const uint32_t* dr = DR + (size_t)i * nblk * 8;
-        uint32_t* child = reinterpret_cast<uint32_t*>(popn + (c0 + i) * MS);
+        uint32_t* child = reinterpret_cast<uint32_t*>(popn + slot * MS);
         int pa_, pb_;
         int64_t split;
         if (n < E) {
           pa_ = pb_ = elites[n];
           split = LK;
         } else {
-          int best = -1;
-          for (int t = lane; t < T_; t += 32) {
-            const int c = (int)below(dr[t], (uint32_t)N);
-            if (best < 0 || better_s(fit, c, best)) best = c;
-          }
-          for (int off = 16; off > 0; off >>= 1) {
-            const int o = __shfl_xor_sync(0xffffffffu, best, off);
-            if (o >= 0 && (best < 0 || better_s(fit, o, best))) best = o;
-          }
-          pa_ = best;
-          best = -1;
-          for (int t = lane; t < T_; t += 32) {
-            const int c = (int)below(dr[T_ + t], (uint32_t)N);
-            if (best < 0 || better_s(fit, c, best)) best = c;
-          }
-          for (int off = 16; off > 0; off >>= 1) {
-            const int o = __shfl_xor_sync(0xffffffffu, best, off);
-            if (o >= 0 && (best < 0 || better_s(fit, o, best))) best = o;
-          }
-          pb_ = best;
+          // every lane runs both tournaments itself: no cross-lane traffic
+          pa_ = tournament_lane(fit, N, T_, dr);
+          pb_ = tournament_lane(fit, N, T_, dr + T_);
           int cut = L;
           if ((uint64_t)dr[2 * T_] < a.pc_thresh) cut = 1 + (int)below(dr[2 * T_ + 1], (uint32_t)(L - 1));
           split = (int64_t)cut * K;
