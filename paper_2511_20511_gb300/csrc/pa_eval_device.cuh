@@ -66,22 +66,23 @@ struct F32Smem {
   float M, pc;
 };
 
-// Threads per (member, pilot) of the FP32 evaluation: two for float2 tables
-// with at least 8 BS columns (each takes half of the columns), else one.
+// Threads per (member, pilot) of the batch FP32 evaluation: two for float2
+// tables with at least 8 BS columns (each takes half of the columns), else one.
 template <int NJ, int VEC>
 struct PilotSplit {
   static constexpr int JS = (VEC == 2 && NJ >= 8) ? 2 : 1;
 };
 
-// Sum of SE over the BSs j of this thread's column share for the users
-// holding pilot p in one member, where invp[l*stride] is the user of cell l
-// holding p.  Accumulates the member's per-pilot interference for all BSs of
-// the share at once: for each cell l, the row of user inv_l(p) (its gains at
-// every BS) is added into the accumulators, squared for S2 and plain for S1
-// (FINITE_M).  Share h of JS covers column pairs [h*NJ/(2 JS), (h+1)*NJ/(2 JS)).
+// SE of the users holding pilot p in one member, for the BS column pairs
+// [h*NP, (h+1)*NP) with NP = NJ/(2 JS); invp[l*stride] is the user of cell l
+// holding p.  For each cell l the row of user inv_l(p) (its gains at every
+// BS) is added into the accumulators, squared for S2 and plain for S1
+// (FINITE_M).  pair_se[c] receives se(2c) + se(2c+1) for each pair c of the
+// share (zero for columns past L), so that the member's fitness can be
+// summed over (pilot, pair) in one fixed order whatever JS is.
 template <int NJ, int VEC, bool FIN, int JS>
-__device__ __forceinline__ float eval_pilot_f32(const F32Smem& s, const uint8_t* invp, int stride,
-                                                int h) {
+__device__ __forceinline__ void eval_pilot_f32(const F32Smem& s, const uint8_t* invp, int stride,
+                                               int h, float* pair_se) {
   static_assert(NJ % (2 * JS) == 0, "NJ must split into JS shares of column pairs");
   constexpr int NP = NJ / 2 / JS;
   unsigned long long acc2[NP];
@@ -94,9 +95,10 @@ __device__ __forceinline__ float eval_pilot_f32(const F32Smem& s, const uint8_t*
   const int L = s.L, K = s.K, RS = s.RS;
   const int c0 = h * NP;
   const float* Tl = s.T + 2 * c0;
-  for (int l = 0; l < L; ++l, Tl += K * RS) {
+#pragma unroll 2
+  for (int l = 0; l < L; ++l) {
     const int u = invp[l * stride];
-    const float* row = Tl + u * RS;
+    const float* row = Tl + (l * K + u) * RS;
 #pragma unroll
     for (int c = 0; c < NP; ++c) {
       unsigned long long v;
@@ -108,12 +110,12 @@ __device__ __forceinline__ float eval_pilot_f32(const F32Smem& s, const uint8_t*
       if (FIN) acc1[c] = fadd2(acc1[c], v);
     }
   }
-  float se = 0.f;
 #pragma unroll
   for (int c = 0; c < NP; ++c) {
     float s2[2], s1[2] = {0.f, 0.f};
     unpack2(acc2[c], s2[0], s2[1]);
     if (FIN) unpack2(acc1[c], s1[0], s1[1]);
+    float ps = 0.f;
 #pragma unroll
     for (int hh = 0; hh < 2; ++hh) {
       const int j = 2 * (c0 + c) + hh;
@@ -129,16 +131,16 @@ __device__ __forceinline__ float eval_pilot_f32(const F32Smem& s, const uint8_t*
           num = b2;
           den = s2[hh];
         }
-        se += __log2f(1.f + __fdividef(num, den));
+        ps += __log2f(1.f + __fdividef(num, den));
       }
     }
+    pair_se[c] = ps;
   }
-  return se;
 }
 
-// Fitness of one member from its n per-(pilot, share) partial SE sums, by
-// one warp: lane i takes partials i, i+32, ...; then a fixed xor-shuffle
-// tree.  The same tree in every kernel keeps their results identical.
+// Fitness of one member from its n per-(pilot, pair) SE sums, by one warp:
+// lane i adds entries i, i+32, ... in order, then a fixed xor-shuffle tree.
+// Every kernel sums the same entries this way, so their results agree.
 __device__ __forceinline__ float member_sum(const float* part, int n, int lane) {
   float s = 0.f;
   for (int i = lane; i < n; i += 32) s += part[i];

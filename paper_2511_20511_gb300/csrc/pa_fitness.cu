@@ -53,7 +53,7 @@ __global__ void __launch_bounds__(512) k_eval_f32(const F32Args a) {
   float* OWN = T + a.tab_floats;
   float* BN = OWN + ((a.L * a.K + 3) & ~3);
   float* PART = BN + ((a.L + 3) & ~3);
-  uint8_t* INV = reinterpret_cast<uint8_t*>(PART + ((2 * a.NTK + 3) & ~3));
+  uint8_t* INV = reinterpret_cast<uint8_t*>(PART + (((int64_t)a.NTK * (NJ / 2) + 3) & ~3));
   const int tid = threadIdx.x;
   const int L = a.L, K = a.K, NT = a.NT, NTK = a.NTK;
   const int64_t LK = (int64_t)L * K;
@@ -86,10 +86,10 @@ __global__ void __launch_bounds__(512) k_eval_f32(const F32Args a) {
     const int nvalid = (int)((a.n - n0) < NT ? (a.n - n0) : NT);
     decode_members(a.pop + n0 * LK, LK, nvalid, NT, L, K, INV);
     __syncthreads();
-    if (active) PART[q * JS + h] = eval_pilot_f32<NJ, VEC, FIN, JS>(sm, invp, NTK, h);
+    if (active) eval_pilot_f32<NJ, VEC, FIN, JS>(sm, invp, NTK, h, PART + q * (NJ / 2) + h * (NJ / 2 / JS));
     __syncthreads();
     for (int c = tid >> 5; c < nvalid; c += blockDim.x >> 5) {
-      const float f = member_sum(PART + c * K * JS, K * JS, lane);
+      const float f = member_sum(PART + c * K * (NJ / 2), K * (NJ / 2), lane);
       if (lane == 0) a.fit[n0 + c] = f;
     }
   }
@@ -158,7 +158,8 @@ F32Launch f32_shape(int L, int K, int RS, int NJ) {
   }
   const size_t LK = (size_t)L * K;
   const size_t tab = ((LK * RS + 3) / 4) * 4;
-  s.smem = 4 * (tab + ((LK + 3) & ~size_t(3)) + ((L + 3) & ~3) + ((2 * (size_t)NTK + 3) & ~size_t(3))) +
+  s.smem = 4 * (tab + ((LK + 3) & ~size_t(3)) + ((L + 3) & ~3) +
+                ((size_t)NTK * (NJ / 2) + 3) / 4 * 4) +
            (((size_t)L * NTK + 15) & ~size_t(15));
   return s;
 }

@@ -33,7 +33,7 @@ namespace cg = cooperative_groups;
 namespace pa {
 namespace {
 
-constexpr int kSolveThreads = 512;
+constexpr int kSolveThreads = 1024;
 
 struct SolveArgs {
   const uint8_t* pop_in;  // N*LK, starting population
@@ -91,15 +91,22 @@ __device__ __forceinline__ double shfl_xor_ft(double v, int off) {
 // the best by (fitness desc, index asc) wins.  Every lane computes it.
 template <typename FT>
 __device__ __forceinline__ int tournament_lane(const FT* fit, int N, int T, const uint32_t* dr) {
-  int best = (int)below(dr[0], (uint32_t)N);
-  FT bv = fit[best];
-  for (int t = 1; t < T; ++t) {
-    const int c = (int)below(dr[t], (uint32_t)N);
-    const FT cv = fit[c];
-    if (better_v(cv, c, bv, best)) {
-      best = c;
-      bv = cv;
-    }
+  constexpr int kU = 4;  // candidates fetched together
+  int best = -1;
+  FT bv = (FT)0;
+  for (int t0 = 0; t0 < T; t0 += kU) {
+    int c[kU];
+    FT v[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) c[u] = t0 + u < T ? (int)below(dr[t0 + u], (uint32_t)N) : -1;
+#pragma unroll
+    for (int u = 0; u < kU; ++u) v[u] = c[u] >= 0 ? fit[c[u]] : (FT)0;
+#pragma unroll
+    for (int u = 0; u < kU; ++u)
+      if (c[u] >= 0 && (best < 0 || better_v(v[u], c[u], bv, best))) {
+        best = c[u];
+        bv = v[u];
+      }
   }
   return best;
 }
@@ -169,6 +176,13 @@ __device__ __forceinline__ uint32_t dsmem_addr(const void* local, int rank) {
   return r;
 }
 
+// Column-pair share of the fused evaluation: each thread takes two BS column
+// pairs of one (member, pilot), so the per-thread dependency chain is short.
+template <int NJ>
+struct FusedSplit {
+  static constexpr int JS = NJ >= 8 ? NJ / 4 : 1;
+};
+
 // Member record in shared memory (MS bytes): the chromosome X (L*K bytes,
 // pilot of each user) at offset 0 and its inverse INV (L*K bytes, user of
 // each pilot, row by row) at offset XO.  Crossover takes whole rows, so the
@@ -184,7 +198,8 @@ __global__ void __launch_bounds__(kSolveThreads) k_solve(const SolveArgs a) {
   const int L = a.L, K = a.K, N = a.N, NT = a.NT, MS = a.MS, XO = a.XO;
   const int LK = L * K;
   constexpr bool F64 = sizeof(FT) == 8;
-  constexpr int JS = F64 ? 1 : PilotSplit<NJ, VEC>::JS;
+  constexpr int JS = F64 ? 1 : FusedSplit<NJ>::JS;
+  constexpr int NPR = NJ / 2;  // column pairs per (member, pilot)
 
   // ---- carve shared memory
   unsigned char* p = smem;
@@ -199,20 +214,24 @@ __global__ void __launch_bounds__(kSolveThreads) k_solve(const SolveArgs a) {
     BN = reinterpret_cast<float*>(p);
     p += 4 * ((L + 3) & ~3);
   }
-  FT* FIT[2];
-  FIT[0] = reinterpret_cast<FT*>(p);
+  // double buffers are addressed as offsets from the shared-memory base
+  const int fit_off0 = (int)(p - smem);
   p += sizeof(FT) * ((N + 1) & ~1);
-  FIT[1] = reinterpret_cast<FT*>(p);
+  const int fit_off1 = (int)(p - smem);
   p += sizeof(FT) * ((N + 1) & ~1);
+  auto FITp = [&](int b) { return reinterpret_cast<FT*>(smem + (b ? fit_off1 : fit_off0)); };
   double* SE = reinterpret_cast<double*>(p);  // FP64: NTT*LK per-user SE
-  float* PART = reinterpret_cast<float*>(p);  // FP32: NTT*K*JS per-share sums
-  p += F64 ? 8 * (size_t)a.NTT * LK : 4 * (size_t)((a.NTT * K * JS + 3) & ~3);
-  unsigned char* POP[2];
-  POP[0] = p;
+  float* PART = reinterpret_cast<float*>(p);  // FP32: NTT*K*NPR per-(pilot, pair) SE
+  p += F64 ? 8 * (size_t)a.NTT * LK : 4 * (size_t)((a.NTT * K * NPR + 3) & ~3);
+  const int pop_off0 = (int)(p - smem);
   p += (size_t)NT * MS;
-  POP[1] = p;
+  const int pop_off1 = (int)(p - smem);
   p += (size_t)NT * MS;
+  auto POPp = [&](int b) { return smem + (b ? pop_off1 : pop_off0); };
   uint32_t* DR = reinterpret_cast<uint32_t*>(p);  // [CH][nblk*8] draws of staged children
+  p += (size_t)a.CH * a.nblk * 32;
+  FT* CV = reinterpret_cast<FT*>(p);  // [32][E] elite candidates (value)
+  int* CI = reinterpret_cast<int*>(p + sizeof(FT) * 32 * 64);  // [32][E] (index)
 
   const int base_n = rank * NT;
   const int nvalid = max(0, min(NT, N - base_n));
@@ -226,17 +245,17 @@ __global__ void __launch_bounds__(kSolveThreads) k_solve(const SolveArgs a) {
     if (FIN)
       for (int i = tid; i < L; i += blockDim.x) BN[i] = __ldg(a.bn + i);
   }
-  for (int i = tid; i < NT * MS; i += blockDim.x) POP[0][i] = 0;
+  for (int i = tid; i < NT * MS; i += blockDim.x) POPp(0)[i] = 0;
   __syncthreads();
   for (int i = tid; i < nvalid * LK; i += blockDim.x) {
     const int c = i / LK, r = i - c * LK;
-    POP[0][c * MS + r] = a.pop_in[(int64_t)base_n * LK + i];
+    POPp(0)[c * MS + r] = a.pop_in[(int64_t)base_n * LK + i];
   }
   __syncthreads();
   for (int i = tid; i < nvalid * L; i += blockDim.x) {
     const int c = i / L, l = i - c * L;
-    const uint8_t* x = POP[0] + c * MS + l * K;
-    uint8_t* inv = POP[0] + c * MS + XO + l * K;
+    const uint8_t* x = POPp(0) + c * MS + l * K;
+    uint8_t* inv = POPp(0) + c * MS + XO + l * K;
     for (int k = 0; k < K; ++k) {
       const int q = x[k];
       if (q < K) inv[q] = (uint8_t)k;
@@ -249,34 +268,36 @@ __global__ void __launch_bounds__(kSolveThreads) k_solve(const SolveArgs a) {
   const int lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
   const int T_ = a.tour, nblk = a.nblk, E = a.E;
   const int nwords = MS >> 2;
-  // FP32 evaluation thread roles: q = member*K + pilot, column share h
-  const int h = JS == 2 ? (lane >> 4) : 0;
-  const int q = JS == 2 ? (warp << 4) + (lane & 15) : tid;
+  // FP32 evaluation roles: q = member*K + pilot, column-pair share h
+  const int q = tid / JS, h = tid - (tid / JS) * JS;
+  const bool one_chunk = nvalid <= a.CH;
+  const int n_elite_here = max(0, min(E - base_n, nvalid));
   for (int g = 0;; ++g) {
-    FT* fit = FIT[g & 1];
-    const unsigned char* popc = POP[cur];
+    FT* fit = FITp(g & 1);
+    const unsigned char* popc = POPp(cur);
     // ---- 1. evaluate own members, broadcast their fitness.  When all
-    //         children fit in one draw chunk, the warps the evaluation leaves
-    //         idle generate this generation's draws meanwhile (draws do not
-    //         depend on fitness).
-    const bool one_chunk = nvalid <= a.CH;
+    //         children fit in one draw chunk, the threads the evaluation
+    //         leaves idle generate this generation's draws meanwhile (draws
+    //         do not depend on fitness).
     bool drawn = false;
     for (int c0 = 0; c0 < nvalid; c0 += a.NTT) {
       const int nv = min(a.NTT, nvalid - c0);
       if (!F64) {
-        const int eval_warps = JS == 2 ? (nv * K + 15) / 16 : (nv * K + 31) / 32;
+        const int eval_threads = nv * K * JS;
         if (q < nv * K) {
           const int c = q / K, pp = q - c * K;
-          PART[q * JS + h] =
-              eval_pilot_f32<NJ, VEC, FIN, JS>(sm, popc + (c0 + c) * MS + XO + pp, K, h);
-        } else if (c0 == 0 && one_chunk && g < a.G && eval_warps < nwarps && warp >= eval_warps) {
+          eval_pilot_f32<NJ, VEC, FIN, JS>(sm, popc + (c0 + c) * MS + XO + pp, K, h,
+                                           PART + q * NPR + h * (NPR / JS));
+        } else if (c0 == 0 && one_chunk && g < a.G && eval_threads + 32 <= (int)blockDim.x &&
+                   tid >= ((eval_threads + 31) & ~31)) {
+          const int t0 = (eval_threads + 31) & ~31;
           gen_child_draws_from(DR, base_n, nvalid, nblk, a.seed, (uint64_t)(a.gen0 + g), E,
-                               tid - eval_warps * 32, blockDim.x - eval_warps * 32);
+                               tid - t0, blockDim.x - t0);
         }
-        if (c0 == 0 && one_chunk && eval_warps < nwarps) drawn = true;
+        if (c0 == 0 && one_chunk && eval_threads + 32 <= (int)blockDim.x) drawn = true;
         __syncthreads();
         for (int c = warp; c < nv; c += nwarps) {
-          const float f = member_sum(PART + c * K * JS, K * JS, lane);
+          const float f = member_sum(PART + c * K * NPR, K * NPR, lane);
           const int n = base_n + c0 + c;
           if (lane < C) cluster.map_shared_rank(fit, lane)[n] = (FT)f;
         }
@@ -300,55 +321,83 @@ __global__ void __launch_bounds__(kSolveThreads) k_solve(const SolveArgs a) {
     // ---- 2. all fitness values and members of generation g are visible
     cluster.sync();
     if (g == a.G) break;
-    // ---- 3. children of this CTA's slots.  Elite slots (n < E) go to warp
-    //         0, which first finds the elites; the other slots are spread
-    //         over the remaining warps (all warps when this CTA has no
-    //         elite slot).
-    unsigned char* popn = POP[cur ^ 1];
-    const int n_elite_here = max(0, min(E - base_n, nvalid));
+    // ---- 3. elites (CTA holding slots below E): every warp finds the top E
+    //         of its stripe of the population, warp 0 merges the candidates
+    if (n_elite_here > 0) {
+      const int stripe = (N + nwarps - 1) / nwarps;
+      const int lo = warp * stripe, hi = min(N, lo + stripe);
+      for (int e = 0; e < E; ++e) {
+        int best = -1;
+        FT bv = (FT)0;
+        for (int i = lo + lane; i < hi; i += 32) {
+          bool taken = false;
+          for (int f = 0; f < e; ++f) taken |= (CI[warp * E + f] == i);
+          if (taken) continue;
+          const FT v = fit[i];
+          if (best < 0 || better_v(v, i, bv, best)) {
+            best = i;
+            bv = v;
+          }
+        }
+        for (int off = 16; off > 0; off >>= 1) {
+          const int o = __shfl_xor_sync(0xffffffffu, best, off);
+          const FT ov = shfl_xor_ft(bv, off);
+          if (o >= 0 && (best < 0 || better_v(ov, o, bv, best))) {
+            best = o;
+            bv = ov;
+          }
+        }
+        if (lane == 0) {
+          CI[warp * E + e] = best;
+          CV[warp * E + e] = bv;
+        }
+        __syncwarp();
+      }
+      __syncthreads();
+      if (warp == 0) {
+        const int ncand = nwarps * E;
+        for (int e = 0; e < E; ++e) {
+          int best = -1, slot = -1;
+          FT bv = (FT)0;
+          for (int i = lane; i < ncand; i += 32) {
+            const int ci = CI[i];
+            if (ci < 0) continue;
+            const FT v = CV[i];
+            if (best < 0 || better_v(v, ci, bv, best)) {
+              best = ci;
+              bv = v;
+              slot = i;
+            }
+          }
+          for (int off = 16; off > 0; off >>= 1) {
+            const int o = __shfl_xor_sync(0xffffffffu, best, off);
+            const FT ov = shfl_xor_ft(bv, off);
+            const int os = __shfl_xor_sync(0xffffffffu, slot, off);
+            if (o >= 0 && (best < 0 || better_v(ov, o, bv, best))) {
+              best = o;
+              bv = ov;
+              slot = os;
+            }
+          }
+          if (lane == 0) {
+            elites[e] = best;
+            CI[slot] = -1;  // consumed
+          }
+          __syncwarp();
+        }
+      }
+      __syncthreads();
+    }
+    // ---- 4. children of this CTA's slots: warp w builds slots w, w+nwarps, ...
+    unsigned char* popn = POPp(cur ^ 1);
     for (int c0 = 0; c0 < nvalid; c0 += a.CH) {
       const int nc = min(a.CH, nvalid - c0);
       if (!(drawn && c0 == 0)) {
         gen_child_draws(DR, base_n + c0, nc, nblk, a.seed, (uint64_t)(a.gen0 + g), E);
         __syncthreads();
       }
-      if (c0 == 0 && n_elite_here > 0 && warp == 0) {
-        for (int e = 0; e < E; ++e) {
-          int best = -1;
-          FT bv = (FT)0;
-          for (int i = lane; i < N; i += 32) {
-            bool taken = false;
-            for (int f = 0; f < e; ++f) taken |= (elites[f] == i);
-            if (taken) continue;
-            const FT v = fit[i];
-            if (best < 0 || better_v(v, i, bv, best)) {
-              best = i;
-              bv = v;
-            }
-          }
-          for (int off = 16; off > 0; off >>= 1) {
-            const int o = __shfl_xor_sync(0xffffffffu, best, off);
-            const FT ov = shfl_xor_ft(bv, off);
-            if (o >= 0 && (best < 0 || better_v(ov, o, bv, best))) {
-              best = o;
-              bv = ov;
-            }
-          }
-          if (lane == 0) elites[e] = best;
-          __syncwarp();
-        }
-      }
-      // slot order within the chunk: elite slots by warp 0, others round robin
-      const int first_w = (c0 == 0 && n_elite_here > 0) ? 1 : 0;
-      const int span = nwarps - first_w;
-      for (int i = 0; i < nc; ++i) {
+      for (int i = warp; i < nc; i += nwarps) {
         const int slot = c0 + i;
-        const bool elite_slot = slot < n_elite_here;
-        int owner;
-        if (elite_slot) owner = 0;
-        else owner = first_w + (span > 0 ? (slot - (c0 == 0 ? n_elite_here : 0)) % span : 0);
-        if (span <= 0) owner = 0;
-        if (warp != owner) continue;
         const int n = base_n + slot;
         const uint32_t* dr = DR + (size_t)i * nblk * 8;
         uint32_t* child = reinterpret_cast<uint32_t*>(popn + slot * MS);
@@ -358,7 +407,6 @@ __global__ void __launch_bounds__(kSolveThreads) k_solve(const SolveArgs a) {
           pa_ = pb_ = elites[n];
           split = LK;
         } else {
-          // every lane runs both tournaments itself: no cross-lane traffic
           pa_ = tournament_lane(fit, N, T_, dr);
           pb_ = tournament_lane(fit, N, T_, dr + T_);
           int cut = L;
@@ -366,8 +414,8 @@ __global__ void __launch_bounds__(kSolveThreads) k_solve(const SolveArgs a) {
           split = (int64_t)cut * K;
         }
         // parents' records from their owners: all remote loads issued first
-        const uint32_t ra = dsmem_addr(POP[cur] + (pa_ % NT) * MS, pa_ / NT);
-        const uint32_t rb = dsmem_addr(POP[cur] + (pb_ % NT) * MS, pb_ / NT);
+        const uint32_t ra = dsmem_addr(POPp(cur) + (pa_ % NT) * MS, pa_ / NT);
+        const uint32_t rb = dsmem_addr(POPp(cur) + (pb_ % NT) * MS, pb_ / NT);
         constexpr int kMaxW = 4;  // words per lane held at once (records <= 512 bytes)
         uint32_t wa[kMaxW], wb[kMaxW];
 #pragma unroll
@@ -417,22 +465,32 @@ __global__ void __launch_bounds__(kSolveThreads) k_solve(const SolveArgs a) {
   }
 
   // ---- outputs: final population and fitness, best member
-  const FT* fit = FIT[a.G & 1];
+  const FT* fit = FITp(a.G & 1);
   for (int i = tid; i < nvalid * LK; i += blockDim.x) {
     const int c = i / LK, r = i - c * LK;
-    a.pop_out[(int64_t)base_n * LK + i] = POP[cur][c * MS + r];
+    a.pop_out[(int64_t)base_n * LK + i] = POPp(cur)[c * MS + r];
   }
   FT* fo = static_cast<FT*>(a.fit_out);
   for (int c = tid; c < nvalid; c += blockDim.x) fo[base_n + c] = fit[base_n + c];
   if (rank == 0 && a.best_row && warp == 0) {
     int best = -1;
-    for (int i = lane; i < N; i += 32)
-      if (best < 0 || better_s(fit, i, best)) best = i;
+    FT bv = (FT)0;
+    for (int i = lane; i < N; i += 32) {
+      const FT v = fit[i];
+      if (best < 0 || better_v(v, i, bv, best)) {
+        best = i;
+        bv = v;
+      }
+    }
     for (int off = 16; off > 0; off >>= 1) {
       const int o = __shfl_xor_sync(0xffffffffu, best, off);
-      if (o >= 0 && (best < 0 || better_s(fit, o, best))) best = o;
+      const FT ov = shfl_xor_ft(bv, off);
+      if (o >= 0 && (best < 0 || better_v(ov, o, bv, best))) {
+        best = o;
+        bv = ov;
+      }
     }
-    const uint8_t* src = cluster.map_shared_rank(POP[cur], best / NT) + (best % NT) * MS;
+    const uint8_t* src = cluster.map_shared_rank(POPp(cur), best / NT) + (best % NT) * MS;
     for (int r = lane; r < LK; r += 32) a.best_row[r] = src[r];
     if (lane == 0) *a.best_fit = (double)fit[best];
   }
@@ -459,13 +517,13 @@ SolveShape solve_shape(const pa_ctx* ctx, int C) {
   s.XO = ((LK + 3) / 4) * 4;
   s.MS = 2 * s.XO;
   if ((s.MS / 4) % 2 == 0) s.MS += 4;
-  const int JS = (!f64 && ctx->t32.vec == 2 && ctx->t32.NJ >= 8) ? 2 : 1;
+  const int NJ = ctx->t32.NJ;
+  const int JS = (!f64 && NJ >= 8) ? NJ / 4 : 1;
+  const int NPR = f64 ? 0 : NJ / 2;
   if (f64) {
     s.NTT = std::max(1, std::min(s.NT, 2048 / std::max(1, LK)));
-  } else if (JS == 2) {
-    s.NTT = std::max(1, std::min(s.NT, (kSolveThreads / 2) / c.K));
   } else {
-    s.NTT = std::max(1, std::min(s.NT, kSolveThreads / c.K));
+    s.NTT = std::max(1, std::min(s.NT, kSolveThreads / (c.K * JS)));
   }
   size_t b = 0;
   if (!f64) {
@@ -474,9 +532,10 @@ SolveShape solve_shape(const pa_ctx* ctx, int C) {
   }
   const size_t fsz = f64 ? 8 : 4;
   b += 2 * fsz * (size_t)((c.N + 1) & ~1);
-  b += f64 ? 8 * (size_t)s.NTT * LK : 4 * (size_t)((s.NTT * c.K * JS + 3) & ~3);
+  b += f64 ? 8 * (size_t)s.NTT * LK : 4 * (size_t)((s.NTT * c.K * NPR + 3) & ~3);
   b += 2 * (size_t)s.NT * s.MS;
   b += (size_t)s.CH * s.nblk * 32;
+  b += (f64 ? 8 : 4) * 32 * 64 + 4 * 32 * 64;  // elite candidates
   s.smem = (b + 15) & ~size_t(15);
   return s;
 }
