@@ -34,6 +34,7 @@ namespace pa {
 namespace {
 
 constexpr int kSolveThreads = 1024;
+constexpr int kSmallE = 8;  // elites found by one warp in registers up to this E
 
 struct SolveArgs {
   const uint8_t* pop_in;  // N*LK, starting population
@@ -85,6 +86,82 @@ __device__ __forceinline__ float shfl_xor_ft(float v, int off) {
 }
 __device__ __forceinline__ double shfl_xor_ft(double v, int off) {
   return __shfl_xor_sync(0xffffffffu, v, off);
+}
+
+// The E best members (fitness desc, index asc) of fit[0..N), E <= EMAX, by
+// one warp: each lane keeps a sorted list of its best E among members
+// lane, lane+32, ...; five xor-shuffle levels merge the lists.  Every lane
+// ends with the same list; lane 0 writes it to out[0..E).
+template <typename FT, int EMAX>
+__device__ __forceinline__ void warp_top_e(const FT* fit, int N, int E, int lane, int* out) {
+  int bi[EMAX];
+  FT bv[EMAX];
+#pragma unroll
+  for (int e = 0; e < EMAX; ++e) {
+    bi[e] = -1;
+    bv[e] = (FT)0;
+  }
+  for (int i = lane; i < N; i += 32) {
+    const FT v = fit[i];
+    // insert (v, i) into the sorted list (entries past E stay empty)
+    int ci = i;
+    FT cv = v;
+#pragma unroll
+    for (int e = 0; e < EMAX; ++e) {
+      if (e < E && ci >= 0 && (bi[e] < 0 || better_v(cv, ci, bv[e], bi[e]))) {
+        const int ti = bi[e];
+        const FT tv = bv[e];
+        bi[e] = ci;
+        bv[e] = cv;
+        ci = ti;
+        cv = tv;
+      }
+    }
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    int oi[EMAX];
+    FT ov[EMAX];
+#pragma unroll
+    for (int e = 0; e < EMAX; ++e) {
+      oi[e] = __shfl_xor_sync(0xffffffffu, bi[e], off);
+      ov[e] = shfl_xor_ft(bv[e], off);
+    }
+    // merge two sorted lists, keep the first E
+    int mi[EMAX];
+    FT mv[EMAX];
+    int x = 0, y = 0;
+#pragma unroll
+    for (int e = 0; e < EMAX; ++e) {
+      int ai = -1, bi2 = -1;
+      FT av = (FT)0, bv2 = (FT)0;
+#pragma unroll
+      for (int k = 0; k < EMAX; ++k) {
+        if (k == x) {
+          ai = bi[k];
+          av = bv[k];
+        }
+        if (k == y) {
+          bi2 = oi[k];
+          bv2 = ov[k];
+        }
+      }
+      const bool take_a = ai >= 0 && (bi2 < 0 || better_v(av, ai, bv2, bi2));
+      mi[e] = take_a ? ai : bi2;
+      mv[e] = take_a ? av : bv2;
+      x += take_a ? 1 : 0;
+      y += take_a ? 0 : 1;
+    }
+#pragma unroll
+    for (int e = 0; e < EMAX; ++e) {
+      bi[e] = e < E ? mi[e] : -1;
+      bv[e] = mv[e];
+    }
+  }
+  if (lane == 0)
+#pragma unroll
+    for (int e = 0; e < EMAX; ++e)
+      if (e < E) out[e] = bi[e];
 }
 
 // Tournament over draws dr[0 .. T): candidates uniform with replacement,
@@ -321,9 +398,12 @@ __global__ void __launch_bounds__(kSolveThreads) k_solve(const SolveArgs a) {
     // ---- 2. all fitness values and members of generation g are visible
     cluster.sync();
     if (g == a.G) break;
-    // ---- 3. elites (CTA holding slots below E): every warp finds the top E
-    //         of its stripe of the population, warp 0 merges the candidates
-    if (n_elite_here > 0) {
+    // ---- 3. elites (CTA holding slots below E).  For E <= 8 warp 0 alone
+    //         finds them (register lists) and then fills the elite slots while
+    //         the other warps build the other children; for larger E every
+    //         warp takes a stripe of the population and warp 0 merges.
+    const bool small_e = E <= kSmallE;
+    if (n_elite_here > 0 && !small_e) {
       const int stripe = (N + nwarps - 1) / nwarps;
       const int lo = warp * stripe, hi = min(N, lo + stripe);
       for (int e = 0; e < E; ++e) {
@@ -388,6 +468,15 @@ __global__ void __launch_bounds__(kSolveThreads) k_solve(const SolveArgs a) {
       }
       __syncthreads();
     }
+    if (n_elite_here > 0 && small_e && warp == 0) {
+      if (E <= 2)
+        warp_top_e<FT, 2>(fit, N, E, lane, elites);
+      else if (E <= 4)
+        warp_top_e<FT, 4>(fit, N, E, lane, elites);
+      else
+        warp_top_e<FT, kSmallE>(fit, N, E, lane, elites);
+      __syncwarp();
+    }
     // ---- 4. children of this CTA's slots: warp w builds slots w, w+nwarps, ...
     unsigned char* popn = POPp(cur ^ 1);
     for (int c0 = 0; c0 < nvalid; c0 += a.CH) {
@@ -396,7 +485,21 @@ __global__ void __launch_bounds__(kSolveThreads) k_solve(const SolveArgs a) {
         gen_child_draws(DR, base_n + c0, nc, nblk, a.seed, (uint64_t)(a.gen0 + g), E);
         __syncthreads();
       }
-      for (int i = warp; i < nc; i += nwarps) {
+      // elite slots of a small E are warp 0's (it found the elites); other
+      // slots go round robin to the remaining warps
+      const int ne = (small_e && c0 == 0) ? min(n_elite_here, nc) : 0;
+      const int w_first = ne > 0 ? 1 : 0;
+      const int w_span = nwarps - w_first;
+      int i_begin, i_step;
+      if (ne > 0 && warp == 0) {
+        i_begin = 0;
+        i_step = 1;
+      } else {
+        i_begin = ne + (warp - w_first);
+        i_step = w_span;
+      }
+      const int i_end = (ne > 0 && warp == 0) ? ne : nc;
+      for (int i = i_begin; i < i_end; i += i_step) {
         const int slot = c0 + i;
         const int n = base_n + slot;
         const uint32_t* dr = DR + (size_t)i * nblk * 8;
