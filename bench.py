@@ -340,6 +340,8 @@ def run_ours(args):
         "gpu_launches": launches,
         "clocks": clk,
     }
+    if not args.no_batched:
+        line["batched_c3"] = run_batched(B, inputs)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
     ctx.close()
@@ -348,6 +350,66 @@ def run_ours(args):
     if world > 1:
         torch.distributed.destroy_process_group()
     return 0
+
+
+def c3_instances(B, inputs, n=512, seed0=0):
+    """Batched uneven instances: L from {7, 19, 37}, K uniform in [4, 16],
+    tau_p = K, M = 256 (finite-M SINR), N = 128, FP32 beta, seeds 0..n-1."""
+    import numpy as np
+
+    rng = np.random.default_rng(seed0)
+    out = []
+    for i in range(n):
+        L = int(rng.choice([7, 19, 37]))
+        K = int(rng.integers(4, 17))
+        inst = inputs.instance(L, K, seed=seed0 + i, dtype=np.float32)
+        cfg = B.pa_config_default(L, K, mode=B.PA_SINR_FINITE_M, M=256.0, tau_p=K, N=128,
+                                  rho=inst["rho"], seed=seed0 + i)
+        out.append(dict(cfg=cfg, beta=inst["beta"], user_xy_mm=inst["user_xy_mm"],
+                        bs_xy_mm=inst["bs_xy_mm"]))
+    return out
+
+
+def run_batched(B, inputs, G=100, n=512, reps=3):
+    """512 uneven instances: one batched solve (persistent cluster launches
+    per kernel variant, CUDA graph, tuned cluster sizes) against the same
+    instances solved one launch sequence per instance."""
+    import torch
+
+    insts = c3_instances(B, inputs, n)
+    batch = B.Batch(insts)
+    chosen = batch.tune(10)
+    batch.solve(G)  # capture + warm
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        batch.solve(G)
+    t_batch = (time.perf_counter() - t0) / reps
+    rows, fits = batch.solve(G)
+    batch.close()
+    ctxs = [B.Context(d["cfg"], d["beta"], d["user_xy_mm"], d["bs_xy_mm"]) for d in insts]
+    ctxs[0].solve(G)
+    lat = []
+    t0 = time.perf_counter()
+    same = True
+    for i, c in enumerate(ctxs):
+        t1 = time.perf_counter()
+        best, bf = c.solve(G)
+        lat.append(time.perf_counter() - t1)
+        same &= bool((best == rows[i]).all()) and bf == fits[i]
+    t_seq = time.perf_counter() - t0
+    for c in ctxs:
+        c.close()
+    lat.sort()
+    evals = sum(d["cfg"].N for d in insts) * (G + 1)
+    return {"instances": n, "generations": G, "population": 128,
+            "batched": {"seconds_per_batch": t_batch, "solves_per_s": n / t_batch,
+                        "evals_per_s": evals / t_batch, "cluster_sizes": [int(x) for x in chosen]},
+            "one_launch_sequence_per_instance": {
+                "seconds": t_seq, "solves_per_s": n / t_seq, "evals_per_s": evals / t_seq,
+                "p50_ms": 1e3 * lat[len(lat) // 2], "p99_ms": 1e3 * lat[int(0.99 * (len(lat) - 1))]},
+            "speedup": t_seq / t_batch, "identical_results": same,
+            "timing": "host wall clock around synchronous calls (batched: graph replay)"}
 
 
 def run_eval_only(args, B, inputs, ctx, stream, dev, rank):
@@ -375,6 +437,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-batched", action="store_true",
+                    help="skip the 512-instance batched-solve comparison")
     ap.add_argument("--only", choices=["all", "eval", "solve"], default="all",
                     help="eval / solve: run only the 2^20-chromosome evaluation or only the "
                          "solves, untimed (for profilers)")

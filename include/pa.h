@@ -204,6 +204,62 @@ pa_status pa_population_device(pa_ctx* ctx, uint8_t** pop_dev, void** fit_dev);
 pa_status pa_validate_population(pa_ctx* ctx, const uint8_t* pop_dev, int64_t n,
                                  int64_t* first_bad);
 
+/* ------------------------------------------------------------------------
+ * Batches: many independent instances, possibly of different L, K and N,
+ * solved together.  Instances sharing a kernel variant (precision, SINR mode,
+ * L rounded up to a multiple of 4, K <= 16 or not) run as one persistent
+ * launch in which thread-block clusters take instances from a queue; the
+ * seeding of all instances is one launch; the whole batch solve is captured
+ * once per generation count into a CUDA graph and replayed.  Each instance
+ * gives exactly the result pa_solve gives for it alone.
+ * ------------------------------------------------------------------------ */
+typedef struct pa_batch pa_batch;
+
+/*
+ * Create a batch of n instances: cfgs[i], betas[i] (host, L_i*L_i*K_i
+ * float64) and optional positions user_xy_mm[i] / bs_xy_mm[i] as for
+ * pa_create (the arrays of positions may be NULL for all instances).  Work
+ * goes to `stream`.  Synchronous.  On failure pa_last_error(NULL) explains.
+ */
+pa_status pa_batch_create(int32_t n, const pa_config* cfgs, const double* const* betas,
+                          const int32_t* const* user_xy_mm, const int32_t* const* bs_xy_mm,
+                          void* stream, pa_batch** out);
+
+/* Destroy a batch and all its device memory (NULL is ignored). */
+void pa_batch_destroy(pa_batch* b);
+
+/* Replace instance i's gains and positions (same shapes; positions exactly
+ * when the instance was created with them).  Asynchronous. */
+pa_status pa_batch_load(pa_batch* b, int32_t i, const double* beta, const int32_t* user_xy_mm,
+                        const int32_t* bs_xy_mm);
+
+/*
+ * Autotune: for each kernel-variant group, time the group's solve with
+ * clusters of 1, 2, 4, 8 and 16 CTAs per instance (as far as they fit) for
+ * `generations` generations on the batch itself and keep the fastest.
+ * chosen (optional, one entry per group) receives the chosen sizes.  Runs
+ * real solves (results are discarded).  Synchronous.
+ */
+pa_status pa_batch_tune(pa_batch* b, int32_t generations, int32_t* chosen);
+
+/* Number of kernel-variant groups, their cluster sizes, and the group of
+ * each instance (each output optional). */
+pa_status pa_batch_groups(pa_batch* b, int32_t* n_groups, int32_t* cluster_sizes,
+                          int32_t* group_of_instance);
+
+/*
+ * Solve every instance (Alg. 1 as in pa_solve): best_host receives the best
+ * members back to back (instance i at offset sum_{m<i} L_m*K_m bytes),
+ * best_fit their fitness (n values).  Either may be NULL.  Synchronous.
+ */
+pa_status pa_batch_solve(pa_batch* b, int32_t generations, uint8_t* best_host, double* best_fit);
+
+/* Context of instance i (owned by the batch): for pa_get_population etc. */
+pa_status pa_batch_context(pa_batch* b, int32_t i, pa_ctx** out);
+
+/* Last error message of a batch ("" if none). */
+const char* pa_batch_last_error(const pa_batch* b);
+
 /*
  * Size of the device array behind pa_eval_population_noalloc (bytes).
  */

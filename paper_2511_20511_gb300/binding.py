@@ -61,6 +61,15 @@ _SIGS = {
     "pa_status_str": (C.c_char_p, [C.c_int]),
     "pa_last_error": (C.c_char_p, [C.c_void_p]),
     "pa_kernel_launches": (C.c_uint64, []),
+    "pa_batch_create": (C.c_int, [C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                  C.c_void_p, C.POINTER(C.c_void_p)]),
+    "pa_batch_destroy": (None, [C.c_void_p]),
+    "pa_batch_load": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "pa_batch_tune": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p]),
+    "pa_batch_groups": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "pa_batch_solve": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p]),
+    "pa_batch_context": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_void_p)]),
+    "pa_batch_last_error": (C.c_char_p, [C.c_void_p]),
     "pa_eval_population_noalloc": (C.c_int, [C.POINTER(pa_config), C.c_void_p, C.c_void_p,
                                              C.c_int64, C.c_void_p, C.c_void_p]),
 }
@@ -317,3 +326,94 @@ class Context:
 
     def validate_population(self, pop):
         return pa_validate_population(self.handle, pop)
+
+
+class Batch:
+    """Many instances solved together (pa_batch_*).  instances: list of dicts
+    with keys cfg, beta, and optionally user_xy_mm, bs_xy_mm."""
+
+    def __init__(self, instances, stream=None):
+        n = len(instances)
+        self.n = n
+        self.cfgs = (pa_config * n)(*[d["cfg"] for d in instances])
+        self._keep = []
+        betas = (C.c_void_p * n)()
+        have_pos = all(d.get("user_xy_mm") is not None for d in instances)
+        ux = (C.c_void_p * n)()
+        bx = (C.c_void_p * n)()
+        self.shapes = []
+        for i, d in enumerate(instances):
+            cfg = d["cfg"]
+            b = np.ascontiguousarray(d["beta"], dtype=np.float64)
+            assert b.shape == (cfg.L, cfg.L, cfg.K)
+            self._keep.append(b)
+            betas[i] = b.ctypes.data
+            self.shapes.append((cfg.L, cfg.K))
+            if have_pos:
+                u = np.ascontiguousarray(d["user_xy_mm"], dtype=np.int32)
+                s = np.ascontiguousarray(d["bs_xy_mm"], dtype=np.int32)
+                self._keep += [u, s]
+                ux[i] = u.ctypes.data
+                bx[i] = s.ctypes.data
+        out = C.c_void_p()
+        st = lib().pa_batch_create(n, C.cast(self.cfgs, C.c_void_p), C.cast(betas, C.c_void_p),
+                                   C.cast(ux, C.c_void_p) if have_pos else None,
+                                   C.cast(bx, C.c_void_p) if have_pos else None,
+                                   _stream_handle(stream), C.byref(out))
+        _check(st, None)
+        self.handle = out
+        self.offsets = np.cumsum([0] + [L * K for L, K in self.shapes])
+
+    def _bcheck(self, st):
+        if st != PA_OK:
+            raise PaError(st, lib().pa_status_str(st).decode() + ": " +
+                          lib().pa_batch_last_error(self.handle).decode())
+
+    def tune(self, generations):
+        ng = C.c_int32(0)
+        self._bcheck(lib().pa_batch_groups(self.handle, C.byref(ng), None, None))
+        chosen = np.zeros(max(1, ng.value), dtype=np.int32)
+        self._bcheck(lib().pa_batch_tune(self.handle, int(generations), _host_ptr(chosen)))
+        return chosen[:ng.value]
+
+    def groups(self):
+        ng = C.c_int32(0)
+        self._bcheck(lib().pa_batch_groups(self.handle, C.byref(ng), None, None))
+        cs = np.zeros(max(1, ng.value), dtype=np.int32)
+        gi = np.zeros(self.n, dtype=np.int32)
+        self._bcheck(lib().pa_batch_groups(self.handle, None, _host_ptr(cs), _host_ptr(gi)))
+        return cs[:ng.value], gi
+
+    def solve(self, generations):
+        best = np.zeros(int(self.offsets[-1]), dtype=np.uint8)
+        fit = np.zeros(self.n, dtype=np.float64)
+        self._bcheck(lib().pa_batch_solve(self.handle, int(generations), _host_ptr(best),
+                                          _host_ptr(fit)))
+        rows = [best[self.offsets[i]:self.offsets[i + 1]].reshape(self.shapes[i])
+                for i in range(self.n)]
+        return rows, fit
+
+    def load(self, i, beta, user_xy_mm=None, bs_xy_mm=None):
+        b = np.ascontiguousarray(beta, dtype=np.float64)
+        u = None if user_xy_mm is None else np.ascontiguousarray(user_xy_mm, dtype=np.int32)
+        s = None if bs_xy_mm is None else np.ascontiguousarray(bs_xy_mm, dtype=np.int32)
+        self._bcheck(lib().pa_batch_load(self.handle, int(i), _host_ptr(b), _host_ptr(u),
+                                         _host_ptr(s)))
+        self._keep.append((b, u, s))
+
+    def context(self, i):
+        out = C.c_void_p()
+        self._bcheck(lib().pa_batch_context(self.handle, int(i), C.byref(out)))
+        return out
+
+    def close(self):
+        if self.handle:
+            lib().pa_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+

@@ -1,0 +1,392 @@
+// pa_batch.cu -- many independent pilot-assignment instances of uneven size
+// solved together (the batched form of the Alg. 1 loop).
+//
+// Instances are grouped by kernel variant (precision, SINR mode, BS-column
+// width NJ, load width); each group runs as ONE persistent launch of
+// k_solve_batch in which every thread-block cluster takes the next instance
+// from a counter until the group is done, so uneven instances balance
+// across the GPU.  Seeding of all instances is one launch (one block per
+// instance).  The whole batch solve -- counter reset, seeding, the group
+// launches on parallel streams, and the copies of the best members to the
+// host -- is captured once into a CUDA graph and replayed.  The cluster size
+// of each group (1 CTA per instance up to 16) is picked by pa_batch_tune,
+// which times the candidates on the batch itself; the results do not depend
+// on it (every instance's arithmetic is the same whatever the tiling).
+#include <algorithm>
+#include <cstring>
+#include <map>
+#include <new>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "pa_internal.cuh"
+
+namespace pa {
+void set_thread_error(const std::string& msg);
+}
+
+struct pa_batch {
+  int n = 0;
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  std::vector<pa_ctx*> ctx;
+  struct Group {
+    std::vector<int> members;
+    int C = 0;
+    int clusters = 0;
+    size_t smem = 0;
+    std::vector<unsigned char> h_args;
+    void* d_args = nullptr;
+    cudaStream_t side = nullptr;
+    cudaEvent_t done = nullptr;
+  };
+  std::vector<Group> groups;
+  void* d_seed_args = nullptr;
+  size_t seed_smem = 0;
+  int* d_counters = nullptr;
+  uint8_t* d_best = nullptr;
+  double* d_bestfit = nullptr;
+  uint8_t* h_best = nullptr;     // pinned
+  double* h_bestfit = nullptr;   // pinned
+  std::vector<int64_t> best_off;
+  int64_t best_bytes = 0;
+  cudaGraphExec_t graph = nullptr;
+  int graph_G = -1;
+  cudaEvent_t fork = nullptr;
+  std::string err;
+};
+
+namespace {
+
+pa_status bfail(pa_batch* b, pa_status st, const std::string& m) {
+  if (b) b->err = m;
+  return st;
+}
+
+pa_status bcuda(pa_batch* b, cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return PA_OK;
+  return bfail(b, e == cudaErrorMemoryAllocation ? PA_ENOMEM : PA_ECUDA,
+               std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+void destroy_batch(pa_batch* b) {
+  if (!b) return;
+  if (b->graph) cudaGraphExecDestroy(b->graph);
+  for (auto& g : b->groups) {
+    cudaFree(g.d_args);
+    if (g.side) cudaStreamDestroy(g.side);
+    if (g.done) cudaEventDestroy(g.done);
+  }
+  if (b->fork) cudaEventDestroy(b->fork);
+  cudaFree(b->d_seed_args);
+  cudaFree(b->d_counters);
+  cudaFree(b->d_best);
+  cudaFree(b->d_bestfit);
+  cudaFreeHost(b->h_best);
+  cudaFreeHost(b->h_bestfit);
+  for (pa_ctx* c : b->ctx) pa_destroy(c);
+  delete b;
+}
+
+// (Re)build one group's argument records for cluster size C and G
+// generations; 0 on success, else the status.
+pa_status build_group_args(pa_batch* b, pa_batch::Group& g, int C, int G) {
+  const size_t ab = pa::solve_args_bytes();
+  std::vector<unsigned char> h(ab * g.members.size());
+  size_t smem = 0;
+  for (size_t m = 0; m < g.members.size(); ++m) {
+    const int i = g.members[m];
+    pa_ctx* c = b->ctx[i];
+    const size_t s = pa::solve_fill_args(c, C, 0, G, c->pop[0], c->pop[1], c->fit,
+                                         b->d_best + b->best_off[i], b->d_bestfit + i,
+                                         h.data() + m * ab);
+    if (s == 0) return PA_EUNSUPPORTED;
+    smem = std::max(smem, s);
+  }
+  const int maxc = pa::solve_batch_max_clusters(b->ctx[g.members[0]], C, smem);
+  if (maxc < 1) return PA_EUNSUPPORTED;
+  if (!g.d_args) {
+    pa_status st = bcuda(b, cudaMalloc(&g.d_args, h.size()), "cudaMalloc batch args");
+    if (st != PA_OK) return st;
+  }
+  pa_status st = bcuda(b, cudaMemcpy(g.d_args, h.data(), h.size(), cudaMemcpyHostToDevice),
+                       "copy batch args");
+  if (st != PA_OK) return st;
+  g.h_args.swap(h);
+  g.C = C;
+  g.smem = smem;
+  g.clusters = std::min<int>((int)g.members.size(), maxc);
+  return PA_OK;
+}
+
+// Cluster size with the fewest CTAs that still gives every SM work, as the
+// starting point before tuning.
+int default_cluster(const pa_batch* b, const pa_batch::Group& g) {
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
+  int C = 1;
+  while (C < 16 && (int)g.members.size() * C < sms) C *= 2;
+  return C;
+}
+
+pa_status run_groups(pa_batch* b, cudaStream_t st) {
+  pa_status s = bcuda(b, cudaMemsetAsync(b->d_counters, 0, sizeof(int) * b->groups.size(), st),
+                      "reset counters");
+  if (s != PA_OK) return s;
+  s = bcuda(b, pa::launch_seed_batch(b->d_seed_args, b->n, b->seed_smem, st), "seed kernel");
+  if (s != PA_OK) return s;
+  s = bcuda(b, cudaEventRecord(b->fork, st), "fork");
+  if (s != PA_OK) return s;
+  for (size_t k = 0; k < b->groups.size(); ++k) {
+    auto& g = b->groups[k];
+    s = bcuda(b, cudaStreamWaitEvent(g.side, b->fork, 0), "fork wait");
+    if (s != PA_OK) return s;
+    s = bcuda(b, pa::launch_solve_batch(b->ctx[g.members[0]], g.C, g.clusters, g.d_args,
+                                        (int)g.members.size(), b->d_counters + k, g.smem, g.side),
+              "batched solve kernel");
+    if (s != PA_OK) return s;
+    s = bcuda(b, cudaEventRecord(g.done, g.side), "join");
+    if (s != PA_OK) return s;
+    s = bcuda(b, cudaStreamWaitEvent(st, g.done, 0), "join wait");
+    if (s != PA_OK) return s;
+  }
+  return PA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+pa_status pa_batch_create(int32_t n, const pa_config* cfgs, const double* const* betas,
+                          const int32_t* const* user_xy_mm, const int32_t* const* bs_xy_mm,
+                          void* stream, pa_batch** out) {
+  if (!out) return PA_EINVAL;
+  *out = nullptr;
+  if (n < 1 || !cfgs || !betas) {
+    pa::set_thread_error("n >= 1, cfgs and betas are required");
+    return PA_EINVAL;
+  }
+  pa_batch* b = new (std::nothrow) pa_batch();
+  if (!b) return PA_ENOMEM;
+  b->n = n;
+  b->stream = static_cast<cudaStream_t>(stream);
+  cudaGetDevice(&b->device);
+  pa_status st = PA_OK;
+  b->ctx.assign(n, nullptr);
+  b->best_off.assign(n, 0);
+  for (int i = 0; i < n && st == PA_OK; ++i) {
+    const int32_t* u = user_xy_mm ? user_xy_mm[i] : nullptr;
+    const int32_t* s = bs_xy_mm ? bs_xy_mm[i] : nullptr;
+    st = pa_create(&cfgs[i], betas[i], u, s, stream, &b->ctx[i]);
+    if (st != PA_OK) {
+      b->err = std::string("instance ") + std::to_string(i) + ": " + pa_last_error(nullptr);
+      break;
+    }
+    b->best_off[i] = b->best_bytes;
+    b->best_bytes += (int64_t)cfgs[i].L * cfgs[i].K;
+  }
+  // kernel-variant groups
+  std::map<std::tuple<int, int, int, int>, int> key2g;
+  if (st == PA_OK) {
+    for (int i = 0; i < n; ++i) {
+      const pa_ctx* c = b->ctx[i];
+      const auto key = std::make_tuple(c->cfg.prec, c->cfg.mode,
+                                       c->cfg.prec == PA_FP32 ? c->t32.NJ : 0,
+                                       c->cfg.prec == PA_FP32 ? c->t32.vec : 0);
+      auto it = key2g.find(key);
+      if (it == key2g.end()) {
+        key2g[key] = (int)b->groups.size();
+        b->groups.emplace_back();
+        b->groups.back().members.push_back(i);
+      } else {
+        b->groups[it->second].members.push_back(i);
+      }
+    }
+  }
+  auto chk = [&](cudaError_t e, const char* what) {
+    if (st == PA_OK) st = bcuda(b, e, what);
+    return st == PA_OK;
+  };
+  if (st == PA_OK) {
+    chk(cudaMalloc(&b->d_best, std::max<int64_t>(1, b->best_bytes)), "cudaMalloc best");
+    chk(cudaMalloc(&b->d_bestfit, sizeof(double) * n), "cudaMalloc best fit");
+    chk(cudaMallocHost(&b->h_best, std::max<int64_t>(1, b->best_bytes)), "cudaMallocHost best");
+    chk(cudaMallocHost(&b->h_bestfit, sizeof(double) * n), "cudaMallocHost best fit");
+    chk(cudaMalloc(&b->d_counters, sizeof(int) * std::max<size_t>(1, b->groups.size())),
+        "cudaMalloc counters");
+    chk(cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming), "event");
+  }
+  if (st == PA_OK) {
+    const size_t sb = pa::seed_args_bytes();
+    std::vector<unsigned char> h(sb * n);
+    for (int i = 0; i < n; ++i)
+      b->seed_smem = std::max(b->seed_smem, pa::seed_fill_args(b->ctx[i], h.data() + sb * i));
+    if (chk(cudaMalloc(&b->d_seed_args, h.size()), "cudaMalloc seed args"))
+      chk(cudaMemcpy(b->d_seed_args, h.data(), h.size(), cudaMemcpyHostToDevice), "copy seed args");
+    // one seeding pass now: prepares the kernel outside any later capture
+    if (st == PA_OK) chk(pa::launch_seed_batch(b->d_seed_args, n, b->seed_smem, b->stream), "seed");
+    if (st == PA_OK) chk(cudaStreamSynchronize(b->stream), "seed sync");
+  }
+  for (auto& g : b->groups) {
+    if (st != PA_OK) break;
+    if (!chk(cudaStreamCreateWithFlags(&g.side, cudaStreamNonBlocking), "stream")) break;
+    if (!chk(cudaEventCreateWithFlags(&g.done, cudaEventDisableTiming), "event")) break;
+    // the largest cluster size that fits, starting from the default
+    int C = default_cluster(b, g);
+    pa_status gs = PA_EUNSUPPORTED;
+    for (; C >= 1 && gs != PA_OK; C /= 2) {
+      gs = build_group_args(b, g, C, 1);
+      if (gs != PA_OK && gs != PA_EUNSUPPORTED) break;
+    }
+    if (gs != PA_OK) st = bfail(b, gs, "an instance of the batch does not fit the solve kernel");
+  }
+  if (st != PA_OK) {
+    pa::set_thread_error(b->err);
+    destroy_batch(b);
+    return st;
+  }
+  *out = b;
+  return PA_OK;
+}
+
+void pa_batch_destroy(pa_batch* b) {
+  if (!b) return;
+  cudaStreamSynchronize(b->stream);
+  destroy_batch(b);
+}
+
+const char* pa_batch_last_error(const pa_batch* b) { return b ? b->err.c_str() : ""; }
+
+pa_status pa_batch_load(pa_batch* b, int32_t i, const double* beta, const int32_t* user_xy_mm,
+                        const int32_t* bs_xy_mm) {
+  if (!b) return PA_EINVAL;
+  if (i < 0 || i >= b->n) return bfail(b, PA_EINVAL, "instance index out of range");
+  const bool had = b->ctx[i]->has_positions != 0;
+  if ((user_xy_mm != nullptr) != had)
+    return bfail(b, PA_EINVAL, "positions must be given exactly when the instance had them");
+  pa_status st = pa_load_instance(b->ctx[i], beta, user_xy_mm, bs_xy_mm);
+  if (st != PA_OK) return bfail(b, st, pa_last_error(b->ctx[i]));
+  return PA_OK;
+}
+
+pa_status pa_batch_tune(pa_batch* b, int32_t generations, int32_t* chosen) {
+  if (!b) return PA_EINVAL;
+  if (generations < 1) return bfail(b, PA_EINVAL, "generations must be >= 1");
+  pa_status st = bcuda(b, pa::launch_seed_batch(b->d_seed_args, b->n, b->seed_smem, b->stream),
+                       "seed kernel");
+  if (st != PA_OK) return st;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  for (size_t k = 0; k < b->groups.size() && st == PA_OK; ++k) {
+    auto& g = b->groups[k];
+    int best_C = g.C;
+    float best_ms = -1.f;
+    for (int C : {1, 2, 4, 8, 16}) {
+      pa_status gs = build_group_args(b, g, C, generations);
+      if (gs == PA_EUNSUPPORTED) continue;
+      if (gs != PA_OK) {
+        st = gs;
+        break;
+      }
+      float ms = 0.f;
+      for (int rep = 0; rep < 2; ++rep) {  // first run warms up
+        cudaMemsetAsync(b->d_counters + k, 0, sizeof(int), b->stream);
+        cudaEventRecord(e0, b->stream);
+        cudaError_t e = pa::launch_solve_batch(b->ctx[g.members[0]], g.C, g.clusters, g.d_args,
+                                               (int)g.members.size(), b->d_counters + k, g.smem,
+                                               b->stream);
+        cudaEventRecord(e1, b->stream);
+        st = bcuda(b, e, "batched solve kernel");
+        if (st == PA_OK) st = bcuda(b, cudaEventSynchronize(e1), "tune sync");
+        if (st != PA_OK) break;
+        cudaEventElapsedTime(&ms, e0, e1);
+      }
+      if (st != PA_OK) break;
+      if (best_ms < 0.f || ms < best_ms) {
+        best_ms = ms;
+        best_C = C;
+      }
+    }
+    if (st == PA_OK) st = build_group_args(b, g, best_C, 1);
+    if (chosen && st == PA_OK) chosen[k] = best_C;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  b->graph_G = -1;  // the captured graph used the previous shapes
+  if (b->graph) {
+    cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+  }
+  return st;
+}
+
+pa_status pa_batch_groups(pa_batch* b, int32_t* n_groups, int32_t* cluster_sizes,
+                          int32_t* group_of_instance) {
+  if (!b) return PA_EINVAL;
+  if (n_groups) *n_groups = (int32_t)b->groups.size();
+  for (size_t k = 0; k < b->groups.size(); ++k) {
+    if (cluster_sizes) cluster_sizes[k] = b->groups[k].C;
+    if (group_of_instance)
+      for (int i : b->groups[k].members) group_of_instance[i] = (int32_t)k;
+  }
+  return PA_OK;
+}
+
+pa_status pa_batch_solve(pa_batch* b, int32_t generations, uint8_t* best_host, double* best_fit) {
+  if (!b) return PA_EINVAL;
+  if (generations < 0) return bfail(b, PA_EINVAL, "generations must be >= 0");
+  pa_status st = PA_OK;
+  if (b->graph_G != generations || !b->graph) {
+    if (b->graph) {
+      cudaGraphExecDestroy(b->graph);
+      b->graph = nullptr;
+    }
+    for (auto& g : b->groups) {
+      st = build_group_args(b, g, g.C, generations);
+      if (st != PA_OK) return bfail(b, st, "rebuilding batch arguments failed");
+    }
+    cudaGraph_t graph = nullptr;
+    st = bcuda(b, cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal),
+               "begin capture");
+    if (st != PA_OK) return st;
+    pa_status rs = run_groups(b, b->stream);
+    if (rs == PA_OK)
+      rs = bcuda(b, cudaMemcpyAsync(b->h_best, b->d_best, std::max<int64_t>(1, b->best_bytes),
+                                    cudaMemcpyDeviceToHost, b->stream),
+                 "copy best");
+    if (rs == PA_OK)
+      rs = bcuda(b, cudaMemcpyAsync(b->h_bestfit, b->d_bestfit, sizeof(double) * b->n,
+                                    cudaMemcpyDeviceToHost, b->stream),
+                 "copy best fit");
+    cudaError_t ee = cudaStreamEndCapture(b->stream, &graph);
+    if (rs != PA_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return rs;
+    }
+    st = bcuda(b, ee, "end capture");
+    if (st == PA_OK) st = bcuda(b, cudaGraphInstantiate(&b->graph, graph, 0), "instantiate graph");
+    if (graph) cudaGraphDestroy(graph);
+    if (st != PA_OK) return st;
+    b->graph_G = generations;
+  }
+  st = bcuda(b, cudaGraphLaunch(b->graph, b->stream), "graph launch");
+  if (st == PA_OK) st = bcuda(b, cudaStreamSynchronize(b->stream), "sync");
+  if (st != PA_OK) return st;
+  for (pa_ctx* c : b->ctx) {
+    c->cur = 1;
+    c->generation = generations;
+  }
+  if (best_host) std::memcpy(best_host, b->h_best, (size_t)b->best_bytes);
+  if (best_fit) std::memcpy(best_fit, b->h_bestfit, sizeof(double) * b->n);
+  return PA_OK;
+}
+
+pa_status pa_batch_context(pa_batch* b, int32_t i, pa_ctx** out) {
+  if (!b || !out || i < 0 || i >= b->n) return PA_EINVAL;
+  *out = b->ctx[i];
+  return PA_OK;
+}
+
+}  // extern "C"

@@ -28,6 +28,7 @@
 //   uniformly random rows (Fisher-Yates).
 #include <algorithm>
 #include <atomic>
+#include <cstring>
 
 #include "pa_internal.cuh"
 
@@ -202,8 +203,7 @@ __device__ void random_row(uint8_t* row, int K, DrawStream& ds, uint32_t first) 
 constexpr int kSeedThreads = 1024;
 constexpr int kMaxU = 64 * 64;  // users handled by the single-block K-means
 
-__global__ void __launch_bounds__(kSeedThreads) k_seed(const SeedArgs a) {
-  extern __shared__ __align__(16) unsigned char smem[];
+__device__ __forceinline__ void seed_body(const SeedArgs& a, unsigned char* smem, int& changed) {
   const int L = a.L, K = a.K, U = L * K, kk = a.kk;
   const int64_t LK = U;
   double* cx = reinterpret_cast<double*>(smem);
@@ -215,7 +215,6 @@ __global__ void __launch_bounds__(kSeedThreads) k_seed(const SeedArgs a) {
   int* idx = label + U;          // [U] scratch for the initial shuffle
   int32_t* feat = idx + U;       // [U][2] position relative to the own BS
   uint8_t* astar = reinterpret_cast<uint8_t*>(feat + 2 * U);  // [U]
-  __shared__ int changed;
   const bool kmeans = a.user_xy != nullptr && a.n_seeded > 0;
 
   if (kmeans) {
@@ -352,6 +351,25 @@ __global__ void __launch_bounds__(kSeedThreads) k_seed(const SeedArgs a) {
   }
 }
 
+__global__ void __launch_bounds__(kSeedThreads) k_seed(const SeedArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ int changed;
+  seed_body(a, smem, changed);
+}
+
+// Block b seeds instance b of a batch.
+__global__ void __launch_bounds__(kSeedThreads) k_seed_batch(const SeedArgs* __restrict__ args,
+                                                             int n) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ int changed;
+  for (int i = blockIdx.x; i < n; i += gridDim.x) {
+    const SeedArgs a = args[i];
+    seed_body(a, smem, changed);
+    __syncthreads();
+  }
+}
+
+
 // ------------------------------------------------------------------ best member
 template <typename FT>
 __global__ void __launch_bounds__(1024) k_argbest(const FT* fit, int N, const uint8_t* pop,
@@ -450,6 +468,50 @@ cudaError_t launch_seed(pa_ctx* ctx, uint8_t* pop, cudaStream_t st) {
   }
   (void)cudaGetLastError();  // drop a stale error of an earlier call
   k_seed<<<1, kSeedThreads, smem, st>>>(a);
+  count_launch();
+  return cudaGetLastError();
+}
+
+size_t seed_args_bytes() { return sizeof(SeedArgs); }
+
+static SeedArgs seed_args_of(pa_ctx* ctx, uint8_t* pop) {
+  const pa_config& c = ctx->cfg;
+  SeedArgs a;
+  a.user_xy = ctx->has_positions ? ctx->user_xy : nullptr;
+  a.bs_xy = ctx->has_positions ? ctx->bs_xy : nullptr;
+  a.L = c.L;
+  a.K = c.K;
+  a.kk = c.kmeans_k;
+  a.max_iter = c.kmeans_max_iter;
+  a.N = c.N;
+  a.n_seeded = c.n_seeded;
+  a.seed = c.seed;
+  a.pop = pop;
+  a.labels = ctx->labels;
+  a.centroids = ctx->centroids;
+  return a;
+}
+
+size_t seed_fill_args(pa_ctx* ctx, void* out) {
+  const SeedArgs a = seed_args_of(ctx, ctx->pop[0]);
+  std::memcpy(out, &a, sizeof a);
+  return seed_smem(ctx->cfg.L, ctx->cfg.K, ctx->cfg.kmeans_k);
+}
+
+cudaError_t launch_seed_batch(const void* d_args, int n, size_t smem, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  static std::atomic<uint64_t> capped{0};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const uint64_t bit = 1ULL << (dev & 63);
+  if (!(capped.load() & bit)) {
+    e = raise_smem_cap((const void*)k_seed_batch, dev);
+    if (e != cudaSuccess) return e;
+    capped.fetch_or(bit);
+  }
+  (void)cudaGetLastError();  // drop a stale error of an earlier call
+  k_seed_batch<<<n, kSeedThreads, smem, st>>>(static_cast<const SeedArgs*>(d_args), n);
   count_launch();
   return cudaGetLastError();
 }
