@@ -396,7 +396,7 @@ def run_batched(B, inputs, G=100, n=512, reps=3):
         t1 = time.perf_counter()
         best, bf = c.solve(G)
         lat.append(time.perf_counter() - t1)
-        same &= bool((best == rows[i]).all()) and bf == fits[i]
+        same = same and bool((best == rows[i]).all()) and bool(bf == fits[i])
     t_seq = time.perf_counter() - t0
     for c in ctxs:
         c.close()

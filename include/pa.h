@@ -219,7 +219,9 @@ typedef struct pa_batch pa_batch;
  * Create a batch of n instances: cfgs[i], betas[i] (host, L_i*L_i*K_i
  * float64) and optional positions user_xy_mm[i] / bs_xy_mm[i] as for
  * pa_create (the arrays of positions may be NULL for all instances).  Work
- * goes to `stream`.  Synchronous.  On failure pa_last_error(NULL) explains.
+ * goes to `stream` (NULL: a stream the batch creates; the legacy default
+ * stream cannot be captured into a graph).  Synchronous.  On failure
+ * pa_last_error(NULL) explains.
  */
 pa_status pa_batch_create(int32_t n, const pa_config* cfgs, const double* const* betas,
                           const int32_t* const* user_xy_mm, const int32_t* const* bs_xy_mm,

@@ -54,6 +54,7 @@ struct pa_batch {
   cudaGraphExec_t graph = nullptr;
   int graph_G = -1;
   cudaEvent_t fork = nullptr;
+  bool own_stream = false;
   std::string err;
 };
 
@@ -86,6 +87,7 @@ void destroy_batch(pa_batch* b) {
   cudaFreeHost(b->h_best);
   cudaFreeHost(b->h_bestfit);
   for (pa_ctx* c : b->ctx) pa_destroy(c);
+  if (b->own_stream) cudaStreamDestroy(b->stream);
   delete b;
 }
 
@@ -170,8 +172,19 @@ pa_status pa_batch_create(int32_t n, const pa_config* cfgs, const double* const*
   pa_batch* b = new (std::nothrow) pa_batch();
   if (!b) return PA_ENOMEM;
   b->n = n;
-  b->stream = static_cast<cudaStream_t>(stream);
   cudaGetDevice(&b->device);
+  // graphs cannot be captured on the legacy default stream: without a
+  // caller stream the batch uses a stream of its own
+  if (stream) {
+    b->stream = static_cast<cudaStream_t>(stream);
+  } else {
+    if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      delete b;
+      return PA_ECUDA;
+    }
+    b->own_stream = true;
+  }
+  stream = b->stream;
   pa_status st = PA_OK;
   b->ctx.assign(n, nullptr);
   b->best_off.assign(n, 0);
@@ -232,12 +245,15 @@ pa_status pa_batch_create(int32_t n, const pa_config* cfgs, const double* const*
     if (st != PA_OK) break;
     if (!chk(cudaStreamCreateWithFlags(&g.side, cudaStreamNonBlocking), "stream")) break;
     if (!chk(cudaEventCreateWithFlags(&g.done, cudaEventDisableTiming), "event")) break;
-    // the largest cluster size that fits, starting from the default
-    int C = default_cluster(b, g);
+    // the default size if it fits, else the nearest larger one, else smaller
+    const int C0 = default_cluster(b, g);
+    std::vector<int> order{C0};
+    for (int C = C0 * 2; C <= 16; C *= 2) order.push_back(C);
+    for (int C = C0 / 2; C >= 1; C /= 2) order.push_back(C);
     pa_status gs = PA_EUNSUPPORTED;
-    for (; C >= 1 && gs != PA_OK; C /= 2) {
+    for (int C : order) {
       gs = build_group_args(b, g, C, 1);
-      if (gs != PA_OK && gs != PA_EUNSUPPORTED) break;
+      if (gs != PA_EUNSUPPORTED) break;
     }
     if (gs != PA_OK) st = bfail(b, gs, "an instance of the batch does not fit the solve kernel");
   }
