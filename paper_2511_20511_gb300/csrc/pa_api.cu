@@ -185,6 +185,8 @@ static void free_ctx(pa_ctx* c) {
   cudaFree(c->t32.tab);
   cudaFree(c->t32.own);
   cudaFree(c->t32.bn);
+  cudaFree(c->t32.partial);
+  cudaFree(c->t32.err_flag);
   cudaFree(c->user_xy);
   cudaFree(c->bs_xy);
   cudaFree(c->labels);
@@ -217,7 +219,9 @@ pa_status pa_create(const pa_config* cfg, const double* beta, const int32_t* use
   if (!pa::instance_ok(*cfg, beta, user_xy_mm, bs_xy_mm, &bmax))
     return reject(PA_EINVAL, "beta must be finite and > 0; relative positions within int32");
   const int L = cfg->L, K = cfg->K;
-  if (cfg->prec == PA_FP32 && !pa::f32_supported(L, K, nullptr))
+  int sJT = 0, sRSt = 0, svec = 0, sntile = 0;
+  const bool resident = cfg->prec != PA_FP32 || pa::f32_supported(L, K, nullptr);
+  if (!resident && !pa::f32_stream_geometry(L, K, &sJT, &sRSt, &svec, &sntile))
     return reject(PA_EUNSUPPORTED, "FP32 gain table of this (L, K) exceeds shared memory");
 
   pa_ctx* c = new (std::nothrow) pa_ctx();
@@ -240,7 +244,20 @@ pa_status pa_create(const pa_config* cfg, const double* beta, const int32_t* use
       break;
     if (!chk(cudaMalloc(&c->beta64, sizeof(double) * n_beta), "cudaMalloc beta")) break;
     if (!chk(cudaMalloc(&c->bnc64, sizeof(double) * L), "cudaMalloc bnc")) break;
-    if (cfg->prec == PA_FP32) {
+    if (cfg->prec == PA_FP32 && !resident) {
+      c->t32.streamed = 1;
+      c->t32.JT = sJT;
+      c->t32.RSt = sRSt;
+      c->t32.vec = svec;
+      c->t32.ntile = sntile;
+      c->t32.tile_floats = ((LK * sRSt + 3) / 4) * 4;
+      if (!chk(cudaMalloc(&c->t32.tab, sizeof(float) * c->t32.tile_floats * sntile), "cudaMalloc tab"))
+        break;
+      if (!chk(cudaMalloc(&c->t32.own, sizeof(float) * LK), "cudaMalloc own")) break;
+      if (!chk(cudaMalloc(&c->t32.bn, sizeof(float) * L), "cudaMalloc bn")) break;
+      if (!chk(cudaMalloc(&c->t32.err_flag, sizeof(int)), "cudaMalloc flag")) break;
+      if (!chk(cudaMemset(c->t32.err_flag, 0, sizeof(int)), "memset flag")) break;
+    } else if (cfg->prec == PA_FP32) {
       int NJ, RS, vec;
       pa::f32_geometry(L, K, &NJ, &RS, &vec);
       c->t32.NJ = NJ;
@@ -305,7 +322,21 @@ pa_status pa_set_stream(pa_ctx* ctx, void* stream) {
 static cudaError_t eval_any(pa_ctx* ctx, const uint8_t* pop, int64_t n, void* fit) {
   if (ctx->cfg.prec == PA_FP64)
     return pa::launch_eval_f64(ctx, pop, n, static_cast<double*>(fit), ctx->stream);
+  if (ctx->t32.streamed)
+    return pa::launch_eval_f32_stream(ctx, pop, n, static_cast<float*>(fit), ctx->stream);
   return pa::launch_eval_f32(ctx, pop, n, static_cast<float*>(fit), ctx->stream);
+}
+
+// A bounded device wait of an earlier kernel that gave up (column-tiled
+// evaluation): reported once, then cleared.
+static pa_status check_timeout(pa_ctx* ctx) {
+  if (!ctx->t32.err_flag) return PA_OK;
+  int flag = 0;
+  PA_TRY(ctx, cudaMemcpy(&flag, ctx->t32.err_flag, sizeof flag, cudaMemcpyDeviceToHost),
+         "read flag");
+  if (!flag) return PA_OK;
+  cudaMemset(ctx->t32.err_flag, 0, sizeof(int));
+  return fail(ctx, PA_ETIMEOUT, "a shared-memory tile copy did not complete in time");
 }
 
 pa_status pa_eval_population(pa_ctx* ctx, const uint8_t* pop_dev, int64_t n, void* fit_dev) {
@@ -350,7 +381,7 @@ pa_status pa_eval_population_host(pa_ctx* ctx, const uint8_t* pop_host, int64_t 
                               ctx->stream),
          "copy fitness");
   PA_TRY(ctx, cudaStreamSynchronize(ctx->stream), "sync");
-  return PA_OK;
+  return check_timeout(ctx);
 }
 
 pa_status pa_ga_step(pa_ctx* ctx, const uint8_t* pop_dev, const void* fit_dev, int32_t generation,

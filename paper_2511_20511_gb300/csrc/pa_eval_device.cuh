@@ -64,6 +64,7 @@ struct F32Smem {
   const float* BN;   // [L]
   int L, K, RS;
   float M, pc;
+  int jbase = 0;     // BS index of the table's first column (column tiles)
 };
 
 // Threads per (member, pilot) of the batch FP32 evaluation: two for float2
@@ -118,7 +119,7 @@ __device__ __forceinline__ void eval_pilot_f32(const F32Smem& s, const uint8_t* 
     float ps = 0.f;
 #pragma unroll
     for (int hh = 0; hh < 2; ++hh) {
-      const int j = 2 * (c0 + c) + hh;
+      const int j = s.jbase + 2 * (c0 + c) + hh;
       if (j < L) {
         const int u = invp[j * stride];
         const float b = s.OWN[j * K + u];

@@ -32,6 +32,15 @@ struct F32Tables {
   float pc = 0.f;        // sigma2/(tau_p rho) * 2^s
   int scale_exp = 0;     // s
   double scale = 1.0;    // 2^s
+  // column-tiled table for instances whose table exceeds shared memory:
+  // ntile tiles of JT BS columns, each [L*K rows][RSt] floats, tile_floats
+  // (padded to 4) apart; tab then holds the tiles back to back
+  int streamed = 0;
+  int JT = 0, ntile = 0, RSt = 0;
+  int64_t tile_floats = 0;
+  float* partial = nullptr;  // scratch: per-(member, tile) fitness partials
+  int64_t partial_cap = 0;   // members it can hold
+  int* err_flag = nullptr;   // set by a kernel whose bounded wait gave up
 };
 
 }  // namespace pa
@@ -88,6 +97,10 @@ cudaError_t launch_eval_f32(const pa_ctx* ctx, const uint8_t* pop, int64_t n, fl
 cudaError_t launch_eval_f64(const pa_ctx* ctx, const uint8_t* pop, int64_t n, double* fit,
                             cudaStream_t st);
 bool f32_supported(int L, int K, size_t* smem_bytes);
+// pa_stream.cu: column-tiled evaluation for tables beyond shared memory
+bool f32_stream_geometry(int L, int K, int* JT, int* RSt, int* vec, int* ntile);
+cudaError_t launch_eval_f32_stream(pa_ctx* ctx, const uint8_t* pop, int64_t n, float* fit,
+                                   cudaStream_t st);
 // pa_ga.cu
 cudaError_t launch_ga_step(const pa_ctx* ctx, const uint8_t* pop, const void* fit, int32_t gen,
                            uint8_t* next, cudaStream_t st);

@@ -51,6 +51,32 @@ __global__ void k_prep_table(const double* __restrict__ beta, int L, int K, int 
   }
 }
 
+// Column-tiled layout: tile t, row r = l*K + u, column jj holds
+// beta[t*JT + jj][l][u] * 2^s (0 for the own cell and past L).
+__global__ void k_prep_table_tiled(const double* __restrict__ beta, int L, int K, int JT, int RSt,
+                                   int64_t tile_floats, int ntile, double scale,
+                                   float* __restrict__ tab, float* __restrict__ own) {
+  const int64_t LK = (int64_t)L * K;
+  const int64_t total = tile_floats * ntile;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int t = (int)(idx / tile_floats);
+    const int64_t rem = idx - (int64_t)t * tile_floats;
+    const int64_t r = rem / RSt;
+    const int jj = (int)(rem - r * RSt);
+    float v = 0.f;
+    if (r < LK) {
+      const int l = (int)(r / K), u = (int)(r - (int64_t)l * K);
+      const int j = t * JT + jj;
+      if (jj < JT && j < L && j != l)
+        v = __double2float_rn(__dmul_rn(beta[((int64_t)j * L + l) * K + u], scale));
+      if (t == 0 && jj == 0)
+        own[r] = __double2float_rn(__dmul_rn(beta[((int64_t)l * L + l) * K + u], scale));
+    }
+    tab[idx] = v;
+  }
+}
+
 }  // namespace
 
 cudaError_t launch_prep(pa_ctx* ctx) {
@@ -63,6 +89,16 @@ cudaError_t launch_prep(pa_ctx* ctx) {
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || !f32) return e;
   const int64_t rows = (int64_t)L * K;
+  if (ctx->t32.streamed) {
+    const int64_t total = ctx->t32.tile_floats * ctx->t32.ntile;
+    const int64_t blocks = (total + 255) / 256;
+    (void)cudaGetLastError();  // drop a stale error of an earlier call
+    k_prep_table_tiled<<<(unsigned)(blocks < 4096 ? blocks : 4096), 256, 0, ctx->stream>>>(
+        ctx->beta64, L, K, ctx->t32.JT, ctx->t32.RSt, ctx->t32.tile_floats, ctx->t32.ntile,
+        ctx->t32.scale, ctx->t32.tab, ctx->t32.own);
+    count_launch();
+    return cudaGetLastError();
+  }
   // table storage is padded to a multiple of 4 floats; pad rows are zero
   const int64_t total = ((rows * ctx->t32.RS + 3) / 4) * 4;
   const int64_t blocks = (total + 255) / 256;

@@ -747,7 +747,7 @@ cudaError_t pick_solve(int NJ, const SolveArgs& a, const SolveShape& s, bool chk
 // the per-generation kernels).
 cudaError_t launch_solve(pa_ctx* ctx, const uint8_t* pop_in, uint8_t* pop_out, int gen0, int G,
                          void* fit_out, uint8_t* best_row, double* best_fit, cudaStream_t st) {
-  if (ctx->solve_C == 0) return cudaErrorNotSupported;
+  if (ctx->solve_C == 0 || ctx->t32.streamed) return cudaErrorNotSupported;
   const pa_config& c = ctx->cfg;
   static const int sizes[] = {16, 8, 4, 2, 1};
   for (int C : sizes) {
@@ -898,7 +898,7 @@ size_t solve_fill_args(const pa_ctx* ctx, int C, int gen0, int G, const uint8_t*
                        uint8_t* pop_out, void* fit_out, uint8_t* best_row, double* best_fit,
                        void* args_out) {
   const pa_config& c = ctx->cfg;
-  if (C > c.N) return 0;
+  if (C > c.N || ctx->t32.streamed) return 0;
   const SolveShape s = solve_shape(ctx, C);
   if (s.smem + 64 * 4 + 16 > (size_t)kSmemBudget) return 0;
   SolveArgs a{};

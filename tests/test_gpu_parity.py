@@ -66,10 +66,10 @@ def test_fp64_fitness_bit_exact(B, oracle, L, K, mode):
 
 
 @pytest.mark.parametrize("L,K", [(2, 2), (7, 4), (19, 10), (7, 1), (19, 13), (37, 16), (19, 17),
-                                 (7, 32), (37, 4), (19, 64), (47, 5)])
+                                 (7, 32), (37, 4), (19, 64), (47, 5), (61, 32), (61, 12), (53, 20)])
 @pytest.mark.parametrize("mode", [0, 1])
 def test_fp32_fitness_within_tolerance(B, oracle, L, K, mode):
-    rings_L = {2: 7, 47: 61}.get(L, L)
+    rings_L = {2: 7, 47: 61, 53: 61}.get(L, L)
     inst = inputs.instance(rings_L, K, seed=L * 7 + K, dtype=np.float32)
     beta = np.ascontiguousarray(inst["beta"][:L, :L, :])
     cfg = _cfg(B, L, K, B.PA_FP32, mode)
@@ -312,5 +312,28 @@ def test_fused_generations_equal_per_generation_kernels(B, L, K, N, E, mode):
         torch.cuda.synchronize()
         assert (pop.cpu().numpy() == fused).all()
         assert (fit.cpu().numpy() == ffit).all()
+    finally:
+        ctx.close()
+
+
+def test_streamed_table_solve_steps(B, oracle):
+    """61 cells x 32 users: the FP32 gain table (476 KB) exceeds shared
+    memory, so evaluation streams BS-column tiles and generations run as
+    per-generation kernels; the elite never decreases and the final fitness
+    agrees with the oracle."""
+    L, K, N = 61, 32, 64
+    inst = inputs.instance(L, K, seed=5, dtype=np.float32)
+    cfg = _cfg(B, L, K, B.PA_FP32, 1, M=512.0, N=N, seed=2)
+    ctx = B.Context(cfg, inst["beta"], inst["user_xy_mm"], inst["bs_xy_mm"])
+    try:
+        ctx.kmeans_seed()
+        hist = []
+        for _ in range(4):
+            ctx.step(3)
+            pop, fit, _ = ctx.get_population()
+            hist.append(fit.max())
+        assert all(b >= a for a, b in zip(hist, hist[1:]))
+        ref = oracle.fitness_batch(inst["beta"], pop[:16], _sp(oracle, cfg))
+        assert (np.abs(fit[:16].astype(np.float64) - ref) / ref).max() <= F32_RTOL
     finally:
         ctx.close()
