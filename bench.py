@@ -343,6 +343,7 @@ def run_ours(args):
     if not args.no_batched:
         line["batched_c3"] = run_batched(B, inputs)
         line["streamed_c5"] = run_streamed(B, inputs, dev)
+        line["serving_c4"] = run_serving(B, inputs, seconds=args.serve_seconds)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
     ctx.close()
@@ -460,6 +461,104 @@ def run_streamed(B, inputs, dev, n=1 << 17, reps=5):
             "sampled_max_rel_err_vs_oracle": float(np.max(np.abs(got - ref) / ref))}
 
 
+def run_serving(B, inputs, rate=2000.0, seconds=2.0, G=40, N=64, tick=10, budget=40 << 30):
+    """Poisson arrivals (rate per second for `seconds`), each request a solve
+    of a fresh seeded instance with L in {7, 19}, K in {8, 16} (tau_p = K,
+    M = 256, finite-M SINR, N = 64, G = 40, FP32 beta).  Served: the
+    continuous-batching server (slots admitted under a device-memory budget,
+    populations resident, `tick` generations per scheduling round).  Plain:
+    one resident context per (L, K), requests solved one at a time in arrival
+    order (load instance + pa_solve).  Latency = completion - arrival."""
+    import numpy as np
+
+    rng = np.random.default_rng(0)
+    arr = np.cumsum(rng.exponential(1.0 / rate, size=int(rate * seconds * 1.5)))
+    arr = arr[arr < seconds]
+    n = len(arr)
+    shapes = [(int(rng.choice([7, 19])), int(rng.choice([8, 16]))) for _ in range(n)]
+    insts = [inputs.instance(L, K, seed=10_000 + i, dtype=np.float32)
+             for i, (L, K) in enumerate(shapes)]
+    base = B.pa_config_default(7, 8, mode=B.PA_SINR_FINITE_M, M=256.0, N=N,
+                               rho=insts[0]["rho"])
+
+    def pct(v, p):
+        v = sorted(v)
+        return v[min(len(v) - 1, int(round(p / 100.0 * (len(v) - 1))))]
+
+    # ---- served
+    srv = B.Server(base, G, tick, budget)
+    for i in range(min(8, n)):  # warm the slot pool and kernels
+        srv.submit(-1 - i, shapes[i][0], shapes[i][1], 1, insts[i]["beta"],
+                   insts[i]["user_xy_mm"], insts[i]["bs_xy_mm"])
+    while srv.stats()["completed"] < min(8, n):
+        srv.poll()
+    done_at = {}
+    results = {}
+    t0 = time.perf_counter()
+    nxt = 0
+    ticks = 0
+    while len(done_at) < n:
+        now = time.perf_counter() - t0
+        while nxt < n and arr[nxt] <= now:
+            L, K = shapes[nxt]
+            srv.submit(nxt, L, K, 10_000 + nxt, insts[nxt]["beta"], insts[nxt]["user_xy_mm"],
+                       insts[nxt]["bs_xy_mm"])
+            nxt += 1
+        done, active, pending = srv.poll()
+        ticks += 1
+        tnow = time.perf_counter() - t0
+        for rid, best, fit in done:
+            if rid >= 0:
+                done_at[rid] = tnow
+                results[rid] = fit
+        if not done and active == 0 and pending == 0 and nxt < n:
+            time.sleep(max(0.0, arr[nxt] - (time.perf_counter() - t0)))
+    served_lat = [done_at[i] - arr[i] for i in range(n)]
+    served_span = max(done_at.values()) - arr[0]
+    stats = srv.stats()
+    srv.close()
+
+    # ---- plain: one solve at a time in arrival order
+    ctxs = {}
+    for (L, K) in set(shapes):
+        i = shapes.index((L, K))
+        cfg = B.pa_config_default(L, K, mode=B.PA_SINR_FINITE_M, M=256.0, tau_p=K, N=N,
+                                  rho=insts[i]["rho"], kmeans_k=K)
+        ctxs[(L, K)] = B.Context(cfg, insts[i]["beta"], insts[i]["user_xy_mm"],
+                                 insts[i]["bs_xy_mm"])
+        ctxs[(L, K)].solve(G)
+    plain_lat = []
+    same = True
+    t0 = time.perf_counter()
+    for i in range(n):
+        now = time.perf_counter() - t0
+        if now < arr[i]:
+            time.sleep(arr[i] - now)
+        c = ctxs[shapes[i]]
+        B.pa_load_instance(c.handle, insts[i]["beta"], insts[i]["user_xy_mm"],
+                           insts[i]["bs_xy_mm"])
+        B.pa_set_seed(c.handle, 10_000 + i)
+        _, bf = c.solve(G)
+        plain_lat.append(time.perf_counter() - t0 - arr[i])
+        same = same and bool(bf == results[i])
+    plain_span = time.perf_counter() - t0 - arr[0]
+    for c in ctxs.values():
+        c.close()
+    ms = lambda x: 1e3 * x  # noqa: E731
+    return {"requests": n, "rate_per_s": rate, "seconds": seconds, "generations": G,
+            "population": N, "tick_generations": tick, "budget_bytes": budget,
+            "served": {"p50_ms": ms(pct(served_lat, 50)), "p99_ms": ms(pct(served_lat, 99)),
+                       "p999_ms": ms(pct(served_lat, 99.9)), "solves_per_s": n / served_span,
+                       "ticks": ticks, "slots": stats["slots"],
+                       "slot_bytes": stats["used_bytes"]},
+            "plain_sequential": {"p50_ms": ms(pct(plain_lat, 50)),
+                                 "p99_ms": ms(pct(plain_lat, 99)),
+                                 "p999_ms": ms(pct(plain_lat, 99.9)),
+                                 "solves_per_s": n / plain_span},
+            "identical_results": same,
+            "timing": "host wall clock; arrivals replayed in real time"}
+
+
 def run_eval_only(args, B, inputs, ctx, stream, dev, rank):
     """Only the population evaluation of 2^20 chromosomes (for profilers)."""
     import torch
@@ -485,6 +584,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--serve-seconds", type=float, default=2.0,
+                    help="length of the Poisson arrival window of the serving comparison")
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the 512-instance batched-solve comparison")
     ap.add_argument("--only", choices=["all", "eval", "solve"], default="all",

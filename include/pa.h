@@ -134,6 +134,9 @@ pa_status pa_load_instance(pa_ctx* ctx, const double* beta, const int32_t* user_
 /* Destroy a context and free its device memory (NULL is ignored). */
 void pa_destroy(pa_ctx* ctx);
 
+/* Replace the seed of every later random draw (seeding and GA steps). */
+pa_status pa_set_seed(pa_ctx* ctx, uint64_t seed);
+
 /* Replace the context stream (cudaStream_t or NULL). */
 pa_status pa_set_stream(pa_ctx* ctx, void* stream);
 
@@ -261,6 +264,53 @@ pa_status pa_batch_context(pa_batch* b, int32_t i, pa_ctx** out);
 
 /* Last error message of a batch ("" if none). */
 const char* pa_batch_last_error(const pa_batch* b);
+
+/* ------------------------------------------------------------------------
+ * Continuous-batching server.  Requests (one instance each) are queued by
+ * pa_server_submit; each pa_server_poll runs one scheduling tick: queued
+ * requests are admitted into resident slots of their (L, K) class while
+ * the device memory of the slots stays within the budget, newly admitted
+ * slots are seeded (one launch), every active slot advances by up to `tick`
+ * generations (one persistent launch per kernel variant; populations stay
+ * resident between ticks), and requests that reach `generations` are
+ * returned.  A request's result equals pa_solve's for the same instance,
+ * configuration and seed.  Not thread safe.
+ * ------------------------------------------------------------------------ */
+typedef struct pa_server pa_server;
+
+/* Create a server: base supplies every configuration field except L, K,
+ * tau_p and kmeans_k (set from each request: tau_p = kmeans_k = K) and seed
+ * (per request).  budget_bytes bounds the device memory of all slots.
+ * stream: cudaStream_t or NULL (a stream of its own). */
+pa_status pa_server_create(const pa_config* base, int32_t generations, int32_t tick,
+                           uint64_t budget_bytes, void* stream, pa_server** out);
+
+/* Destroy a server and its slots (NULL is ignored). */
+void pa_server_destroy(pa_server* s);
+
+/* Queue a request: beta (L*L*K float64), user_xy_mm (L*K*2), bs_xy_mm (L*2)
+ * host arrays, copied before returning; id is returned on completion. */
+pa_status pa_server_submit(pa_server* s, int64_t id, int32_t L, int32_t K, uint64_t seed,
+                           const double* beta, const int32_t* user_xy_mm,
+                           const int32_t* bs_xy_mm);
+
+/*
+ * One scheduling tick (synchronous).  Up to max_done finished requests are
+ * returned: done_ids[i], their best member at done_best + i*best_stride
+ * (L*K bytes) and its fitness done_fit[i] (each output optional);
+ * *n_done = how many.  n_active / n_pending (optional): slots still running
+ * and requests still queued after the tick.
+ */
+pa_status pa_server_poll(pa_server* s, int32_t max_done, int64_t* done_ids, uint8_t* done_best,
+                         int64_t best_stride, double* done_fit, int32_t* n_done,
+                         int32_t* n_active, int32_t* n_pending);
+
+/* Device bytes held by slots, number of slots, requests completed. */
+pa_status pa_server_stats(const pa_server* s, uint64_t* used_bytes, int32_t* n_slots,
+                          int64_t* completed);
+
+/* Last error message of a server ("" if none). */
+const char* pa_server_last_error(const pa_server* s);
 
 /*
  * Size of the device array behind pa_eval_population_noalloc (bytes).

@@ -47,6 +47,7 @@ _SIGS = {
     "pa_load_instance": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "pa_destroy": (None, [C.c_void_p]),
     "pa_set_stream": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "pa_set_seed": (C.c_int, [C.c_void_p, C.c_uint64]),
     "pa_eval_population": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p]),
     "pa_eval_population_host": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p]),
     "pa_ga_step": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p]),
@@ -70,6 +71,17 @@ _SIGS = {
     "pa_batch_solve": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p]),
     "pa_batch_context": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_void_p)]),
     "pa_batch_last_error": (C.c_char_p, [C.c_void_p]),
+    "pa_server_create": (C.c_int, [C.POINTER(pa_config), C.c_int32, C.c_int32, C.c_uint64,
+                                   C.c_void_p, C.POINTER(C.c_void_p)]),
+    "pa_server_destroy": (None, [C.c_void_p]),
+    "pa_server_submit": (C.c_int, [C.c_void_p, C.c_int64, C.c_int32, C.c_int32, C.c_uint64,
+                                   C.c_void_p, C.c_void_p, C.c_void_p]),
+    "pa_server_poll": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_int64,
+                                 C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
+                                 C.POINTER(C.c_int32)]),
+    "pa_server_stats": (C.c_int, [C.c_void_p, C.POINTER(C.c_uint64), C.POINTER(C.c_int32),
+                                  C.POINTER(C.c_int64)]),
+    "pa_server_last_error": (C.c_char_p, [C.c_void_p]),
     "pa_eval_population_noalloc": (C.c_int, [C.POINTER(pa_config), C.c_void_p, C.c_void_p,
                                              C.c_int64, C.c_void_p, C.c_void_p]),
 }
@@ -184,6 +196,10 @@ def pa_kernel_launches():
 
 def pa_destroy(ctx):
     lib().pa_destroy(ctx)
+
+
+def pa_set_seed(ctx, seed):
+    _check(lib().pa_set_seed(ctx, int(seed)), ctx)
 
 
 def pa_set_stream(ctx, stream):
@@ -409,6 +425,60 @@ class Batch:
     def close(self):
         if self.handle:
             lib().pa_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Continuous-batching solve server (pa_server_*)."""
+
+    MAX_LK = 64 * 64
+
+    def __init__(self, base_cfg, generations, tick, budget_bytes, stream=None, max_done=4096):
+        out = C.c_void_p()
+        _check(lib().pa_server_create(C.byref(base_cfg), int(generations), int(tick),
+                                      int(budget_bytes), _stream_handle(stream), C.byref(out)),
+               None)
+        self.handle = out
+        self.max_done = max_done
+        self._ids = np.zeros(max_done, dtype=np.int64)
+        self._best = np.zeros((max_done, self.MAX_LK), dtype=np.uint8)
+        self._fit = np.zeros(max_done, dtype=np.float64)
+
+    def _scheck(self, st):
+        if st != PA_OK:
+            raise PaError(st, lib().pa_status_str(st).decode() + ": " +
+                          lib().pa_server_last_error(self.handle).decode())
+
+    def submit(self, rid, L, K, seed, beta, user_xy_mm, bs_xy_mm):
+        b = np.ascontiguousarray(beta, dtype=np.float64)
+        u = np.ascontiguousarray(user_xy_mm, dtype=np.int32)
+        s = np.ascontiguousarray(bs_xy_mm, dtype=np.int32)
+        self._scheck(lib().pa_server_submit(self.handle, int(rid), int(L), int(K), int(seed),
+                                            _host_ptr(b), _host_ptr(u), _host_ptr(s)))
+
+    def poll(self):
+        nd, na, npd = C.c_int32(0), C.c_int32(0), C.c_int32(0)
+        self._scheck(lib().pa_server_poll(self.handle, self.max_done, _host_ptr(self._ids),
+                                          _host_ptr(self._best), self.MAX_LK, _host_ptr(self._fit),
+                                          C.byref(nd), C.byref(na), C.byref(npd)))
+        k = nd.value
+        return ([(int(self._ids[i]), self._best[i], float(self._fit[i])) for i in range(k)],
+                na.value, npd.value)
+
+    def stats(self):
+        u, ns, c = C.c_uint64(0), C.c_int32(0), C.c_int64(0)
+        self._scheck(lib().pa_server_stats(self.handle, C.byref(u), C.byref(ns), C.byref(c)))
+        return dict(used_bytes=u.value, slots=ns.value, completed=c.value)
+
+    def close(self):
+        if self.handle:
+            lib().pa_server_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

@@ -313,6 +313,12 @@ void pa_destroy(pa_ctx* ctx) {
   free_ctx(ctx);
 }
 
+pa_status pa_set_seed(pa_ctx* ctx, uint64_t seed) {
+  if (!ctx) return PA_EINVAL;
+  ctx->cfg.seed = seed;
+  return PA_OK;
+}
+
 pa_status pa_set_stream(pa_ctx* ctx, void* stream) {
   if (!ctx) return PA_EINVAL;
   ctx->stream = static_cast<cudaStream_t>(stream);
