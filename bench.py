@@ -306,7 +306,7 @@ def run_ours(args):
     sm_max = pk.get("sm_max_mhz", 2070.0)
     peak_gword = n_sms * 32 * sm_max * 1e6 / 1e9
     achieved_gword = nb * words / ev_avg / 1e9
-    roofline = {"bound": "alu", "kernel": "k_eval_f32 (population fitness, FP32)",
+    roofline = {"bound": "alu", "kernel": "k_eval_f32_pilot (population fitness, FP32)",
                 "achieved": achieved_gword, "peak": peak_gword, "unit": "Gword/s",
                 "frac": achieved_gword / peak_gword, "traffic": None,
                 "path": f"shared-memory gather data path: 32 x 4-byte words/clk/SM x {n_sms} "

@@ -145,7 +145,11 @@ pa_status pa_set_stream(pa_ctx* ctx, void* stream);
  * or the finite-M reading of Eq. 3).  pop_dev: device, n*L*K bytes;
  * fit_dev: device, n float32 (PA_FP32) or float64 (PA_FP64).  Rows that are
  * not permutations give an unspecified value but never an out-of-bounds
- * access.  n == 0 is a no-op.  Asynchronous.
+ * access.  n == 0 is a no-op.  Asynchronous.  The FP32 kernels stage data
+ * in shared memory with bulk copies under a bounded wait (about a second);
+ * a wait that gives up leaves the outputs unspecified and is reported as
+ * PA_ETIMEOUT by the context's next synchronous call
+ * (pa_eval_population_host, pa_solve, pa_get_population).
  */
 pa_status pa_eval_population(pa_ctx* ctx, const uint8_t* pop_dev, int64_t n, void* fit_dev);
 

@@ -255,8 +255,6 @@ pa_status pa_create(const pa_config* cfg, const double* beta, const int32_t* use
         break;
       if (!chk(cudaMalloc(&c->t32.own, sizeof(float) * LK), "cudaMalloc own")) break;
       if (!chk(cudaMalloc(&c->t32.bn, sizeof(float) * L), "cudaMalloc bn")) break;
-      if (!chk(cudaMalloc(&c->t32.err_flag, sizeof(int)), "cudaMalloc flag")) break;
-      if (!chk(cudaMemset(c->t32.err_flag, 0, sizeof(int)), "memset flag")) break;
     } else if (cfg->prec == PA_FP32) {
       int NJ, RS, vec;
       pa::f32_geometry(L, K, &NJ, &RS, &vec);
@@ -267,6 +265,10 @@ pa_status pa_create(const pa_config* cfg, const double* beta, const int32_t* use
       if (!chk(cudaMalloc(&c->t32.tab, sizeof(float) * tab_floats), "cudaMalloc tab")) break;
       if (!chk(cudaMalloc(&c->t32.own, sizeof(float) * LK), "cudaMalloc own")) break;
       if (!chk(cudaMalloc(&c->t32.bn, sizeof(float) * L), "cudaMalloc bn")) break;
+    }
+    if (cfg->prec == PA_FP32) {
+      if (!chk(cudaMalloc(&c->t32.err_flag, sizeof(int)), "cudaMalloc flag")) break;
+      if (!chk(cudaMemset(c->t32.err_flag, 0, sizeof(int)), "memset flag")) break;
     }
     if (!chk(cudaMalloc(&c->user_xy, sizeof(int32_t) * 2 * LK), "cudaMalloc user_xy")) break;
     if (!chk(cudaMalloc(&c->bs_xy, sizeof(int32_t) * 2 * L), "cudaMalloc bs_xy")) break;
@@ -328,15 +330,17 @@ pa_status pa_set_stream(pa_ctx* ctx, void* stream) {
 static cudaError_t eval_any(pa_ctx* ctx, const uint8_t* pop, int64_t n, void* fit) {
   if (ctx->cfg.prec == PA_FP64)
     return pa::launch_eval_f64(ctx, pop, n, static_cast<double*>(fit), ctx->stream);
+  ctx->wait_check = 1;
   if (ctx->t32.streamed)
     return pa::launch_eval_f32_stream(ctx, pop, n, static_cast<float*>(fit), ctx->stream);
   return pa::launch_eval_f32(ctx, pop, n, static_cast<float*>(fit), ctx->stream);
 }
 
-// A bounded device wait of an earlier kernel that gave up (column-tiled
-// evaluation): reported once, then cleared.
+// A bounded device wait of an earlier kernel that gave up (shared-memory
+// staging of the FP32 evaluations): reported once, then cleared.
 static pa_status check_timeout(pa_ctx* ctx) {
-  if (!ctx->t32.err_flag) return PA_OK;
+  if (!ctx->t32.err_flag || !ctx->wait_check) return PA_OK;
+  ctx->wait_check = 0;
   int flag = 0;
   PA_TRY(ctx, cudaMemcpy(&flag, ctx->t32.err_flag, sizeof flag, cudaMemcpyDeviceToHost),
          "read flag");
@@ -497,7 +501,7 @@ pa_status pa_solve(pa_ctx* ctx, int32_t generations, uint8_t* best_host, double*
                                 ctx->stream),
            "copy best fit");
   PA_TRY(ctx, cudaStreamSynchronize(ctx->stream), "sync");
-  return PA_OK;
+  return check_timeout(ctx);
 }
 
 pa_status pa_get_population(pa_ctx* ctx, uint8_t* pop_host, void* fit_host, int32_t* generation) {
@@ -516,7 +520,7 @@ pa_status pa_get_population(pa_ctx* ctx, uint8_t* pop_host, void* fit_host, int3
   }
   if (generation) *generation = ctx->generation;
   PA_TRY(ctx, cudaStreamSynchronize(ctx->stream), "sync");
-  return PA_OK;
+  return check_timeout(ctx);
 }
 
 pa_status pa_validate_population(pa_ctx* ctx, const uint8_t* pop_dev, int64_t n,

@@ -7,6 +7,46 @@
 
 namespace pa {
 
+// ----------------------------------------------------------------- async copies
+// Bulk global->shared copies completing on an mbarrier (TMA engine), and a
+// bounded wait on the barrier's phase.
+constexpr long long kWaitCycles = 2000000000LL;  // ~1 s at 2 GHz
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint32_t mb, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mb), "r"(count) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t mb, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb), "r"(bytes)
+               : "memory");
+}
+// dst, src 16-byte aligned, bytes a multiple of 16
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes,
+                                         uint32_t mb) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+      ::"r"(dst), "l"(src), "r"(bytes), "r"(mb)
+      : "memory");
+}
+// Wait for phase `parity` of an mbarrier; false after about a second.
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
+  const long long t0 = clock64();
+  for (;;) {
+    uint32_t done = 0;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(mbar), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (clock64() - t0 > kWaitCycles) return false;
+  }
+}
+
 // ----------------------------------------------------------------- decode
 // Pilot -> user maps of NT members: INV[(l*NT + c)*K + p] = k where member c
 // gives pilot p to user k of cell l.  Member c's row l starts at
@@ -35,27 +75,11 @@ __device__ __forceinline__ void decode_members(const uint8_t* src, int64_t membe
 }
 
 // ----------------------------------------------------------------- FP32
-// Packed two-lane FP32 arithmetic (f32x2): one instruction, two independent
-// IEEE single-precision operations, each rounded exactly as the scalar one.
-__device__ __forceinline__ unsigned long long ffma2(unsigned long long a, unsigned long long b,
-                                                    unsigned long long c) {
-  unsigned long long d;
-  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
-  return d;
-}
-__device__ __forceinline__ unsigned long long fadd2(unsigned long long a, unsigned long long b) {
-  unsigned long long d;
-  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-  return d;
-}
-__device__ __forceinline__ unsigned long long pack2(float lo, float hi) {
-  unsigned long long d;
-  asm("mov.b64 %0, {%1, %2};" : "=l"(d) : "f"(lo), "f"(hi));
-  return d;
-}
-__device__ __forceinline__ void unpack2(unsigned long long v, float& lo, float& hi) {
-  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
-}
+// Packed two-lane FP32 arithmetic (sm_100 f32x2 instructions): one
+// instruction, two independent IEEE single-precision operations, each
+// rounded exactly as the scalar one.
+__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 fadd2(float2 a, float2 b) { return __fadd2_rn(a, b); }
 
 // Read-only view of the FP32 tables staged in shared memory.
 struct F32Smem {
@@ -66,6 +90,40 @@ struct F32Smem {
   float M, pc;
   int jbase = 0;     // BS index of the table's first column (column tiles)
 };
+
+// Hardware approximations (MUFU) with subnormals flushed: the arguments here
+// are normal numbers (gains are scaled to at most 1; sums of squares of them
+// stay far above 2^-126), so flushing costs nothing and saves the fix-up
+// instructions of the non-flushing forms.
+__device__ __forceinline__ float rcp_ftz(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ float lg2_ftz(float x) {
+  float r;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
+// SE of one user from its pilot's sums at its own BS j (Eq. 4-5, or the
+// finite-M reading of Eq. 3): s2 = sum_{l != j} of squared gains, s1 = sum
+// over l != j of gains, b = own gain, bn = B_j + s2/rho (scaled).  Every FP32
+// kernel takes this exact sequence of roundings.
+template <bool FIN>
+__device__ __forceinline__ float se_pilot_f32(float s2, float s1, float b, float bn, float M,
+                                              float pc) {
+  const float b2 = b * b;
+  float num, den;
+  if (FIN) {
+    num = M * b2;
+    den = fmaf(M, s2, bn * (s1 + b + pc));
+  } else {
+    num = b2;
+    den = s2;
+  }
+  return lg2_ftz(1.f + num * rcp_ftz(den));
+}
 
 // Threads per (member, pilot) of the batch FP32 evaluation: two for float2
 // tables with at least 8 BS columns (each takes half of the columns), else one.
@@ -86,12 +144,12 @@ __device__ __forceinline__ void eval_pilot_f32(const F32Smem& s, const uint8_t* 
                                                int h, float* pair_se) {
   static_assert(NJ % (2 * JS) == 0, "NJ must split into JS shares of column pairs");
   constexpr int NP = NJ / 2 / JS;
-  unsigned long long acc2[NP];
-  unsigned long long acc1[FIN ? NP : 1];
+  float2 acc2[NP];
+  float2 acc1[FIN ? NP : 1];
 #pragma unroll
   for (int c = 0; c < NP; ++c) {
-    acc2[c] = 0ULL;
-    if (FIN) acc1[c] = 0ULL;
+    acc2[c] = make_float2(0.f, 0.f);
+    if (FIN) acc1[c] = make_float2(0.f, 0.f);
   }
   const int L = s.L, K = s.K, RS = s.RS;
   const int c0 = h * NP;
@@ -102,37 +160,27 @@ __device__ __forceinline__ void eval_pilot_f32(const F32Smem& s, const uint8_t* 
     const float* row = Tl + (l * K + u) * RS;
 #pragma unroll
     for (int c = 0; c < NP; ++c) {
-      unsigned long long v;
+      float2 v;
       if (VEC == 2)
-        v = reinterpret_cast<const unsigned long long*>(row)[c];
+        v = reinterpret_cast<const float2*>(row)[c];
       else
-        v = pack2(row[2 * c], row[2 * c + 1]);
+        v = make_float2(row[2 * c], row[2 * c + 1]);
       acc2[c] = ffma2(v, v, acc2[c]);
       if (FIN) acc1[c] = fadd2(acc1[c], v);
     }
   }
 #pragma unroll
   for (int c = 0; c < NP; ++c) {
-    float s2[2], s1[2] = {0.f, 0.f};
-    unpack2(acc2[c], s2[0], s2[1]);
-    if (FIN) unpack2(acc1[c], s1[0], s1[1]);
+    const float s2[2] = {acc2[c].x, acc2[c].y};
+    const float s1[2] = {FIN ? acc1[c].x : 0.f, FIN ? acc1[c].y : 0.f};
     float ps = 0.f;
 #pragma unroll
     for (int hh = 0; hh < 2; ++hh) {
       const int j = s.jbase + 2 * (c0 + c) + hh;
       if (j < L) {
         const int u = invp[j * stride];
-        const float b = s.OWN[j * K + u];
-        const float b2 = b * b;
-        float num, den;
-        if (FIN) {
-          num = s.M * b2;
-          den = fmaf(s.M, s2[hh], s.BN[j] * (s1[hh] + b + s.pc));
-        } else {
-          num = b2;
-          den = s2[hh];
-        }
-        ps += __log2f(1.f + __fdividef(num, den));
+        ps += se_pilot_f32<FIN>(s2[hh], s1[hh], s.OWN[j * K + u], FIN ? s.BN[j] : 0.f, s.M,
+                                s.pc);
       }
     }
     pair_se[c] = ps;
@@ -145,6 +193,18 @@ __device__ __forceinline__ void eval_pilot_f32(const F32Smem& s, const uint8_t* 
 __device__ __forceinline__ float member_sum(const float* part, int n, int lane) {
   float s = 0.f;
   for (int i = lane; i < n; i += 32) s += part[i];
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+  return s;
+}
+
+// member_sum for n <= NMAX with the loop unrolled (same additions, same order).
+template <int NMAX>
+__device__ __forceinline__ float member_sum_bounded(const float* part, int n, int lane) {
+  float s = 0.f;
+#pragma unroll
+  for (int i0 = 0; i0 < NMAX; i0 += 32)
+    if (i0 + lane < n) s += part[i0 + lane];
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
   return s;

@@ -95,6 +95,195 @@ __global__ void __launch_bounds__(512) k_eval_f32(const F32Args a) {
   }
 }
 
+// ------------------------------------------------------- FP32, K <= 16, L <= 24
+// One thread per (member c, pilot p) over all NJ BS columns, so that the
+// accumulators stay in registers and each table word is read by one thread.
+// Per tile of NT members:
+//   * the tile's chromosome bytes (contiguous, NT*L*K bytes, a multiple of 16)
+//     arrive in shared memory by one bulk copy on an mbarrier, issued two
+//     tiles ahead (double buffer);
+//   * decode: one thread per (member, cell) row writes the row's inverse
+//     transposed, INVT[(c*K + p)*NJ + l] = user of cell l holding pilot p, so
+//     that thread (c, p) finds its users at consecutive bytes;
+//   * accumulate: the same per-column ascending-l sums, SINR and SE steps as
+//     eval_pilot_f32, so every per-(pilot, pair) SE and every fitness is bit
+//     for bit the one the other FP32 kernels compute.
+// Partial tiles, or a population not 16-byte aligned, are decoded straight
+// from global memory instead.
+constexpr int kPilotThreads = 256;
+
+struct PilotArgs {
+  const uint8_t* pop;
+  int64_t n;
+  float* fit;
+  const float* tab;
+  const float* own;
+  const float* bn;
+  int* err_flag;  // null: no bulk copies (decode from global memory)
+  int L, K, RS, NT;
+  int64_t tab_floats;
+  int xbytes;     // shared bytes of one chromosome buffer
+  float M, pc;
+};
+
+template <int NJ, bool FIN>
+__global__ void __launch_bounds__(kPilotThreads, 4) k_eval_f32_pilot(const PilotArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ __align__(8) uint64_t mbar[2];
+  __shared__ int s_timeout;
+  constexpr int NPAIR = NJ / 2;
+  const int L = a.L, K = a.K, NT = a.NT, NTK = NT * K, LK = L * K;
+  float* T = reinterpret_cast<float*>(smem);
+  float* OWN = T + a.tab_floats;
+  float* BN = OWN + ((LK + 3) & ~3);
+  float* PART = BN + ((L + 3) & ~3);
+  uint8_t* INVT = reinterpret_cast<uint8_t*>(PART + (((int64_t)NTK * NPAIR + 3) & ~3));
+  uint8_t* X0 = INVT + ((NTK * NJ + 15) & ~15);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int64_t tiles = (a.n + NT - 1) / NT;
+  const uint32_t tile_bytes = (uint32_t)NT * (uint32_t)LK;
+  const bool bulk = a.err_flag != nullptr && (reinterpret_cast<uintptr_t>(a.pop) & 15) == 0 &&
+                    (tile_bytes & 15) == 0;
+  auto full = [&](int64_t tile) { return (tile + 1) * NT <= a.n; };
+  const uint32_t mb0 = smem_u32(&mbar[0]);
+  auto issue = [&](int64_t tile, int buf) {
+    if (tid == 0 && bulk && tile < tiles && full(tile)) {
+      const uint32_t mb = mb0 + 8 * buf;
+      mbar_expect_tx(mb, tile_bytes);
+      bulk_g2s(smem_u32(X0 + buf * a.xbytes), a.pop + tile * (int64_t)tile_bytes, tile_bytes, mb);
+    }
+  };
+
+  if (tid == 0) {
+    mbar_init(mb0, 1);
+    mbar_init(mb0 + 8, 1);
+    s_timeout = 0;
+  }
+  {
+    const float4* s4 = reinterpret_cast<const float4*>(a.tab);
+    float4* d4 = reinterpret_cast<float4*>(T);
+    for (int64_t i = tid; i < a.tab_floats / 4; i += blockDim.x) d4[i] = __ldg(s4 + i);
+    for (int i = tid; i < LK; i += blockDim.x) OWN[i] = __ldg(a.own + i);
+    if (FIN)
+      for (int i = tid; i < L; i += blockDim.x) BN[i] = __ldg(a.bn + i);
+    // every byte decode may skip (a pilot >= K) still names a valid user
+    for (int i = tid; i < NTK * NJ / 4; i += blockDim.x) reinterpret_cast<uint32_t*>(INVT)[i] = 0;
+  }
+  __syncthreads();
+  issue(blockIdx.x, 0);
+  issue(blockIdx.x + (int64_t)gridDim.x, 1);
+
+  const int c_me = tid / K;
+  const int KRS = K * a.RS;
+  const uint8_t* inv_me = INVT + tid * NJ;
+  uint32_t parity = 0;  // bit b: phase of buffer b's next completion
+  int i = 0;
+  for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x, ++i) {
+    const int buf = i & 1;
+    const int64_t n0 = tile * NT;
+    const int nvalid = (int)((a.n - n0) < NT ? (a.n - n0) : NT);
+    const bool staged = bulk && full(tile);
+    const uint8_t* xs = X0 + buf * a.xbytes;
+    if (staged) {
+      const uint32_t mb = mb0 + 8 * buf, ph = (parity >> buf) & 1;
+      if (tid == 0 && !mbar_wait(mb, ph)) {
+        atomicExch(a.err_flag, 1);
+        // let this copy and the other buffer's (if any) land before leaving
+        mbar_wait(mb, ph);
+        if (tile + gridDim.x < tiles && full(tile + gridDim.x))
+          mbar_wait(mb0 + 8 * (buf ^ 1), (parity >> (buf ^ 1)) & 1);
+        s_timeout = 1;
+      }
+      __syncthreads();
+      if (s_timeout) return;
+      mbar_wait(mb, ph);  // complete: returns at once, orders the copied bytes
+      parity ^= 1u << buf;
+    }
+
+    // ---- decode: INVT[(c*K + p)*NJ + l] = k where row (c, l) gives pilot p to
+    // user k; one thread per row, cells fastest (a warp's byte stores then
+    // share words or fall in distinct banks)
+    for (int r = tid; r < nvalid * L; r += blockDim.x) {
+      const int c = r / L, l = r - c * L;
+      const int o = c * LK + l * K;
+      uint8_t* dst = INVT + c * K * NJ + l;
+      if (staged) {
+        // the row's K <= 16 bytes, realigned from the words that hold them
+        const uint32_t* w = reinterpret_cast<const uint32_t*>(xs + (o & ~3));
+        const uint32_t sh = 8 * (o & 3);
+        uint32_t rw[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) rw[q] = __funnelshift_r(w[q], w[q + 1], sh);
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+          const uint32_t p = (rw[k >> 2] >> (8 * (k & 3))) & 0xffu;
+          if (k < K && p < (uint32_t)K) dst[p * NJ] = (uint8_t)k;
+        }
+      } else {
+        const uint8_t* row = a.pop + n0 * LK + o;
+        for (int k = 0; k < K; ++k) {
+          const uint32_t p = __ldg(row + k);
+          if (p < (uint32_t)K) dst[p * NJ] = (uint8_t)k;
+        }
+      }
+    }
+    __syncthreads();
+    issue(tile + 2 * (int64_t)gridDim.x, buf);
+
+    // ---- accumulate over cells, then SINR / SE per BS column
+    if (c_me < nvalid) {
+      float2 acc2[NPAIR];
+      float2 acc1[FIN ? NPAIR : 1];
+#pragma unroll
+      for (int q = 0; q < NPAIR; ++q) {
+        acc2[q] = make_float2(0.f, 0.f);
+        if (FIN) acc1[q] = make_float2(0.f, 0.f);
+      }
+      const float* Tl = T;
+      const uint32_t* iw = reinterpret_cast<const uint32_t*>(inv_me);
+      uint32_t w = 0;
+#pragma unroll 4
+      for (int l = 0; l < L; ++l, Tl += KRS) {
+        if ((l & 3) == 0) w = iw[l >> 2];  // users of cells l .. l+3
+        const int u = (w >> (8 * (l & 3))) & 0xffu;
+        const float2* row = reinterpret_cast<const float2*>(Tl + u * a.RS);
+#pragma unroll
+        for (int q = 0; q < NPAIR; ++q) {
+          const float2 v = row[q];
+          acc2[q] = ffma2(v, v, acc2[q]);
+          if (FIN) acc1[q] = fadd2(acc1[q], v);
+        }
+      }
+      float ps[NPAIR];
+      uint32_t uw = 0;
+#pragma unroll
+      for (int q = 0; q < NPAIR; ++q) {
+        if ((q & 1) == 0) uw = iw[q >> 1];  // users of cells 2q .. 2q+3
+        const float s2[2] = {acc2[q].x, acc2[q].y};
+        const float s1[2] = {FIN ? acc1[q].x : 0.f, FIN ? acc1[q].y : 0.f};
+        float pse = 0.f;
+#pragma unroll
+        for (int hh = 0; hh < 2; ++hh) {
+          const int j = 2 * q + hh;
+          if (j < L)
+            pse += se_pilot_f32<FIN>(s2[hh], s1[hh], OWN[j * K + ((uw >> (8 * (j & 3))) & 0xff)],
+                                     FIN ? BN[j] : 0.f, a.M, a.pc);
+        }
+        ps[q] = pse;
+      }
+      float2* dst = reinterpret_cast<float2*>(PART + tid * NPAIR);
+#pragma unroll
+      for (int q = 0; q < NPAIR / 2; ++q) dst[q] = make_float2(ps[2 * q], ps[2 * q + 1]);
+    }
+    __syncthreads();
+    float* fit = a.fit + n0;
+    for (int c = warp; c < nvalid; c += kPilotThreads / 32) {
+      const float f = member_sum_bounded<16 * NPAIR>(PART + c * K * NPAIR, K * NPAIR, lane);
+      if (lane == 0) fit[c] = f;
+    }
+  }
+}
+
 // --------------------------------------------------------------------- FP64
 struct F64Args {
   const uint8_t* pop;
@@ -227,6 +416,57 @@ cudaError_t run_f32(const F32Args& a, const F32Launch& s, int num_sms, cudaStrea
   return cudaGetLastError();
 }
 
+// Block shape of k_eval_f32_pilot: NT members (NT*L*K a multiple of 16 so
+// that a full tile is one bulk copy), one thread per (member, pilot).
+struct PilotLaunch {
+  int NT, xbytes;
+  size_t smem;
+};
+PilotLaunch pilot_shape(int L, int K, int RS, int NJ) {
+  PilotLaunch s{};
+  const int LK = L * K;
+  int g = 16;
+  while (LK % g) g >>= 1;
+  const int m = 16 / g;
+  s.NT = std::max(m, (kPilotThreads / K) / m * m);
+  s.xbytes = (s.NT * LK + 20 + 15) & ~15;  // +20: a row reads up to 5 words from its first
+  const size_t tab = (((size_t)LK * RS + 3) / 4) * 4;
+  const size_t NTK = (size_t)s.NT * K;
+  s.smem = 4 * (tab + ((LK + 3) & ~size_t(3)) + ((L + 3) & ~3) + ((NTK * (NJ / 2) + 3) & ~size_t(3))) +
+           ((NTK * NJ + 15) & ~size_t(15)) + 2 * (size_t)s.xbytes;
+  return s;
+}
+
+bool pilot_kernel_applies(int NJ, int vec, int K) { return vec == 2 && NJ <= 24 && K <= 16; }
+
+template <int NJ, bool FIN>
+cudaError_t run_pilot(const PilotArgs& a, const PilotLaunch& s, int num_sms, cudaStream_t st) {
+  auto kern = k_eval_f32_pilot<NJ, FIN>;
+  cudaError_t e = cudaSuccess;
+  const int per_sm = cached_occupancy((const void*)kern, kPilotThreads, s.smem, &e);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  const int64_t tiles = (a.n + a.NT - 1) / a.NT;
+  const int64_t grid = std::min<int64_t>(tiles, (int64_t)per_sm * num_sms);
+  (void)cudaGetLastError();  // drop a stale error of an earlier call
+  kern<<<(unsigned)grid, kPilotThreads, s.smem, st>>>(a);
+  count_launch();
+  return cudaGetLastError();
+}
+
+template <bool FIN>
+cudaError_t pick_pilot(int NJ, const PilotArgs& a, const PilotLaunch& s, int sms, cudaStream_t st) {
+  switch (NJ) {
+    case 4: return run_pilot<4, FIN>(a, s, sms, st);
+    case 8: return run_pilot<8, FIN>(a, s, sms, st);
+    case 12: return run_pilot<12, FIN>(a, s, sms, st);
+    case 16: return run_pilot<16, FIN>(a, s, sms, st);
+    case 20: return run_pilot<20, FIN>(a, s, sms, st);
+    case 24: return run_pilot<24, FIN>(a, s, sms, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 template <int VEC, bool FIN>
 cudaError_t pick_nj(int NJ, const F32Args& a, const F32Launch& s, int sms, cudaStream_t st) {
   switch (NJ) {
@@ -259,9 +499,10 @@ bool f32_supported(int L, int K, size_t* smem_bytes) {
   int NJ, RS, vec;
   f32_geometry(L, K, &NJ, &RS, &vec);
   if (NJ > kMaxNJ || K > kMaxK) return false;
-  const F32Launch s = f32_shape(L, K, RS, NJ);
-  if (smem_bytes) *smem_bytes = s.smem;
-  return s.smem <= (size_t)kSmemBudget;
+  const size_t smem = pilot_kernel_applies(NJ, vec, K) ? pilot_shape(L, K, RS, NJ).smem
+                                                       : f32_shape(L, K, RS, NJ).smem;
+  if (smem_bytes) *smem_bytes = smem;
+  return smem <= (size_t)kSmemBudget;
 }
 
 cudaError_t launch_eval_f32(const pa_ctx* ctx, const uint8_t* pop, int64_t n, float* fit,
@@ -269,6 +510,28 @@ cudaError_t launch_eval_f32(const pa_ctx* ctx, const uint8_t* pop, int64_t n, fl
   if (n <= 0) return cudaSuccess;
   const pa::F32Tables& t = ctx->t32;
   const int L = ctx->cfg.L, K = ctx->cfg.K;
+  const bool fin = ctx->cfg.mode == PA_SINR_FINITE_M;
+  if (pilot_kernel_applies(t.NJ, t.vec, K)) {
+    const PilotLaunch s = pilot_shape(L, K, t.RS, t.NJ);
+    PilotArgs a;
+    a.pop = pop;
+    a.n = n;
+    a.fit = fit;
+    a.tab = t.tab;
+    a.own = t.own;
+    a.bn = t.bn;
+    a.err_flag = t.err_flag;
+    a.L = L;
+    a.K = K;
+    a.RS = t.RS;
+    a.NT = s.NT;
+    a.tab_floats = (((int64_t)L * K * t.RS + 3) / 4) * 4;
+    a.xbytes = s.xbytes;
+    a.M = t.M;
+    a.pc = t.pc;
+    return fin ? pick_pilot<true>(t.NJ, a, s, ctx->num_sms, st)
+               : pick_pilot<false>(t.NJ, a, s, ctx->num_sms, st);
+  }
   const F32Launch s = f32_shape(L, K, t.RS, t.NJ);
   F32Args a;
   a.pop = pop;
@@ -285,7 +548,6 @@ cudaError_t launch_eval_f32(const pa_ctx* ctx, const uint8_t* pop, int64_t n, fl
   a.tab_floats = (((int64_t)L * K * t.RS + 3) / 4) * 4;
   a.M = t.M;
   a.pc = t.pc;
-  const bool fin = ctx->cfg.mode == PA_SINR_FINITE_M;
   if (t.vec == 2)
     return fin ? pick_nj<2, true>(t.NJ, a, s, ctx->num_sms, st)
                : pick_nj<2, false>(t.NJ, a, s, ctx->num_sms, st);

@@ -67,6 +67,7 @@ struct pa_ctx {
   void* fit = nullptr;         // [N] float or double
   int32_t generation = 0;
   int solve_C = -1;            // cluster size of the fused solve kernel (-1: not chosen, 0: none)
+  int wait_check = 0;          // an FP32 evaluation ran since t32.err_flag was last read
   // scratch
   int64_t* scratch_i64 = nullptr;  // small device scratch (flags, argbest)
   uint8_t* best_row = nullptr;     // [L*K]

@@ -34,32 +34,11 @@ struct StreamArgs {
 };
 
 constexpr int kStreamThreads = 512;
-constexpr long long kWaitCycles = 2000000000LL;  // ~1 s at 2 GHz
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-// Bounded wait for phase `parity` of an mbarrier; false on timeout.
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
-  const long long t0 = clock64();
-  for (;;) {
-    uint32_t done = 0;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-        " selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(done)
-        : "r"(mbar), "r"(parity)
-        : "memory");
-    if (done) return true;
-    if (clock64() - t0 > kWaitCycles) return false;
-  }
-}
-
 template <int JT, int VEC, bool FIN>
 __global__ void __launch_bounds__(kStreamThreads) k_eval_f32_stream(const StreamArgs a) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ __align__(8) uint64_t mbar;
+  __shared__ int s_timeout;
   const int L = a.L, K = a.K, LK = L * K, NTM = a.NTM, NTK = NTM * K;
   constexpr int NPR = JT / 2;
   float* TT = reinterpret_cast<float*>(smem);
@@ -74,35 +53,34 @@ __global__ void __launch_bounds__(kStreamThreads) k_eval_f32_stream(const Stream
   // ---- stage tile t with bulk copies (one thread issues, all wait)
   const uint32_t mb = smem_u32(&mbar);
   if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb) : "memory");
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    mbar_init(mb, 1);
+    s_timeout = 0;
   }
   __syncthreads();
   const uint32_t bytes = (uint32_t)(a.tile_floats * 4);
   if (tid == 0) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb), "r"(bytes)
-                 : "memory");
+    mbar_expect_tx(mb, bytes);
     const char* src = reinterpret_cast<const char*>(a.tab + (int64_t)t * a.tile_floats);
     const uint32_t dst = smem_u32(TT);
     constexpr uint32_t kChunk = 32768;
     for (uint32_t off = 0; off < bytes; off += kChunk) {
       const uint32_t sz = bytes - off < kChunk ? bytes - off : kChunk;
-      asm volatile(
-          "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-          ::"r"(dst + off), "l"(src + off), "r"(sz), "r"(mb)
-          : "memory");
+      bulk_g2s(dst + off, src + off, sz, mb);
     }
   }
   for (int i = tid; i < LK; i += blockDim.x) OWN[i] = __ldg(a.own + i);
   if (FIN)
     for (int i = tid; i < L; i += blockDim.x) BN[i] = __ldg(a.bn + i);
   for (int i = tid; i < L * NTK; i += blockDim.x) INV[i] = 0;
-  if (!mbar_wait(mb, 0)) {
-    if (tid == 0) atomicExch(a.err_flag, 1);
+  // one thread waits (bounded) and the block leaves together on a timeout
+  if (tid == 0 && !mbar_wait(mb, 0)) {
+    atomicExch(a.err_flag, 1);
     mbar_wait(mb, 0);  // give the copy another bounded chance to land before leaving
-    return;
+    s_timeout = 1;
   }
   __syncthreads();
+  if (s_timeout) return;
+  mbar_wait(mb, 0);  // phase complete: returns at once, orders the copied data
   F32Smem sm{TT, OWN, BN, L, K, a.RSt, a.M, a.pc};
   sm.jbase = t * JT;
 

@@ -109,6 +109,35 @@ def test_fp32_large_batch_sampled(B, oracle):
             B.pa_destroy(ctx)
 
 
+@pytest.mark.parametrize("L,K", [(19, 10), (7, 4), (24, 16), (13, 3), (5, 16), (3, 1)])
+def test_fp32_staged_and_direct_decode_agree(B, oracle, L, K):
+    """The per-pilot FP32 kernel takes full member tiles into shared memory
+    by bulk copies and decodes partial tiles (or a population that is not
+    16-byte aligned) straight from global memory: both routes give the same
+    bits, for tile counts that leave ragged tails, and match the oracle."""
+    rings_L = 7 if L <= 7 else (19 if L <= 19 else 37)
+    inst = inputs.instance(rings_L, K, seed=L + 5 * K, dtype=np.float32)
+    beta = np.ascontiguousarray(inst["beta"][:L, :L, :])
+    for mode in (0, 1):
+        cfg = _cfg(B, L, K, B.PA_FP32, mode)
+        ctx = B.pa_create(cfg, beta)
+        try:
+            for n in (1, 23, 24, 25, 97, 4099):
+                pop_np = inputs.random_population(n, L, K, seed=n + L)
+                aligned = _eval(B, ctx, pop_np, B.PA_FP32)
+                raw = torch.zeros(n * L * K + 16, dtype=torch.uint8, device="cuda")
+                view = raw[1:1 + n * L * K].view(n, L, K)
+                view.copy_(torch.from_numpy(pop_np).cuda())
+                fit = torch.empty(n, dtype=torch.float32, device="cuda")
+                B.pa_eval_population(ctx, view, fit)
+                torch.cuda.synchronize()
+                assert (fit.cpu().numpy().astype(np.float64) == aligned).all()
+                ref = oracle.fitness_batch(beta, pop_np, _sp(oracle, cfg))
+                assert (np.abs(aligned - ref) / np.abs(ref)).max() <= F32_RTOL
+        finally:
+            B.pa_destroy(ctx)
+
+
 def test_eval_edge_cases(B, oracle):
     L, K = 7, 4
     inst = inputs.instance(L, K, seed=5)
