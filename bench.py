@@ -343,7 +343,11 @@ def run_ours(args):
     if not args.no_batched:
         line["batched_c3"] = run_batched(B, inputs)
         line["streamed_c5"] = run_streamed(B, inputs, dev)
-        line["serving_c4"] = run_serving(B, inputs, seconds=args.serve_seconds)
+        line["serving_c4"] = run_serving(B, inputs, seconds=args.serve_seconds,
+                                         tick=args.serve_tick)
+        # twice the rate: beyond what one solve at a time can sustain
+        line["serving_c4"]["overload_4000_per_s"] = run_serving(
+            B, inputs, rate=4000.0, seconds=max(0.5, args.serve_seconds / 2), tick=args.serve_tick)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
     ctx.close()
@@ -461,7 +465,7 @@ def run_streamed(B, inputs, dev, n=1 << 17, reps=5):
             "sampled_max_rel_err_vs_oracle": float(np.max(np.abs(got - ref) / ref))}
 
 
-def run_serving(B, inputs, rate=2000.0, seconds=2.0, G=40, N=64, tick=10, budget=40 << 30):
+def run_serving(B, inputs, rate=2000.0, seconds=2.0, G=40, N=64, tick=20, budget=40 << 30):
     """Poisson arrivals (rate per second for `seconds`), each request a solve
     of a fresh seeded instance with L in {7, 19}, K in {8, 16} (tau_p = K,
     M = 256, finite-M SINR, N = 64, G = 40, FP32 beta).  Served: the
@@ -584,6 +588,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--serve-tick", type=int, default=20,
+                    help="generations per scheduling tick of the serving comparison")
     ap.add_argument("--serve-seconds", type=float, default=2.0,
                     help="length of the Poisson arrival window of the serving comparison")
     ap.add_argument("--no-batched", action="store_true",

@@ -44,6 +44,7 @@ struct pa_batch {
   std::vector<Group> groups;
   void* d_seed_args = nullptr;
   size_t seed_smem = 0;
+  int seed_C = 1;  // cluster size of the batched seeding launch
   int* d_counters = nullptr;
   uint8_t* d_best = nullptr;
   double* d_bestfit = nullptr;
@@ -136,7 +137,8 @@ pa_status run_groups(pa_batch* b, cudaStream_t st) {
   pa_status s = bcuda(b, cudaMemsetAsync(b->d_counters, 0, sizeof(int) * b->groups.size(), st),
                       "reset counters");
   if (s != PA_OK) return s;
-  s = bcuda(b, pa::launch_seed_batch(b->d_seed_args, b->n, b->seed_smem, st), "seed kernel");
+  s = bcuda(b, pa::launch_seed_batch(b->d_seed_args, b->n, b->seed_smem, b->seed_C, st),
+            "seed kernel");
   if (s != PA_OK) return s;
   s = bcuda(b, cudaEventRecord(b->fork, st), "fork");
   if (s != PA_OK) return s;
@@ -233,12 +235,15 @@ pa_status pa_batch_create(int32_t n, const pa_config* cfgs, const double* const*
   if (st == PA_OK) {
     const size_t sb = pa::seed_args_bytes();
     std::vector<unsigned char> h(sb * n);
+    b->seed_C = pa::seed_batch_cluster(n);
     for (int i = 0; i < n; ++i)
-      b->seed_smem = std::max(b->seed_smem, pa::seed_fill_args(b->ctx[i], h.data() + sb * i));
+      b->seed_smem =
+          std::max(b->seed_smem, pa::seed_fill_args(b->ctx[i], h.data() + sb * i, b->seed_C));
     if (chk(cudaMalloc(&b->d_seed_args, h.size()), "cudaMalloc seed args"))
       chk(cudaMemcpy(b->d_seed_args, h.data(), h.size(), cudaMemcpyHostToDevice), "copy seed args");
     // one seeding pass now: prepares the kernel outside any later capture
-    if (st == PA_OK) chk(pa::launch_seed_batch(b->d_seed_args, n, b->seed_smem, b->stream), "seed");
+    if (st == PA_OK)
+      chk(pa::launch_seed_batch(b->d_seed_args, n, b->seed_smem, b->seed_C, b->stream), "seed");
     if (st == PA_OK) chk(cudaStreamSynchronize(b->stream), "seed sync");
   }
   for (auto& g : b->groups) {
@@ -289,7 +294,9 @@ pa_status pa_batch_load(pa_batch* b, int32_t i, const double* beta, const int32_
 pa_status pa_batch_tune(pa_batch* b, int32_t generations, int32_t* chosen) {
   if (!b) return PA_EINVAL;
   if (generations < 1) return bfail(b, PA_EINVAL, "generations must be >= 1");
-  pa_status st = bcuda(b, pa::launch_seed_batch(b->d_seed_args, b->n, b->seed_smem, b->stream),
+  pa_status st = bcuda(b,
+                       pa::launch_seed_batch(b->d_seed_args, b->n, b->seed_smem, b->seed_C,
+                                             b->stream),
                        "seed kernel");
   if (st != PA_OK) return st;
   cudaEvent_t e0, e1;

@@ -16,7 +16,8 @@
 //                 row a permutation), else a copy of a; then for each row l,
 //                 with draw 2t+2+3l < pm_thresh, swap two distinct positions
 //                 chosen by draws 2t+3+3l and 2t+4+3l.
-// Seeding (single block):
+// Seeding (a cluster of blocks per instance, cells split among them; one
+// block per instance when instances are seeded in a batch):
 //   Lloyd's K-means on the users' positions relative to their own BS
 //   (integer mm; exact int64 centroid sums, one FP64 division; nearest
 //   centroid with ties to the lower index; an empty cluster keeps its
@@ -26,11 +27,15 @@
 //   take the free pilots in ascending order.  Member 0 = A*, members
 //   1..n_seeded-1 = A* with each row swapped with probability 1/2, the rest
 //   uniformly random rows (Fisher-Yates).
+#include <cooperative_groups.h>
+
 #include <algorithm>
 #include <atomic>
 #include <cstring>
 
 #include "pa_internal.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace pa {
 namespace {
@@ -200,33 +205,87 @@ __device__ void random_row(uint8_t* row, int K, DrawStream& ds, uint32_t first) 
   }
 }
 
-constexpr int kSeedThreads = 1024;
-constexpr int kMaxU = 64 * 64;  // users handled by the single-block K-means
+constexpr int kSeedClusterThreads = 256;  // per CTA of a seeding cluster
 
-__device__ __forceinline__ void seed_body(const SeedArgs& a, unsigned char* smem, int& changed) {
+// Shared scalars of a seeding block.
+struct SeedShared {
+  int changed[2];  // K-means: some label changed, by iteration parity (cluster-wide OR)
+  int chg_local;   // some label of this block's users changed
+};
+
+// Distances of one (user, centroid) pair per thread when the block's
+// user x centroid table fits in this many bytes of shared memory.
+constexpr int kSeedDistBytes = 32 * 1024;
+
+// K-means seeding (Sec. 3.3) of one instance by a cluster of C blocks
+// (C == 1: one block).  Block `rank` owns cells l with l % C == rank: it
+// assigns their users, builds their A* rows and writes their rows of every
+// member.  Centroid sums are integers (features are integer millimetres),
+// so adding the blocks' partial sums in any order gives the oracle's sums:
+// every block adds its partial sums into every block's totals (distributed
+// shared memory atomics), and after one cluster barrier per iteration each
+// block divides its own totals -- the same operands, so the same centroids
+// everywhere.  Totals and change flags are double-buffered by iteration
+// parity: a buffer is cleared one iteration after it was read.
+__device__ __forceinline__ void seed_body(const SeedArgs& a, unsigned char* smem, SeedShared& sh,
+                                          int rank, int C, cg::cluster_group& cluster) {
   const int L = a.L, K = a.K, U = L * K, kk = a.kk;
-  const int64_t LK = U;
+  const int tid = threadIdx.x, nthr = blockDim.x;
   double* cx = reinterpret_cast<double*>(smem);
   double* cy = cx + kk;
-  unsigned long long* sx = reinterpret_cast<unsigned long long*>(cy + kk);
-  unsigned long long* sy = sx + kk;
-  int* cnt = reinterpret_cast<int*>(sy + kk);
-  int* label = cnt + kk;         // [U]
+  unsigned long long* sx = reinterpret_cast<unsigned long long*>(cy + kk);  // totals [2][kk]
+  unsigned long long* sy = sx + 2 * kk;
+  unsigned long long* sn = sy + 2 * kk;
+  unsigned long long* px = sn + 2 * kk;  // this block's partial sums [kk]
+  unsigned long long* py = px + kk;
+  unsigned long long* pn = py + kk;
+  int* label = reinterpret_cast<int*>(pn + kk);  // [U] (this block's users)
   int* idx = label + U;          // [U] scratch for the initial shuffle
   int32_t* feat = idx + U;       // [U][2] position relative to the own BS
-  uint8_t* astar = reinterpret_cast<uint8_t*>(feat + 2 * U);  // [U]
+  uint8_t* astar = reinterpret_cast<uint8_t*>(feat + 2 * U);  // [U] (this block's cells)
+  uint8_t* rows_scratch = astar + ((U + 15) & ~15);          // [nthr][K]
+  double* D = reinterpret_cast<double*>(rows_scratch + ((nthr * K + 15) & ~15));  // [nuser][kk]
   const bool kmeans = a.user_xy != nullptr && a.n_seeded > 0;
+  // this block's cells: rank, rank + C, ...; its users are those cells' users
+  const int ncell = rank < L ? (L - 1 - rank) / C + 1 : 0;
+  const int nuser = ncell * K;
+  auto user_of = [&](int i) { return (rank + (i / K) * C) * K + (i % K); };
+  const bool pair_threads = (int64_t)nuser * kk * 8 <= kSeedDistBytes;
+  // an address in block r's shared memory (this block's own without a cluster)
+  auto at_rank = [&](unsigned long long* p, int r) { return C > 1 ? cluster.map_shared_rank(p, r) : p; };
+  auto sync_all = [&]() {
+    if (C > 1)
+      cluster.sync();
+    else
+      __syncthreads();
+  };
 
   if (kmeans) {
-    for (int u = threadIdx.x; u < U; u += blockDim.x) {
+    for (int u = tid; u < U; u += nthr) {
       idx[u] = u;
       label[u] = -1;
       const int l = u / K;
       feat[2 * u] = a.user_xy[2 * u] - a.bs_xy[2 * l];
       feat[2 * u + 1] = a.user_xy[2 * u + 1] - a.bs_xy[2 * l + 1];
     }
+    for (int c = tid; c < 2 * kk; c += nthr) {
+      sx[c] = 0;
+      sy[c] = 0;
+      sn[c] = 0;
+    }
+    for (int c = tid; c < kk; c += nthr) {
+      px[c] = 0;
+      py[c] = 0;
+      pn[c] = 0;
+    }
+    if (tid == 0) {
+      sh.changed[0] = 0;
+      sh.changed[1] = 0;
+    }
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (tid == 0) {
+      // initial centroids: kk distinct users by a partial Fisher-Yates
+      // shuffle (every block draws the same ones)
       DrawStream ds(a.seed, 0, 0, kTagKmeans);
       for (int i = 0; i < kk; ++i) {
         const int j = i + (int)below(ds.draw((uint32_t)i), (uint32_t)(U - i));
@@ -237,49 +296,91 @@ __device__ __forceinline__ void seed_body(const SeedArgs& a, unsigned char* smem
         cy[i] = (double)feat[2 * idx[i] + 1];
       }
     }
-    __syncthreads();
+    sync_all();  // every block's totals and flags cleared before any remote add
     for (int it = 0; it < a.max_iter; ++it) {
-      if (threadIdx.x == 0) changed = 0;
-      __syncthreads();
-      for (int u = threadIdx.x; u < U; u += blockDim.x) {
+      const int b = it & 1;
+      unsigned long long* tx = sx + b * kk;
+      unsigned long long* ty = sy + b * kk;
+      unsigned long long* tn = sn + b * kk;
+      if (tid == 0) sh.chg_local = 0;
+      __syncthreads();  // the previous iteration's clears are done
+      // ---- assignment of this block's users (nearest centroid, ties to the lower index)
+      if (pair_threads) {
+        for (int t = tid; t < nuser * kk; t += nthr) {
+          const int i = t / kk, c = t - i * kk, u = user_of(i);
+          D[t] = dist2(feat[2 * u], feat[2 * u + 1], cx[c], cy[c]);
+        }
+        __syncthreads();
+      }
+      for (int i = tid; i < nuser; i += nthr) {
+        const int u = user_of(i);
         const int32_t fx = feat[2 * u], fy = feat[2 * u + 1];
         int best = 0;
-        double bd = dist2(fx, fy, cx[0], cy[0]);
-        for (int c = 1; c < kk; ++c) {
-          const double d = dist2(fx, fy, cx[c], cy[c]);
-          if (d < bd) {
-            bd = d;
-            best = c;
+        double bd;
+        if (pair_threads) {
+          const double* d = D + i * kk;
+          bd = d[0];
+          for (int c = 1; c < kk; ++c)
+            if (d[c] < bd) {
+              bd = d[c];
+              best = c;
+            }
+        } else {
+          bd = dist2(fx, fy, cx[0], cy[0]);
+          for (int c = 1; c < kk; ++c) {
+            const double d = dist2(fx, fy, cx[c], cy[c]);
+            if (d < bd) {
+              bd = d;
+              best = c;
+            }
           }
         }
-        if (label[u] != best) changed = 1;
+        if (label[u] != best) sh.chg_local = 1;
         label[u] = best;
+        atomicAdd(&px[best], (unsigned long long)(long long)fx);
+        atomicAdd(&py[best], (unsigned long long)(long long)fy);
+        atomicAdd(&pn[best], 1ULL);
       }
       __syncthreads();
-      if (changed == 0 || it == a.max_iter - 1) break;
-      for (int c = threadIdx.x; c < kk; c += blockDim.x) {
-        sx[c] = 0;
-        sy[c] = 0;
-        cnt[c] = 0;
-      }
-      __syncthreads();
-      for (int u = threadIdx.x; u < U; u += blockDim.x) {
-        const int c = label[u];
-        atomicAdd(&sx[c], (unsigned long long)(long long)feat[2 * u]);
-        atomicAdd(&sy[c], (unsigned long long)(long long)feat[2 * u + 1]);
-        atomicAdd(&cnt[c], 1);
-      }
-      __syncthreads();
-      for (int c = threadIdx.x; c < kk; c += blockDim.x) {
-        if (cnt[c] > 0) {
-          cx[c] = __ddiv_rn((double)(long long)sx[c], (double)cnt[c]);
-          cy[c] = __ddiv_rn((double)(long long)sy[c], (double)cnt[c]);
+      // this block's partial sums go into every block's parity-b totals
+      for (int t = tid; t < C * kk; t += nthr) {
+        const int r = t / kk, c = t - r * kk;
+        if (pn[c]) {
+          atomicAdd(at_rank(&tx[c], r), px[c]);
+          atomicAdd(at_rank(&ty[c], r), py[c]);
+          atomicAdd(at_rank(&tn[c], r), pn[c]);
         }
       }
+      if (tid == 0 && sh.chg_local)
+        for (int r = 0; r < C; ++r)
+          atomicOr(C > 1 ? cluster.map_shared_rank(&sh.changed[b], r) : &sh.changed[b], 1);
+      sync_all();
+      const bool done = sh.changed[b] == 0 || it == a.max_iter - 1;
+      if (!done)  // x and y coordinates by different threads
+        for (int t = tid; t < 2 * kk; t += nthr) {
+          const int c = t < kk ? t : t - kk;
+          if (tn[c] > 0) {
+            const double num = (double)(long long)(t < kk ? tx[c] : ty[c]);
+            (t < kk ? cx : cy)[c] = __ddiv_rn(num, (double)(long long)tn[c]);
+          }
+        }
       __syncthreads();
+      // clear the parity-b totals and flag (read above; the next remote adds
+      // to them come after the next barrier) and the partial sums
+      for (int c = tid; c < kk; c += nthr) {
+        tx[c] = 0;
+        ty[c] = 0;
+        tn[c] = 0;
+        px[c] = 0;
+        py[c] = 0;
+        pn[c] = 0;
+      }
+      if (tid == 0) sh.changed[b] = 0;
+      if (done) break;
     }
-    // A*: one thread per cell
-    for (int l = threadIdx.x; l < L; l += blockDim.x) {
+    // A*: one thread per cell of this block
+    for (int j = tid; j < ncell; j += nthr) {
+      const int l = rank + j * C;
       int order[kMaxK];
       double dist[kMaxK];
       bool used[kMaxK];
@@ -293,12 +394,12 @@ __device__ __forceinline__ void seed_body(const SeedArgs& a, unsigned char* smem
       }
       for (int i = 1; i < K; ++i) {
         const int v = order[i];
-        int j = i - 1;
-        while (j >= 0 && (dist[order[j]] > dist[v] || (dist[order[j]] == dist[v] && order[j] > v))) {
-          order[j + 1] = order[j];
-          --j;
+        int jj = i - 1;
+        while (jj >= 0 && (dist[order[jj]] > dist[v] || (dist[order[jj]] == dist[v] && order[jj] > v))) {
+          order[jj + 1] = order[jj];
+          --jj;
         }
-        order[j + 1] = v;
+        order[jj + 1] = v;
       }
       int nd = 0;
       for (int i = 0; i < K; ++i) {
@@ -319,21 +420,21 @@ __device__ __forceinline__ void seed_body(const SeedArgs& a, unsigned char* smem
       }
     }
     __syncthreads();
-    for (int u = threadIdx.x; u < U; u += blockDim.x)
-      if (a.labels) a.labels[u] = label[u];
-    for (int c = threadIdx.x; c < kk; c += blockDim.x) {
-      a.centroids[2 * c] = cx[c];
-      a.centroids[2 * c + 1] = cy[c];
-    }
+    if (a.labels)
+      for (int i = tid; i < nuser; i += nthr) a.labels[user_of(i)] = label[user_of(i)];
+    if (rank == 0)
+      for (int c = tid; c < kk; c += nthr) {
+        a.centroids[2 * c] = cx[c];
+        a.centroids[2 * c + 1] = cy[c];
+      }
   }
-  // Members: one thread per (member n, cell l) row, built in a per-thread
-  // shared-memory row and written out as K contiguous bytes.
-  __syncthreads();
+  // Members: one thread per (member n, cell l) row of this block's cells,
+  // built in a per-thread shared-memory row and written out as K bytes.
   const int ns = kmeans ? a.n_seeded : 0;
-  uint8_t* row = astar + ((U + 15) & ~15) + threadIdx.x * K;
-  const int64_t rows = (int64_t)a.N * L;
-  for (int64_t r = threadIdx.x; r < rows; r += blockDim.x) {
-    const int n = (int)(r / L), l = (int)(r - (int64_t)n * L);
+  uint8_t* row = rows_scratch + tid * K;
+  const int64_t rows = (int64_t)a.N * ncell;
+  for (int64_t t = tid; t < rows; t += nthr) {
+    const int n = (int)(t / ncell), l = rank + (int)(t - (int64_t)n * ncell) * C;
     DrawStream ds(a.seed, (uint64_t)n, 0, kTagSeed);
     if (n < ns) {
       for (int k = 0; k < K; ++k) row[k] = astar[l * K + k];
@@ -346,29 +447,34 @@ __device__ __forceinline__ void seed_body(const SeedArgs& a, unsigned char* smem
     } else {
       random_row(row, K, ds, (uint32_t)(l * (K > 1 ? K - 1 : 0)));
     }
-    uint8_t* dst = a.pop + r * K;
+    uint8_t* dst = a.pop + ((int64_t)n * L + l) * K;
     for (int k = 0; k < K; ++k) dst[k] = row[k];
   }
+  // remote blocks may still read this block's sums or flags: leave together
+  if (C > 1) cluster.sync();
 }
 
-__global__ void __launch_bounds__(kSeedThreads) k_seed(const SeedArgs a) {
+// One instance by a cluster (launched with a cluster dimension of gridDim.x).
+__global__ void __launch_bounds__(kSeedClusterThreads) k_seed(const SeedArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ int changed;
-  seed_body(a, smem, changed);
+  __shared__ SeedShared sh;
+  cg::cluster_group cluster = cg::this_cluster();
+  seed_body(a, smem, sh, (int)cluster.block_rank(), (int)cluster.num_blocks(), cluster);
 }
 
-// Block b seeds instance b of a batch.
-__global__ void __launch_bounds__(kSeedThreads) k_seed_batch(const SeedArgs* __restrict__ args,
-                                                             int n) {
+// Cluster i (of num_blocks() CTAs, one CTA without a cluster launch) seeds
+// instance i of a batch.
+__global__ void __launch_bounds__(kSeedClusterThreads) k_seed_batch(
+    const SeedArgs* __restrict__ args, int n) {
   extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ int changed;
-  for (int i = blockIdx.x; i < n; i += gridDim.x) {
-    const SeedArgs a = args[i];
-    seed_body(a, smem, changed);
-    __syncthreads();
-  }
+  __shared__ SeedShared sh;
+  cg::cluster_group cluster = cg::this_cluster();
+  const int C = (int)cluster.num_blocks();
+  const int i = blockIdx.x / C;
+  if (i >= n) return;  // whole clusters only: i is uniform within a cluster
+  const SeedArgs a = args[i];
+  seed_body(a, smem, sh, (int)cluster.block_rank(), C, cluster);
 }
-
 
 // ------------------------------------------------------------------ best member
 template <typename FT>
@@ -437,38 +543,57 @@ cudaError_t launch_ga_step(const pa_ctx* ctx, const uint8_t* pop, const void* fi
   return cudaGetLastError();
 }
 
-size_t seed_smem(int L, int K, int kk) {
+size_t seed_smem(int L, int K, int kk, int threads, int C) {
   const int U = L * K;
-  return (size_t)kk * (8 + 8 + 8 + 8 + 4) + (size_t)U * 4 * 4 + (size_t)((U + 15) & ~15) +
-         (size_t)kSeedThreads * K + 16;
+  const int nuser = ((L + C - 1) / C) * K;
+  const size_t dist = (size_t)nuser * kk * 8 <= (size_t)kSeedDistBytes ? (size_t)nuser * kk * 8 : 0;
+  return (size_t)kk * 8 * 11 + (size_t)U * 4 * 4 + (size_t)((U + 15) & ~15) +
+         (((size_t)threads * K + 15) & ~size_t(15)) + dist + 16;
 }
 
+static SeedArgs seed_args_of(pa_ctx* ctx, uint8_t* pop);
+
+// Seeding of one instance by a cluster of min(L, 16) CTAs (one CTA per cell
+// or more cells per CTA); smaller clusters when that one cannot be resident.
 cudaError_t launch_seed(pa_ctx* ctx, uint8_t* pop, cudaStream_t st) {
   const pa_config& c = ctx->cfg;
-  SeedArgs a;
-  a.user_xy = ctx->has_positions ? ctx->user_xy : nullptr;
-  a.bs_xy = ctx->has_positions ? ctx->bs_xy : nullptr;
-  a.L = c.L;
-  a.K = c.K;
-  a.kk = c.kmeans_k;
-  a.max_iter = c.kmeans_max_iter;
-  a.N = c.N;
-  a.n_seeded = c.n_seeded;
-  a.seed = c.seed;
-  a.pop = pop;
-  a.labels = ctx->labels;
-  a.centroids = ctx->centroids;
-  const size_t smem = seed_smem(c.L, c.K, c.kmeans_k);
+  const SeedArgs a = seed_args_of(ctx, pop);
   static std::atomic<uint64_t> capped{0};  // devices whose cap is raised (bit per device)
   const uint64_t bit = 1ULL << (ctx->device & 63);
   if (!(capped.load() & bit)) {
     cudaError_t e = raise_smem_cap((const void*)k_seed, ctx->device);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_seed, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     if (e != cudaSuccess) return e;
     capped.fetch_or(bit);
   }
-  (void)cudaGetLastError();  // drop a stale error of an earlier call
-  k_seed<<<1, kSeedThreads, smem, st>>>(a);
-  count_launch();
+  cudaError_t e = cudaErrorNotSupported;
+  for (int C : {16, 8, 4, 2, 1}) {
+    if (C > c.L && C > 1) continue;
+    const size_t smem = seed_smem(c.L, c.K, c.kmeans_k, kSeedClusterThreads, C);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(C, 1, 1);
+    cfg.blockDim = dim3(kSeedClusterThreads, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int nclusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&nclusters, k_seed, &cfg) != cudaSuccess || nclusters < 1) {
+      (void)cudaGetLastError();
+      continue;
+    }
+    (void)cudaGetLastError();  // drop a stale error of an earlier call
+    e = cudaLaunchKernelEx(&cfg, k_seed, a);
+    count_launch();
+    break;
+  }
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 
@@ -492,13 +617,21 @@ static SeedArgs seed_args_of(pa_ctx* ctx, uint8_t* pop) {
   return a;
 }
 
-size_t seed_fill_args(pa_ctx* ctx, void* out) {
+size_t seed_fill_args(pa_ctx* ctx, void* out, int C) {
   const SeedArgs a = seed_args_of(ctx, ctx->pop[0]);
   std::memcpy(out, &a, sizeof a);
-  return seed_smem(ctx->cfg.L, ctx->cfg.K, ctx->cfg.kmeans_k);
+  return seed_smem(ctx->cfg.L, ctx->cfg.K, ctx->cfg.kmeans_k, kSeedClusterThreads, C);
 }
 
-cudaError_t launch_seed_batch(const void* d_args, int n, size_t smem, cudaStream_t st) {
+int seed_batch_cluster(int n) {
+  // clusters of 16 CTAs while the whole batch stays resident on the GPU
+  // (<= 9 instances on 152 SMs), then 8, 4, 2, 1
+  for (int C : {16, 8, 4, 2})
+    if (n * C <= 152) return C;
+  return 1;
+}
+
+cudaError_t launch_seed_batch(const void* d_args, int n, size_t smem, int C, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   static std::atomic<uint64_t> capped{0};
   int dev = 0;
@@ -507,12 +640,27 @@ cudaError_t launch_seed_batch(const void* d_args, int n, size_t smem, cudaStream
   const uint64_t bit = 1ULL << (dev & 63);
   if (!(capped.load() & bit)) {
     e = raise_smem_cap((const void*)k_seed_batch, dev);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_seed_batch, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     if (e != cudaSuccess) return e;
     capped.fetch_or(bit);
   }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(n * C), 1, 1);
+  cfg.blockDim = dim3(kSeedClusterThreads, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = C;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
   (void)cudaGetLastError();  // drop a stale error of an earlier call
-  k_seed_batch<<<n, kSeedThreads, smem, st>>>(static_cast<const SeedArgs*>(d_args), n);
+  e = cudaLaunchKernelEx(&cfg, k_seed_batch, static_cast<const SeedArgs*>(d_args), n);
   count_launch();
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 

@@ -118,12 +118,14 @@ size_t solve_fill_args(const pa_ctx* ctx, int C, int gen0, int G, const uint8_t*
 int solve_batch_max_clusters(const pa_ctx* proto, int C, size_t smem);
 cudaError_t launch_solve_batch(const pa_ctx* proto, int C, int clusters, const void* d_args, int n,
                                int* d_counter, size_t smem, cudaStream_t st);
-// pa_ga.cu: seed many instances at once (one block each) from n seed
-// argument records (seed_args_bytes() each, filled by seed_fill_args) in
-// device memory; smem = the largest seed_fill_args return value
+// pa_ga.cu: seed many instances at once (a cluster of C CTAs each) from n
+// seed argument records (seed_args_bytes() each, filled by seed_fill_args
+// for that C) in device memory; smem = the largest seed_fill_args value
 size_t seed_args_bytes();
-size_t seed_fill_args(pa_ctx* ctx, void* out);
-cudaError_t launch_seed_batch(const void* d_args, int n, size_t smem, cudaStream_t st);
+size_t seed_fill_args(pa_ctx* ctx, void* out, int C);
+// cluster size of a batched seeding launch of n instances
+int seed_batch_cluster(int n);
+cudaError_t launch_seed_batch(const void* d_args, int n, size_t smem, int C, cudaStream_t st);
 cudaError_t launch_validate(const pa_ctx* ctx, const uint8_t* pop, int64_t n, int64_t* first_bad,
                             cudaStream_t st);
 

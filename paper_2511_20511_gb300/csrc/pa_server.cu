@@ -69,6 +69,10 @@ struct pa_server {
   double* h_bestfit = nullptr;
   double* d_bestfit = nullptr;
   size_t best_cap = 0, fit_cap = 0;
+  // side streams of the variant groups of a tick, with their events
+  std::vector<cudaStream_t> side;
+  std::vector<cudaEvent_t> joined;
+  cudaEvent_t fork = nullptr;
   std::string err;
   int64_t completed = 0;
 };
@@ -117,8 +121,33 @@ pa_status grow(pa_server* s, T** dev, T** host, size_t* cap, size_t need, bool p
   return PA_OK;
 }
 
+// Side stream k (created on first use).
+pa_status side_stream(pa_server* s, int k) {
+  if (!s->fork) {
+    pa_status st = scuda(s, cudaEventCreateWithFlags(&s->fork, cudaEventDisableTiming), "event");
+    if (st != PA_OK) return st;
+  }
+  while ((int)s->side.size() <= k) {
+    cudaStream_t x = nullptr;
+    cudaEvent_t e = nullptr;
+    pa_status st = scuda(s, cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking), "stream");
+    if (st != PA_OK) return st;
+    st = scuda(s, cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "event");
+    if (st != PA_OK) {
+      cudaStreamDestroy(x);
+      return st;
+    }
+    s->side.push_back(x);
+    s->joined.push_back(e);
+  }
+  return PA_OK;
+}
+
 void destroy_server(pa_server* s) {
   if (!s) return;
+  for (auto x : s->side) cudaStreamDestroy(x);
+  for (auto e : s->joined) cudaEventDestroy(e);
+  if (s->fork) cudaEventDestroy(s->fork);
   for (auto& sl : s->slots) pa_destroy(sl.ctx);
   cudaFree(s->d_seed_args);
   cudaFreeHost(s->h_seed_args);
@@ -244,13 +273,14 @@ pa_status pa_server_poll(pa_server* s, int32_t max_done, int64_t* done_ids, uint
     if (st != PA_OK) return st;
     h = static_cast<unsigned char*>(s->h_seed_args);
     size_t smem = 0;
+    const int sc = pa::seed_batch_cluster((int)fresh.size());
     for (size_t i = 0; i < fresh.size(); ++i)
-      smem = std::max(smem, pa::seed_fill_args(s->slots[fresh[i]].ctx, h + sb * i));
+      smem = std::max(smem, pa::seed_fill_args(s->slots[fresh[i]].ctx, h + sb * i, sc));
     st = scuda(s, cudaMemcpyAsync(s->d_seed_args, h, sb * fresh.size(), cudaMemcpyHostToDevice,
                                   s->stream),
                "copy seed args");
     if (st == PA_OK)
-      st = scuda(s, pa::launch_seed_batch(s->d_seed_args, (int)fresh.size(), smem, s->stream),
+      st = scuda(s, pa::launch_seed_batch(s->d_seed_args, (int)fresh.size(), smem, sc, s->stream),
                  "seed kernel");
     if (st != PA_OK) return st;
     for (int i : fresh) s->slots[i].fresh = false;
@@ -310,8 +340,10 @@ pa_status pa_server_poll(pa_server* s, int32_t max_done, int64_t* done_ids, uint
   for (auto& kv : groups) {
     const std::vector<int>& mem = kv.second;
     const pa_ctx* proto = s->slots[mem[0]].ctx;
-    // cluster size: 4 CTAs per instance (falls back to smaller if needed)
-    int C = 4;
+    // cluster size: the largest that keeps every active slot resident at
+    // once (16 CTAs for up to 9 slots on 152 SMs), smaller if it cannot fit
+    int C = 16;
+    while (C > 1 && n_act * C > proto->num_sms) C /= 2;
     size_t smem = 0;
     bool ok = false;
     for (; C >= 1 && !ok; C /= 2) {
@@ -342,13 +374,23 @@ pa_status pa_server_poll(pa_server* s, int32_t max_done, int64_t* done_ids, uint
     st = scuda(s, cudaMemcpyAsync(dargs, ha + a_off, ab * mem.size(), cudaMemcpyHostToDevice,
                                   s->stream),
                "copy solve args");
+    // the variants' launches run side by side: group k on side stream k,
+    // forked from and joined back into the server stream
+    if (st == PA_OK) st = side_stream(s, gk);
+    if (st == PA_OK) st = scuda(s, cudaEventRecord(s->fork, s->stream), "fork");
+    if (st == PA_OK) st = scuda(s, cudaStreamWaitEvent(s->side[gk], s->fork, 0), "fork wait");
     if (st == PA_OK)
       st = scuda(s, pa::launch_solve_batch(proto, C, clusters, dargs, (int)mem.size(),
-                                           s->d_counters + gk, smem, s->stream),
+                                           s->d_counters + gk, smem, s->side[gk]),
                  "batched solve kernel");
+    if (st == PA_OK) st = scuda(s, cudaEventRecord(s->joined[gk], s->side[gk]), "join");
     if (st != PA_OK) return st;
     a_off += ab * mem.size();
     ++gk;
+  }
+  for (int k = 0; k < gk; ++k) {
+    st = scuda(s, cudaStreamWaitEvent(s->stream, s->joined[k], 0), "join wait");
+    if (st != PA_OK) return st;
   }
   // ---- 4. collect finished requests
   for (int i : finishing) {

@@ -618,6 +618,12 @@ __global__ void __launch_bounds__(kSolveThreads)
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int elites[64];
   __shared__ int next;
+  // the instance's arguments live in shared memory (a local copy would sit
+  // in local memory: the kernel runs at the 64-register limit)
+  __shared__ SolveArgs sargs;
+  static_assert(sizeof(SolveArgs) % 8 == 0, "SolveArgs is copied as 8-byte words");
+  constexpr int kArgWords = (int)(sizeof(SolveArgs) / 8);
+  static_assert(kArgWords <= kSolveThreads, "one word per thread");
   cg::cluster_group cluster = cg::this_cluster();
   const int C = (int)cluster.num_blocks();
   for (;;) {
@@ -628,8 +634,11 @@ __global__ void __launch_bounds__(kSolveThreads)
     cluster.sync();
     const int i = next;
     if (i >= n_inst) break;
-    const SolveArgs a = insts[i];
-    solve_body<FT, NJ, VEC, FIN>(a, smem, elites, cluster);
+    if (threadIdx.x < kArgWords)
+      reinterpret_cast<uint64_t*>(&sargs)[threadIdx.x] =
+          reinterpret_cast<const uint64_t*>(insts + i)[threadIdx.x];
+    __syncthreads();
+    solve_body<FT, NJ, VEC, FIN>(sargs, smem, elites, cluster);
   }
 }
 
