@@ -35,6 +35,11 @@ sys.path.insert(0, ROOT)
 
 L, K, TAU_P, M_ANT, N_POP, G_GEN, KMEANS_K = 19, 10, 10, 256.0, 256, 200, 10
 BATCH_LOG2 = 20
+# DRAM bytes (read + write) per launch of the two roofline kernels, from one
+# ncu capture each (profiles/k_solve_L19_K10_N256_G200.md,
+# profiles/k_eval_f32_pilot_2e20_L19_K10.md); None until captured
+TRAFFIC_K_SOLVE = None
+TRAFFIC_EVAL = None
 METRIC = ("chromosome fitness evals/sec and GA gens/sec (L=19,K=10); "
           "p50/p99 solve latency served vs plain")
 WORKLOAD = ("single instance at paper-like scale: L=19 hex cells (2 rings), K=10 users/cell, "
@@ -284,6 +289,19 @@ def run_ours(args):
     h2d = keep[0].nbytes + keep[1].nbytes + keep[2].nbytes
     d2h = best.nbytes + 8
 
+    # ---- the step's dominant kernel: the fused solve k_solve (all G
+    #      generations and the final evaluation in one cluster launch), timed
+    #      alone through pa_step on the context stream
+    ctas = B.pa_solve_cluster_ctas(ctx.handle)
+    ctx.kmeans_seed()
+
+    def generations_step():
+        B.pa_step(ctx.handle, G_GEN)
+
+    generations_step()
+    ks_ms = timed(generations_step, max(3, min(args.steps, 10)))
+    ks_avg = statistics.mean(ks_ms) / 1e3
+
     # ---- population-wide evaluation kernel on 2^20 chromosomes (> L2)
     nb = 1 << BATCH_LOG2
     pop = inputs.random_population_torch(nb, L, K, seed=1000 + rank, device=dev)
@@ -306,13 +324,25 @@ def run_ours(args):
     sm_max = pk.get("sm_max_mhz", 2070.0)
     peak_gword = n_sms * 32 * sm_max * 1e6 / 1e9
     achieved_gword = nb * words / ev_avg / 1e9
-    roofline = {"bound": "alu", "kernel": "k_eval_f32_pilot (population fitness, FP32)",
-                "achieved": achieved_gword, "peak": peak_gword, "unit": "Gword/s",
-                "frac": achieved_gword / peak_gword, "traffic": None,
-                "path": f"shared-memory gather data path: 32 x 4-byte words/clk/SM x {n_sms} "
-                        f"SMs x {sm_max:.0f} MHz",
-                "units_per_launch": nb, "words_per_unit": words,
-                "avg_launch_ms": ev_avg * 1e3}
+    path = (f"shared-memory gather data path: 32 x 4-byte words/clk/SM x {n_sms} SMs x "
+            f"{sm_max:.0f} MHz")
+    # the step's dominant kernel: (G+1) evaluations of N members per launch
+    ks_units = N_POP * (G_GEN + 1)
+    ks_gword = ks_units * words / ks_avg / 1e9
+    roofline = {"bound": "alu", "kernel": "k_solve (fused GA run: G generations + final "
+                                          "evaluation, one cluster)",
+                "achieved": ks_gword, "peak": peak_gword, "unit": "Gword/s",
+                "frac": ks_gword / peak_gword, "traffic": TRAFFIC_K_SOLVE, "path": path,
+                "units_per_launch": ks_units, "words_per_unit": words,
+                "avg_launch_ms": ks_avg * 1e3, "cluster_ctas": ctas,
+                "frac_of_cluster_sms": ks_gword / (peak_gword * ctas / n_sms) if ctas > 0
+                else None,
+                "note": "one instance: 201 dependent generations on one cluster, latency-bound"}
+    roofline_eval = {"bound": "alu", "kernel": "k_eval_f32_pilot (population fitness, FP32)",
+                     "achieved": achieved_gword, "peak": peak_gword, "unit": "Gword/s",
+                     "frac": achieved_gword / peak_gword, "traffic": TRAFFIC_EVAL, "path": path,
+                     "units_per_launch": nb, "words_per_unit": words,
+                     "avg_launch_ms": ev_avg * 1e3}
 
     lat = sorted(step_ms)
 
@@ -333,6 +363,7 @@ def run_ours(args):
         "eval_batch": {"chromosomes": nb, "evals_per_s": evals_batch * world,
                        "avg_launch_ms": ev_avg * 1e3},
         "roofline": roofline,
+        "roofline_eval_batch": roofline_eval,
         "e2e": {"value": world * args.steps * N_POP * (G_GEN + 1) / e2e_total, "unit": "evals/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "what": "pa_load_instance (pinned host beta + positions) + pa_solve (best row "

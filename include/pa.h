@@ -361,6 +361,14 @@ const char* pa_last_error(const pa_ctx* ctx);
  * contexts, all devices); for accounting launches in a timed region. */
 uint64_t pa_kernel_launches(void);
 
+/*
+ * CTAs per thread-block cluster of the context's fused solve kernel (all
+ * generations in one launch, one cluster per instance): *ctas = 1..16, 0
+ * when the instance runs one evaluation and one GA launch per generation,
+ * -1 before the first pa_solve / pa_step has chosen.  No GPU work.
+ */
+pa_status pa_solve_cluster_ctas(const pa_ctx* ctx, int32_t* ctas);
+
 #ifdef __cplusplus
 }
 #endif

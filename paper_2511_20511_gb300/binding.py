@@ -62,6 +62,7 @@ _SIGS = {
     "pa_status_str": (C.c_char_p, [C.c_int]),
     "pa_last_error": (C.c_char_p, [C.c_void_p]),
     "pa_kernel_launches": (C.c_uint64, []),
+    "pa_solve_cluster_ctas": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32)]),
     "pa_batch_create": (C.c_int, [C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                   C.c_void_p, C.POINTER(C.c_void_p)]),
     "pa_batch_destroy": (None, [C.c_void_p]),
@@ -192,6 +193,12 @@ def pa_eval_population_noalloc(cfg, beta, pop, fit, stream=None):
 
 def pa_kernel_launches():
     return int(lib().pa_kernel_launches())
+
+
+def pa_solve_cluster_ctas(ctx):
+    v = C.c_int32(-1)
+    _check(lib().pa_solve_cluster_ctas(ctx, C.byref(v)), ctx)
+    return int(v.value)
 
 
 def pa_destroy(ctx):

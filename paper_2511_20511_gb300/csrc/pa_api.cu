@@ -119,6 +119,12 @@ const char* pa_last_error(const pa_ctx* ctx) {
 
 uint64_t pa_kernel_launches(void) { return pa::g_launches.load(std::memory_order_relaxed); }
 
+pa_status pa_solve_cluster_ctas(const pa_ctx* ctx, int32_t* ctas) {
+  if (!ctx || !ctas) return PA_EINVAL;
+  *ctas = ctx->t32.streamed ? 0 : ctx->solve_C;
+  return PA_OK;
+}
+
 uint64_t pa_prob_to_thresh(double p) {
   if (!(p > 0.0)) return 0;
   if (p >= 1.0) return 1ULL << 32;

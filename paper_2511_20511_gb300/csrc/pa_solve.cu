@@ -344,8 +344,11 @@ __device__ __forceinline__ void solve_body(const SolveArgs& a, unsigned char* sm
   const int lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
   const int T_ = a.tour, nblk = a.nblk, E = a.E;
   const int nwords = MS >> 2;
-  // FP32 evaluation roles: q = member*K + pilot, column-pair share h
-  const int q = tid / JS, h = tid - (tid / JS) * JS;
+  // FP32 evaluation roles: q = member*K + pilot, column-pair share h.  Each
+  // half-warp takes 16 consecutive q with one share h, so the 16 rows it
+  // reads in a step (distinct users, RS/2 odd; equal users read the same
+  // address) fall in distinct banks
+  const int q = (tid / (16 * JS)) * 16 + (tid & 15), h = (tid >> 4) % JS;
   const bool one_chunk = nvalid <= a.CH;
   const int n_elite_here = max(0, min(E - base_n, nvalid));
   for (int g = 0;; ++g) {
@@ -359,7 +362,7 @@ __device__ __forceinline__ void solve_body(const SolveArgs& a, unsigned char* sm
     for (int c0 = 0; c0 < nvalid; c0 += a.NTT) {
       const int nv = min(a.NTT, nvalid - c0);
       if (!F64) {
-        const int eval_threads = nv * K * JS;
+        const int eval_threads = ((nv * K + 15) / 16) * 16 * JS;  // threads up to the last q
         if (q < nv * K) {
           const int c = q / K, pp = q - c * K;
           eval_pilot_f32<NJ, VEC, FIN, JS>(sm, popc + (c0 + c) * MS + XO + pp, K, h,
@@ -668,7 +671,14 @@ SolveShape solve_shape(const pa_ctx* ctx, int C) {
   if (f64) {
     s.NTT = std::max(1, std::min(s.NT, 2048 / std::max(1, LK)));
   } else {
-    s.NTT = std::max(1, std::min(s.NT, kSolveThreads / (c.K * JS)));
+    // members per pass: their (member, pilot) pairs, in half-warp groups of
+    // 16, times JS shares fit the block
+    s.NTT = 1;
+    for (int n = s.NT; n >= 1; --n)
+      if (((n * c.K + 15) / 16) * 16 * JS <= kSolveThreads) {
+        s.NTT = n;
+        break;
+      }
   }
   size_t b = 0;
   if (!f64) {
