@@ -198,13 +198,16 @@ __device__ __forceinline__ float member_sum(const float* part, int n, int lane) 
   return s;
 }
 
-// member_sum for n <= NMAX with the loop unrolled (same additions, same order).
+// member_sum with the first NMAX entries (a multiple of 32) in an unrolled
+// loop: the same additions in the same order.
 template <int NMAX>
 __device__ __forceinline__ float member_sum_bounded(const float* part, int n, int lane) {
+  static_assert(NMAX % 32 == 0, "whole rounds of 32 entries");
   float s = 0.f;
 #pragma unroll
   for (int i0 = 0; i0 < NMAX; i0 += 32)
     if (i0 + lane < n) s += part[i0 + lane];
+  for (int i = NMAX + lane; i < n; i += 32) s += part[i];
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
   return s;

@@ -254,12 +254,17 @@ __device__ __forceinline__ uint32_t dsmem_addr(const void* local, int rank) {
   return r;
 }
 
-// Column-pair share of the fused evaluation: each thread takes two BS column
-// pairs of one (member, pilot), so the per-thread dependency chain is short.
-template <int NJ>
-struct FusedSplit {
-  static constexpr int JS = NJ >= 8 ? NJ / 4 : 1;
-};
+// Column pairs per thread in the fused FP32 evaluation: the largest divisor
+// of NJ/2 not above kFusedMaxNP; JS = NJ/2 / NP threads share a (member,
+// pilot).  Fewer, longer threads issue fewer address and index instructions
+// per table word; more threads finish a pass sooner.
+constexpr int kFusedMaxNP = 2;
+__host__ __device__ constexpr int fused_np(int NJ) {
+  int np = kFusedMaxNP < NJ / 2 ? kFusedMaxNP : NJ / 2;
+  while (np > 1 && (NJ / 2) % np != 0) --np;
+  return np < 1 ? 1 : np;
+}
+__host__ __device__ constexpr int fused_js(int NJ) { return (NJ / 2) / fused_np(NJ); }
 
 // Member record in shared memory (MS bytes): the chromosome X (L*K bytes,
 // pilot of each user) at offset 0 and its inverse INV (L*K bytes, user of
@@ -274,7 +279,7 @@ __device__ __forceinline__ void solve_body(const SolveArgs& a, unsigned char* sm
   const int L = a.L, K = a.K, N = a.N, NT = a.NT, MS = a.MS, XO = a.XO;
   const int LK = L * K;
   constexpr bool F64 = sizeof(FT) == 8;
-  constexpr int JS = F64 ? 1 : FusedSplit<NJ>::JS;
+  constexpr int JS = F64 ? 1 : fused_js(NJ);
   constexpr int NPR = NJ / 2;  // column pairs per (member, pilot)
 
   // ---- carve shared memory
@@ -376,7 +381,7 @@ __device__ __forceinline__ void solve_body(const SolveArgs& a, unsigned char* sm
         if (c0 == 0 && one_chunk && eval_threads + 32 <= (int)blockDim.x) drawn = true;
         __syncthreads();
         for (int c = warp; c < nv; c += nwarps) {
-          const float f = member_sum(PART + c * K * NPR, K * NPR, lane);
+          const float f = member_sum_bounded<16 * NPR>(PART + c * K * NPR, K * NPR, lane);
           const int n = base_n + c0 + c;
           if (lane < C) cluster.map_shared_rank(fit, lane)[n] = (FT)f;
         }
@@ -395,7 +400,7 @@ __device__ __forceinline__ void solve_body(const SolveArgs& a, unsigned char* sm
           for (int r = 0; r < C; ++r) cluster.map_shared_rank(fit, r)[n] = (FT)s;
         }
       }
-      __syncthreads();
+      if (c0 + a.NTT < nvalid) __syncthreads();  // the last pass meets the cluster barrier
     }
     // ---- 2. all fitness values and members of generation g are visible
     cluster.sync();
@@ -666,7 +671,7 @@ SolveShape solve_shape(const pa_ctx* ctx, int C) {
   s.MS = 2 * s.XO;
   if ((s.MS / 4) % 2 == 0) s.MS += 4;
   const int NJ = ctx->t32.NJ;
-  const int JS = (!f64 && NJ >= 8) ? NJ / 4 : 1;
+  const int JS = f64 ? 1 : fused_js(NJ);
   const int NPR = f64 ? 0 : NJ / 2;
   if (f64) {
     s.NTT = std::max(1, std::min(s.NT, 2048 / std::max(1, LK)));
