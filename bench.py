@@ -439,9 +439,18 @@ def run_batched(B, inputs, G=100, n=512, reps=3):
         c.close()
     lat.sort()
     evals = sum(d["cfg"].N for d in insts) * (G + 1)
+    # gather words of all evaluations (L^2 K per chromosome), against the
+    # shared-memory data path of the whole GPU
+    words = sum(d["cfg"].N * d["cfg"].L * d["cfg"].L * d["cfg"].K for d in insts) * (G + 1)
+    n_sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    peak = n_sms * 32 * peaks().get("sm_max_mhz", 2070.0) * 1e6 / 1e9
+    ach = words / t_batch / 1e9
     return {"instances": n, "generations": G, "population": 128,
             "batched": {"seconds_per_batch": t_batch, "solves_per_s": n / t_batch,
-                        "evals_per_s": evals / t_batch, "cluster_sizes": [int(x) for x in chosen]},
+                        "evals_per_s": evals / t_batch, "cluster_sizes": [int(x) for x in chosen],
+                        "roofline": {"bound": "alu", "achieved": ach, "peak": peak,
+                                     "unit": "Gword/s", "frac": ach / peak,
+                                     "what": "all gathers of the batch / batch wall time"}},
             "one_launch_sequence_per_instance": {
                 "seconds": t_seq, "solves_per_s": n / t_seq, "evals_per_s": evals / t_seq,
                 "p50_ms": 1e3 * lat[len(lat) // 2], "p99_ms": 1e3 * lat[int(0.99 * (len(lat) - 1))]},
@@ -482,6 +491,14 @@ def run_streamed(B, inputs, dev, n=1 << 17, reps=5):
     sp = oracle.sinr_params(oracle.FINITE_M, K5, 512.0, inst["rho"], 1.0)
     ref = oracle.fitness_batch(inst["beta"], sub, sp)
     got = fit.cpu().numpy()[idx].astype(np.float64)
+    # the whole configured solve: N = 2048, 500 generations (per-generation
+    # evaluation and GA launches; the table does not fit the fused kernel)
+    G5 = 500
+    ctx.solve(5)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ctx.solve(G5)
+    t_solve = time.perf_counter() - t0
     ctx.close()
     words = L5 * L5 * K5
     n_sms = torch.cuda.get_device_properties(dev).multi_processor_count
@@ -493,7 +510,10 @@ def run_streamed(B, inputs, dev, n=1 << 17, reps=5):
             "input_GBps": n * L5 * K5 / (ms / 1e3) / 1e9,
             "roofline": {"bound": "alu", "achieved": ach, "peak": peak, "unit": "Gword/s",
                          "frac": ach / peak, "words_per_unit": words},
-            "sampled_max_rel_err_vs_oracle": float(np.max(np.abs(got - ref) / ref))}
+            "sampled_max_rel_err_vs_oracle": float(np.max(np.abs(got - ref) / ref)),
+            "solve": {"population": 2048, "generations": G5, "seconds": t_solve,
+                      "evals_per_s": 2048 * (G5 + 1) / t_solve,
+                      "gens_per_s": G5 / t_solve}}
 
 
 def run_serving(B, inputs, rate=2000.0, seconds=2.0, G=40, N=64, tick=20, budget=40 << 30):

@@ -90,9 +90,19 @@ typedef struct {
   int32_t kmeans_k; /* K-means clusters (1..K)                             */
   int32_t kmeans_max_iter; /* assignment passes (>= 1)                     */
   int32_t n_seeded; /* members built from the K-means assignment (0..N)   */
-  int32_t flags;    /* reserved, must be 0                                 */
+  int32_t flags;    /* 0, or PA_FLAG_TEST_STALL_COPIES                      */
   int64_t reserved[4]; /* must be 0                                        */
 } pa_config;
+
+/*
+ * Testing the bounded waits.  With this flag the context's next FP32
+ * evaluation that stages chromosome tiles by bulk copies announces the
+ * copies to its mbarriers but never issues them: every block's wait gives
+ * up after about a second (the kernel returns normally, nothing faults),
+ * and the next synchronous call reports PA_ETIMEOUT.  One-shot: later
+ * evaluations of the context run normally.  The paper has no counterpart.
+ */
+#define PA_FLAG_TEST_STALL_COPIES 1
 
 /*
  * Defaults for an L-cell, K-user layout: FP32, asymptotic SINR (the

@@ -15,6 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libpa.so")
 
 PA_OK, PA_EINVAL, PA_ENOMEM, PA_ECUDA, PA_ETIMEOUT, PA_EUNSUPPORTED, PA_EBUSY = range(7)
+PA_FLAG_TEST_STALL_COPIES = 1
 PA_FP32, PA_FP64 = 0, 1
 PA_SINR_ASYMPTOTIC, PA_SINR_FINITE_M = 0, 1
 

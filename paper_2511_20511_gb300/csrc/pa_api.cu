@@ -178,7 +178,7 @@ static pa_status validate_config(const pa_config* c, std::string* why) {
   if (c->kmeans_k < 1 || c->kmeans_k > c->K) return bad("kmeans_k must be in [1, K]");
   if (c->kmeans_max_iter < 1) return bad("kmeans_max_iter must be >= 1");
   if (c->n_seeded < 0 || c->n_seeded > c->N) return bad("n_seeded must be in [0, N]");
-  if (c->flags != 0) return bad("flags must be 0");
+  if ((c->flags & ~PA_FLAG_TEST_STALL_COPIES) != 0) return bad("unknown flags");
   for (int i = 0; i < 4; ++i)
     if (c->reserved[i] != 0) return bad("reserved fields must be 0");
   return PA_OK;
@@ -233,6 +233,7 @@ pa_status pa_create(const pa_config* cfg, const double* beta, const int32_t* use
   pa_ctx* c = new (std::nothrow) pa_ctx();
   if (!c) return PA_ENOMEM;
   c->cfg = *cfg;
+  c->test_stall = (cfg->flags & PA_FLAG_TEST_STALL_COPIES) ? 1 : 0;
   c->stream = static_cast<cudaStream_t>(stream);
   c->nc = cfg->sigma2 / cfg->rho;
   c->pc = cfg->sigma2 / ((double)cfg->tau_p * cfg->rho);

@@ -5,8 +5,9 @@
 // width NJ, load width); each group runs as ONE persistent launch of
 // k_solve_batch in which every thread-block cluster takes the next instance
 // from a counter until the group is done, so uneven instances balance
-// across the GPU.  Seeding of all instances is one launch (one block per
-// instance).  The whole batch solve -- counter reset, seeding, the group
+// across the GPU.  Seeding of all instances is one launch (a cluster of
+// CTAs per instance, 16 while the batch stays resident, down to 1).  The
+// whole batch solve -- counter reset, seeding, the group
 // launches on parallel streams, and the copies of the best members to the
 // host -- is captured once into a CUDA graph and replayed.  The cluster size
 // of each group (1 CTA per instance up to 16) is picked by pa_batch_tune,

@@ -123,6 +123,7 @@ struct PilotArgs {
   int L, K, RS, NT;
   int64_t tab_floats;
   int xbytes;     // shared bytes of one chromosome buffer
+  int stall;      // testing: announce the bulk copies but never issue them
   float M, pc;
 };
 
@@ -150,7 +151,9 @@ __global__ void __launch_bounds__(kPilotThreads, 4) k_eval_f32_pilot(const Pilot
     if (tid == 0 && bulk && tile < tiles && full(tile)) {
       const uint32_t mb = mb0 + 8 * buf;
       mbar_expect_tx(mb, tile_bytes);
-      bulk_g2s(smem_u32(X0 + buf * a.xbytes), a.pop + tile * (int64_t)tile_bytes, tile_bytes, mb);
+      if (!a.stall)
+        bulk_g2s(smem_u32(X0 + buf * a.xbytes), a.pop + tile * (int64_t)tile_bytes, tile_bytes,
+                 mb);
     }
   };
 
@@ -505,7 +508,7 @@ bool f32_supported(int L, int K, size_t* smem_bytes) {
   return smem <= (size_t)kSmemBudget;
 }
 
-cudaError_t launch_eval_f32(const pa_ctx* ctx, const uint8_t* pop, int64_t n, float* fit,
+cudaError_t launch_eval_f32(pa_ctx* ctx, const uint8_t* pop, int64_t n, float* fit,
                             cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   const pa::F32Tables& t = ctx->t32;
@@ -527,6 +530,8 @@ cudaError_t launch_eval_f32(const pa_ctx* ctx, const uint8_t* pop, int64_t n, fl
     a.NT = s.NT;
     a.tab_floats = (((int64_t)L * K * t.RS + 3) / 4) * 4;
     a.xbytes = s.xbytes;
+    a.stall = ctx->test_stall;
+    ctx->test_stall = 0;
     a.M = t.M;
     a.pc = t.pc;
     return fin ? pick_pilot<true>(t.NJ, a, s, ctx->num_sms, st)

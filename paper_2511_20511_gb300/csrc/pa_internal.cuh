@@ -68,6 +68,7 @@ struct pa_ctx {
   int32_t generation = 0;
   int solve_C = -1;            // cluster size of the fused solve kernel (-1: not chosen, 0: none)
   int wait_check = 0;          // an FP32 evaluation ran since t32.err_flag was last read
+  int test_stall = 0;          // PA_FLAG_TEST_STALL_COPIES still pending (one-shot)
   // scratch
   int64_t* scratch_i64 = nullptr;  // small device scratch (flags, argbest)
   uint8_t* best_row = nullptr;     // [L*K]
@@ -93,7 +94,7 @@ cudaError_t launch_prep(pa_ctx* ctx);
 bool instance_ok(const pa_config& c, const double* beta, const int32_t* user_xy_mm,
                  const int32_t* bs_xy_mm, double* bmax);
 // pa_fitness.cu
-cudaError_t launch_eval_f32(const pa_ctx* ctx, const uint8_t* pop, int64_t n, float* fit,
+cudaError_t launch_eval_f32(pa_ctx* ctx, const uint8_t* pop, int64_t n, float* fit,
                             cudaStream_t st);
 cudaError_t launch_eval_f64(const pa_ctx* ctx, const uint8_t* pop, int64_t n, double* fit,
                             cudaStream_t st);

@@ -63,7 +63,7 @@ def _create_status(B, cfg, beta, u=None, b=None):
 
 @pytest.mark.parametrize("field,value", [("L", 1), ("K", 0), ("K", 65), ("N", 1), ("E", 256),
                                          ("tour", 0), ("kmeans_k", 11), ("kmeans_max_iter", 0),
-                                         ("n_seeded", 300), ("flags", 1), ("prec", 7),
+                                         ("n_seeded", 300), ("flags", 2), ("prec", 7),
                                          ("mode", 3), ("pc_thresh", 2**32 + 1)])
 def test_create_rejects_bad_config(B, field, value):
     cfg = B.pa_config_default(19, 10)
