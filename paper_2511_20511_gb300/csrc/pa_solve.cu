@@ -255,22 +255,28 @@ __device__ __forceinline__ uint32_t dsmem_addr(const void* local, int rank) {
 }
 
 // Column pairs per thread in the fused FP32 evaluation: the largest divisor
-// of NJ/2 not above kFusedMaxNP; JS = NJ/2 / NP threads share a (member,
-// pilot).  Fewer, longer threads issue fewer address and index instructions
-// per table word; more threads finish a pass sooner.
-constexpr int kFusedMaxNP = 2;
-__host__ __device__ constexpr int fused_np(int NJ) {
-  int np = kFusedMaxNP < NJ / 2 ? kFusedMaxNP : NJ / 2;
+// of NJ/2 not above MAXNP; JS = NJ/2 / NP threads share a (member, pilot).
+// More threads per pilot finish an evaluation pass sooner (one instance on a
+// 16-CTA cluster is latency-bound: MAXNP 2); fewer, longer threads issue
+// fewer index and address instructions per table word (batched instances
+// with many members per CTA are issue-bound: MAXNP 5).  The sums are the
+// same whatever the split.
+constexpr int kSoloMaxNP = 2;
+constexpr int kBatchMaxNP = 5;
+__host__ __device__ constexpr int fused_np(int NJ, int maxnp) {
+  int np = maxnp < NJ / 2 ? maxnp : NJ / 2;
   while (np > 1 && (NJ / 2) % np != 0) --np;
   return np < 1 ? 1 : np;
 }
-__host__ __device__ constexpr int fused_js(int NJ) { return (NJ / 2) / fused_np(NJ); }
+__host__ __device__ constexpr int fused_js(int NJ, int maxnp) {
+  return (NJ / 2) / fused_np(NJ, maxnp);
+}
 
 // Member record in shared memory (MS bytes): the chromosome X (L*K bytes,
 // pilot of each user) at offset 0 and its inverse INV (L*K bytes, user of
 // each pilot, row by row) at offset XO.  Crossover takes whole rows, so the
 // child's INV rows are its parents' INV rows; a swap mutation updates both.
-template <typename FT, int NJ, int VEC, bool FIN>
+template <typename FT, int NJ, int VEC, bool FIN, int MAXNP>
 __device__ __forceinline__ void solve_body(const SolveArgs& a, unsigned char* smem, int* elites,
                                            cg::cluster_group& cluster) {
   const int rank = (int)cluster.block_rank();
@@ -279,7 +285,7 @@ __device__ __forceinline__ void solve_body(const SolveArgs& a, unsigned char* sm
   const int L = a.L, K = a.K, N = a.N, NT = a.NT, MS = a.MS, XO = a.XO;
   const int LK = L * K;
   constexpr bool F64 = sizeof(FT) == 8;
-  constexpr int JS = F64 ? 1 : fused_js(NJ);
+  constexpr int JS = F64 ? 1 : fused_js(NJ, MAXNP);
   constexpr int NPR = NJ / 2;  // column pairs per (member, pilot)
 
   // ---- carve shared memory
@@ -613,7 +619,7 @@ __global__ void __launch_bounds__(kSolveThreads) k_solve(const SolveArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int elites[64];
   cg::cluster_group cluster = cg::this_cluster();
-  solve_body<FT, NJ, VEC, FIN>(a, smem, elites, cluster);
+  solve_body<FT, NJ, VEC, FIN, kSoloMaxNP>(a, smem, elites, cluster);
 }
 
 // Many instances per launch (persistent clusters): each cluster takes the
@@ -646,7 +652,7 @@ __global__ void __launch_bounds__(kSolveThreads)
       reinterpret_cast<uint64_t*>(&sargs)[threadIdx.x] =
           reinterpret_cast<const uint64_t*>(insts + i)[threadIdx.x];
     __syncthreads();
-    solve_body<FT, NJ, VEC, FIN>(sargs, smem, elites, cluster);
+    solve_body<FT, NJ, VEC, FIN, kBatchMaxNP>(sargs, smem, elites, cluster);
   }
 }
 
@@ -656,7 +662,7 @@ struct SolveShape {
   size_t smem;
 };
 
-SolveShape solve_shape(const pa_ctx* ctx, int C) {
+SolveShape solve_shape(const pa_ctx* ctx, int C, int maxnp) {
   const pa_config& c = ctx->cfg;
   const bool f64 = c.prec == PA_FP64;
   const int LK = c.L * c.K;
@@ -671,7 +677,7 @@ SolveShape solve_shape(const pa_ctx* ctx, int C) {
   s.MS = 2 * s.XO;
   if ((s.MS / 4) % 2 == 0) s.MS += 4;
   const int NJ = ctx->t32.NJ;
-  const int JS = f64 ? 1 : fused_js(NJ);
+  const int JS = f64 ? 1 : fused_js(NJ, maxnp);
   const int NPR = f64 ? 0 : NJ / 2;
   if (f64) {
     s.NTT = std::max(1, std::min(s.NT, 2048 / std::max(1, LK)));
@@ -777,7 +783,7 @@ cudaError_t launch_solve(pa_ctx* ctx, const uint8_t* pop_in, uint8_t* pop_out, i
   for (int C : sizes) {
     if (ctx->solve_C > 0 && C != ctx->solve_C) continue;
     if (C > c.N) continue;
-    const SolveShape s = solve_shape(ctx, C);
+    const SolveShape s = solve_shape(ctx, C, kSoloMaxNP);
     if (s.smem + 64 * 4 > (size_t)kSmemBudget) continue;
     SolveArgs a{};
     a.pop_in = pop_in;
@@ -923,7 +929,7 @@ size_t solve_fill_args(const pa_ctx* ctx, int C, int gen0, int G, const uint8_t*
                        void* args_out) {
   const pa_config& c = ctx->cfg;
   if (C > c.N || ctx->t32.streamed) return 0;
-  const SolveShape s = solve_shape(ctx, C);
+  const SolveShape s = solve_shape(ctx, C, kBatchMaxNP);
   if (s.smem + 64 * 4 + 16 > (size_t)kSmemBudget) return 0;
   SolveArgs a{};
   a.pop_in = pop_in;
