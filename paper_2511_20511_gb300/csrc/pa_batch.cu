@@ -219,6 +219,25 @@ pa_status pa_batch_create(int32_t n, const pa_config* cfgs, const double* const*
         b->groups[it->second].members.push_back(i);
       }
     }
+    // longest first: each group's queue in decreasing work (N L^2 K gathers
+    // per generation), so the last instances a cluster takes are short ones;
+    // the heaviest group is launched first
+    auto work = [&](int i) {
+      const pa_config& c = b->ctx[i]->cfg;
+      return (int64_t)c.N * c.L * c.L * c.K;
+    };
+    for (auto& g : b->groups)
+      std::stable_sort(g.members.begin(), g.members.end(),
+                       [&](int x, int y) { return work(x) > work(y); });
+    auto gwork = [&](const pa_batch::Group& g) {
+      int64_t w = 0;
+      for (int i : g.members) w += work(i);
+      return w;
+    };
+    std::stable_sort(b->groups.begin(), b->groups.end(),
+                     [&](const pa_batch::Group& x, const pa_batch::Group& y) {
+                       return gwork(x) > gwork(y);
+                     });
   }
   auto chk = [&](cudaError_t e, const char* what) {
     if (st == PA_OK) st = bcuda(b, e, what);
