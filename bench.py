@@ -244,6 +244,8 @@ def run_ours(args):
 
     if args.only == "eval":
         return run_eval_only(args, B, inputs, ctx, stream, dev, rank)
+    if args.only == "stream":
+        return run_stream_only(args, B, inputs, dev)
     if args.only == "solve":
         for _ in range(args.warmup + args.steps):
             ctx.solve(G_GEN)
@@ -614,6 +616,28 @@ def run_serving(B, inputs, rate=2000.0, seconds=2.0, G=40, N=64, tick=20, budget
             "timing": "host wall clock; arrivals replayed in real time"}
 
 
+def run_stream_only(args, B, inputs, dev):
+    """Only the 61-cell, 32-user streamed evaluation of 2^17 chromosomes (for
+    profilers)."""
+    import numpy as np
+    import torch
+
+    inst = inputs.instance(61, 32, seed=0, dtype=np.float32)
+    cfg = B.pa_config_default(61, 32, mode=B.PA_SINR_FINITE_M, M=512.0, tau_p=32, N=2048,
+                              rho=inst["rho"], kmeans_k=32)
+    ctx = B.Context(cfg, inst["beta"], inst["user_xy_mm"], inst["bs_xy_mm"])
+    n = 1 << 17
+    pop = inputs.random_population_torch(n, 61, 32, seed=7, device=dev)
+    fit = torch.empty(n, dtype=torch.float32, device=dev)
+    for _ in range(args.warmup + args.steps):
+        ctx.eval_population(pop, fit)
+    torch.cuda.synchronize()
+    print(json.dumps({"only": "stream", "launches": args.warmup + args.steps,
+                      "checksum": float(fit.double().sum().item())}))
+    ctx.close()
+    return 0
+
+
 def run_eval_only(args, B, inputs, ctx, stream, dev, rank):
     """Only the population evaluation of 2^20 chromosomes (for profilers)."""
     import torch
@@ -645,9 +669,10 @@ def main():
                     help="length of the Poisson arrival window of the serving comparison")
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the 512-instance batched-solve comparison")
-    ap.add_argument("--only", choices=["all", "eval", "solve"], default="all",
-                    help="eval / solve: run only the 2^20-chromosome evaluation or only the "
-                         "solves, untimed (for profilers)")
+    ap.add_argument("--only", choices=["all", "eval", "solve", "stream"], default="all",
+                    help="eval / solve / stream: run only the 2^20-chromosome evaluation, "
+                         "only the solves, or only the 61x32 streamed evaluation, untimed "
+                         "(for profilers)")
     args = ap.parse_args()
     if args.warmup < 3:
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)

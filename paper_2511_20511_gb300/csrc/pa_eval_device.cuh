@@ -74,6 +74,60 @@ __device__ __forceinline__ void decode_members(const uint8_t* src, int64_t membe
   }
 }
 
+// Same as decode_members with a row pitch KP >= K (KP/4 odd keeps the rows
+// of consecutive members in distinct banks): INV[(l*NT + c)*KP + p] = k.
+// Rows are read with 16- or 4-byte loads when K and the addresses allow.
+__device__ __forceinline__ void decode_members_kp(const uint8_t* src, int64_t member_stride,
+                                                  int nvalid, int NT, int L, int K, int KP,
+                                                  uint8_t* INV) {
+  const uintptr_t base = reinterpret_cast<uintptr_t>(src);
+  const bool v16 = K % 16 == 0 && base % 16 == 0 && member_stride % 16 == 0;
+  const bool v4 = !v16 && K % 4 == 0 && base % 4 == 0 && member_stride % 4 == 0;
+  for (int idx = threadIdx.x; idx < NT * L; idx += blockDim.x) {
+    const int l = idx / NT;
+    const int c = idx - l * NT;
+    uint8_t* dst = INV + idx * KP;
+    if (c < nvalid) {
+      const uint8_t* row = src + c * member_stride + (int64_t)l * K;
+      if (v16) {
+        for (int k0 = 0; k0 < K; k0 += 16) {
+          const uint4 w = __ldg(reinterpret_cast<const uint4*>(row + k0));
+          const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const int p = (ws[j >> 2] >> (8 * (j & 3))) & 0xff;
+            if (p < K) dst[p] = (uint8_t)(k0 + j);
+          }
+        }
+      } else if (v4) {
+        for (int k0 = 0; k0 < K; k0 += 4) {
+          const uint32_t w = __ldg(reinterpret_cast<const uint32_t*>(row + k0));
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const int p = (w >> (8 * j)) & 0xff;
+            if (p < K) dst[p] = (uint8_t)(k0 + j);
+          }
+        }
+      } else {
+        for (int k = 0; k < K; ++k) {
+          const int p = row[k];
+          if (p < K) dst[p] = (uint8_t)k;
+        }
+      }
+    } else {
+      for (int k = 0; k < K; ++k) dst[k] = (uint8_t)k;
+    }
+  }
+}
+
+// Row pitch for decode_members_kp: K rounded up to 4 bytes, an odd number
+// of words.
+__host__ __device__ __forceinline__ int inv_pitch(int K) {
+  int kp = (K + 3) & ~3;
+  if ((kp / 4) % 2 == 0) kp += 4;
+  return kp;
+}
+
 // ----------------------------------------------------------------- FP32
 // Packed two-lane FP32 arithmetic (sm_100 f32x2 instructions): one
 // instruction, two independent IEEE single-precision operations, each

@@ -39,7 +39,7 @@ __global__ void __launch_bounds__(kStreamThreads) k_eval_f32_stream(const Stream
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ __align__(8) uint64_t mbar;
   __shared__ int s_timeout;
-  const int L = a.L, K = a.K, LK = L * K, NTM = a.NTM, NTK = NTM * K;
+  const int L = a.L, K = a.K, LK = L * K, NTM = a.NTM, NTK = NTM * K, KP = inv_pitch(K);
   constexpr int NPR = JT / 2;
   float* TT = reinterpret_cast<float*>(smem);
   float* OWN = TT + a.tile_floats;
@@ -71,7 +71,7 @@ __global__ void __launch_bounds__(kStreamThreads) k_eval_f32_stream(const Stream
   for (int i = tid; i < LK; i += blockDim.x) OWN[i] = __ldg(a.own + i);
   if (FIN)
     for (int i = tid; i < L; i += blockDim.x) BN[i] = __ldg(a.bn + i);
-  for (int i = tid; i < L * NTK; i += blockDim.x) INV[i] = 0;
+  for (int i = tid; i < L * NTM * KP; i += blockDim.x) INV[i] = 0;
   // one thread waits (bounded) and the block leaves together on a timeout
   if (tid == 0 && !mbar_wait(mb, 0)) {
     atomicExch(a.err_flag, 1);
@@ -88,12 +88,15 @@ __global__ void __launch_bounds__(kStreamThreads) k_eval_f32_stream(const Stream
   for (int64_t mt = b; mt < mtiles; mt += nb) {
     const int64_t n0 = mt * NTM;
     const int nvalid = (int)((a.n - n0) < NTM ? (a.n - n0) : NTM);
-    decode_members(a.pop + n0 * LK, LK, nvalid, NTM, L, K, INV);
+    decode_members_kp(a.pop + n0 * LK, LK, nvalid, NTM, L, K, KP, INV);
     __syncthreads();
-    if (tid < NTK) eval_pilot_f32<JT, VEC, FIN, 1>(sm, INV + tid, NTK, 0, PART + tid * NPR);
+    if (tid < NTK) {
+      const int c = tid / K, p = tid - c * K;
+      eval_pilot_f32<JT, VEC, FIN, 1>(sm, INV + c * KP + p, NTM * KP, 0, PART + tid * NPR);
+    }
     __syncthreads();
     for (int c = warp; c < nvalid; c += blockDim.x >> 5) {
-      const float f = member_sum(PART + c * K * NPR, K * NPR, lane);
+      const float f = member_sum_bounded<32 * NPR>(PART + c * K * NPR, K * NPR, lane);
       if (lane == 0) a.partial[(n0 + c) * a.ntile + t] = f;
     }
     __syncthreads();
@@ -116,7 +119,7 @@ size_t stream_smem(int L, int K, int JT, int RSt, int NTM) {
   const size_t tile = ((LK * RSt + 3) / 4) * 4;
   const size_t NTK = (size_t)NTM * K;
   return 4 * (tile + ((LK + 3) & ~size_t(3)) + ((L + 3) & ~3) + ((NTK * (JT / 2) + 3) & ~size_t(3))) +
-         (((size_t)L * NTK + 15) & ~size_t(15));
+         (((size_t)L * NTM * inv_pitch(K) + 15) & ~size_t(15));
 }
 
 template <int JT, int VEC, bool FIN>
