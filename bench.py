@@ -37,9 +37,10 @@ L, K, TAU_P, M_ANT, N_POP, G_GEN, KMEANS_K = 19, 10, 10, 256.0, 256, 200, 10
 BATCH_LOG2 = 20
 # DRAM bytes (read + write) per launch of the two roofline kernels, from one
 # ncu capture each (profiles/k_solve_L19_K10_N256_G200.md,
-# profiles/k_eval_f32_pilot_2e20_L19_K10.md); None until captured
-TRAFFIC_K_SOLVE = None
-TRAFFIC_EVAL = None
+# profiles/k_eval_f32_pilot_2e20_L19_K10.md); set to None when a kernel
+# changes until it is captured again
+TRAFFIC_K_SOLVE = 150_528
+TRAFFIC_EVAL = 204_982_784
 METRIC = ("chromosome fitness evals/sec and GA gens/sec (L=19,K=10); "
           "p50/p99 solve latency served vs plain")
 WORKLOAD = ("single instance at paper-like scale: L=19 hex cells (2 rings), K=10 users/cell, "
