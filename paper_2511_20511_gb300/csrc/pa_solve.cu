@@ -90,79 +90,60 @@ __device__ __forceinline__ double shfl_xor_ft(double v, int off) {
 }
 
 // The E best members (fitness desc, index asc) of fit[0..N), E <= EMAX, by
-// one warp: each lane keeps a sorted list of its best E among members
-// lane, lane+32, ...; five xor-shuffle levels merge the lists.  Every lane
-// ends with the same list; lane 0 writes it to out[0..E).
-template <typename FT, int EMAX>
-__device__ __forceinline__ void warp_top_e(const FT* fit, int N, int E, int lane, int* out) {
-  int bi[EMAX];
-  FT bv[EMAX];
+// one warp in E rounds of a warp argmax: round e takes the best member not
+// chosen in rounds 0..e-1.  Each lane keeps the fitness of
+// its members lane, lane+32, ... (up to CACHE of them; larger populations
+// re-read the rest), so every round is a register scan and five shuffles.
+template <typename FT, int EMAX, int CACHE>
+__device__ __forceinline__ void warp_top_e_rounds(const FT* fit, int N, int E, int lane,
+                                                  int* out) {
+  FT vc[CACHE];
+#pragma unroll
+  for (int r = 0; r < CACHE; ++r) vc[r] = lane + 32 * r < N ? fit[lane + 32 * r] : (FT)0;
+  int chosen[EMAX];
 #pragma unroll
   for (int e = 0; e < EMAX; ++e) {
-    bi[e] = -1;
-    bv[e] = (FT)0;
-  }
-  for (int i = lane; i < N; i += 32) {
-    const FT v = fit[i];
-    // insert (v, i) into the sorted list (entries past E stay empty)
-    int ci = i;
-    FT cv = v;
+    chosen[e] = -1;
+    if (e < E) {
+      int best = -1;
+      FT bv = (FT)0;
 #pragma unroll
-    for (int e = 0; e < EMAX; ++e) {
-      if (e < E && ci >= 0 && (bi[e] < 0 || better_v(cv, ci, bv[e], bi[e]))) {
-        const int ti = bi[e];
-        const FT tv = bv[e];
-        bi[e] = ci;
-        bv[e] = cv;
-        ci = ti;
-        cv = tv;
-      }
-    }
-  }
+      for (int r = 0; r < CACHE; ++r) {
+        const int i = lane + 32 * r;
+        bool taken = i >= N;
 #pragma unroll
-  for (int off = 16; off > 0; off >>= 1) {
-    int oi[EMAX];
-    FT ov[EMAX];
-#pragma unroll
-    for (int e = 0; e < EMAX; ++e) {
-      oi[e] = __shfl_xor_sync(0xffffffffu, bi[e], off);
-      ov[e] = shfl_xor_ft(bv[e], off);
-    }
-    // merge two sorted lists, keep the first E
-    int mi[EMAX];
-    FT mv[EMAX];
-    int x = 0, y = 0;
-#pragma unroll
-    for (int e = 0; e < EMAX; ++e) {
-      int ai = -1, bi2 = -1;
-      FT av = (FT)0, bv2 = (FT)0;
-#pragma unroll
-      for (int k = 0; k < EMAX; ++k) {
-        if (k == x) {
-          ai = bi[k];
-          av = bv[k];
-        }
-        if (k == y) {
-          bi2 = oi[k];
-          bv2 = ov[k];
+        for (int f = 0; f < e; ++f) taken |= chosen[f] == i;
+        if (!taken && (best < 0 || better_v(vc[r], i, bv, best))) {
+          best = i;
+          bv = vc[r];
         }
       }
-      const bool take_a = ai >= 0 && (bi2 < 0 || better_v(av, ai, bv2, bi2));
-      mi[e] = take_a ? ai : bi2;
-      mv[e] = take_a ? av : bv2;
-      x += take_a ? 1 : 0;
-      y += take_a ? 0 : 1;
-    }
+      for (int i = lane + 32 * CACHE; i < N; i += 32) {
+        bool taken = false;
 #pragma unroll
-    for (int e = 0; e < EMAX; ++e) {
-      bi[e] = e < E ? mi[e] : -1;
-      bv[e] = mv[e];
+        for (int f = 0; f < e; ++f) taken |= chosen[f] == i;
+        const FT v = fit[i];
+        if (!taken && (best < 0 || better_v(v, i, bv, best))) {
+          best = i;
+          bv = v;
+        }
+      }
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) {
+        const int o = __shfl_xor_sync(0xffffffffu, best, off);
+        const FT ov = shfl_xor_ft(bv, off);
+        if (o >= 0 && (best < 0 || better_v(ov, o, bv, best))) {
+          best = o;
+          bv = ov;
+        }
+      }
+      chosen[e] = best;
     }
   }
   if (lane == 0)
 #pragma unroll
     for (int e = 0; e < EMAX; ++e)
-      if (e < E) out[e] = bi[e];
+      if (e < E) out[e] = chosen[e];
 }
 
 // Tournament over draws dr[0 .. T): candidates uniform with replacement,
@@ -411,11 +392,11 @@ __device__ __forceinline__ void solve_body(const SolveArgs& a, unsigned char* sm
     // ---- 2. all fitness values and members of generation g are visible
     cluster.sync();
     if (g == a.G) break;
+    const bool small_e = E <= kSmallE;
     // ---- 3. elites (CTA holding slots below E).  For E <= 8 warp 0 alone
     //         finds them (register lists) and then fills the elite slots while
     //         the other warps build the other children; for larger E every
     //         warp takes a stripe of the population and warp 0 merges.
-    const bool small_e = E <= kSmallE;
     if (n_elite_here > 0 && !small_e) {
       const int stripe = (N + nwarps - 1) / nwarps;
       const int lo = warp * stripe, hi = min(N, lo + stripe);
@@ -483,11 +464,9 @@ __device__ __forceinline__ void solve_body(const SolveArgs& a, unsigned char* sm
     }
     if (n_elite_here > 0 && small_e && warp == 0) {
       if (E <= 2)
-        warp_top_e<FT, 2>(fit, N, E, lane, elites);
-      else if (E <= 4)
-        warp_top_e<FT, 4>(fit, N, E, lane, elites);
+        warp_top_e_rounds<FT, 2, 8>(fit, N, E, lane, elites);
       else
-        warp_top_e<FT, kSmallE>(fit, N, E, lane, elites);
+        warp_top_e_rounds<FT, kSmallE, 8>(fit, N, E, lane, elites);
       __syncwarp();
     }
     // ---- 4. children of this CTA's slots: warp w builds slots w, w+nwarps, ...
