@@ -202,10 +202,15 @@ static void free_ctx(pa_ctx* c) {
   cudaFree(c->fit);
   cudaFree(c->scratch_i64);
   cudaFree(c->best_row);
+  cudaFreeHost(c->h_best);
   cudaFree(c->stage_pop);
   cudaFree(c->stage_fit);
   delete c;
 }
+
+// Device bytes of the best-member slot: the row, then its FP64 fitness at
+// the next 8-byte boundary.
+static size_t best_bytes(int64_t LK) { return (size_t)(((LK + 7) & ~int64_t(7)) + 8); }
 
 pa_status pa_create(const pa_config* cfg, const double* beta, const int32_t* user_xy_mm,
                     const int32_t* bs_xy_mm, void* stream, pa_ctx** out) {
@@ -286,7 +291,9 @@ pa_status pa_create(const pa_config* cfg, const double* beta, const int32_t* use
     if (!chk(cudaMalloc(&c->pop[1], (size_t)cfg->N * LK), "cudaMalloc pop1")) break;
     if (!chk(cudaMalloc(&c->fit, fsz * cfg->N), "cudaMalloc fit")) break;
     if (!chk(cudaMalloc(&c->scratch_i64, sizeof(int64_t) * 8), "cudaMalloc scratch")) break;
-    if (!chk(cudaMalloc(&c->best_row, (size_t)LK), "cudaMalloc best")) break;
+    // best row, then its fitness at the next 8-byte boundary (one copy back)
+    if (!chk(cudaMalloc(&c->best_row, best_bytes(LK)), "cudaMalloc best")) break;
+    if (!chk(cudaMallocHost(&c->h_best, best_bytes(LK)), "cudaMallocHost best")) break;
     st = upload_instance(c, beta, user_xy_mm, bs_xy_mm, bmax);
     if (st != PA_OK) break;
     if (!chk(cudaStreamSynchronize(c->stream), "prepare sync")) break;
@@ -479,7 +486,8 @@ pa_status pa_solve(pa_ctx* ctx, int32_t generations, uint8_t* best_host, double*
   if (generations < 0) return fail(ctx, PA_EINVAL, "generations must be >= 0");
   pa_status st = pa_kmeans_seed(ctx, nullptr, nullptr);
   if (st != PA_OK) return st;
-  double* best_dev = reinterpret_cast<double*>(ctx->scratch_i64);
+  const int64_t LK = (int64_t)ctx->cfg.L * ctx->cfg.K;
+  double* best_dev = reinterpret_cast<double*>(ctx->best_row + ((LK + 7) & ~int64_t(7)));
   // fused path: all generations, the final evaluation and the best member
   // in one cluster launch
   cudaError_t e = pa::launch_solve(ctx, ctx->pop[0], ctx->pop[1], 0, generations, ctx->fit,
@@ -498,16 +506,14 @@ pa_status pa_solve(pa_ctx* ctx, int32_t generations, uint8_t* best_host, double*
   } else {
     return cuda_check(ctx, e, "solve kernel");
   }
-  const int64_t LK = (int64_t)ctx->cfg.L * ctx->cfg.K;
-  if (best_host)
-    PA_TRY(ctx, cudaMemcpyAsync(best_host, ctx->best_row, (size_t)LK, cudaMemcpyDeviceToHost,
-                                ctx->stream),
+  // the best row and its fitness come back in one copy to pinned memory
+  if (best_host || best_fit)
+    PA_TRY(ctx, cudaMemcpyAsync(ctx->h_best, ctx->best_row, best_bytes(LK),
+                                cudaMemcpyDeviceToHost, ctx->stream),
            "copy best");
-  if (best_fit)
-    PA_TRY(ctx, cudaMemcpyAsync(best_fit, best_dev, sizeof(double), cudaMemcpyDeviceToHost,
-                                ctx->stream),
-           "copy best fit");
   PA_TRY(ctx, cudaStreamSynchronize(ctx->stream), "sync");
+  if (best_host) std::memcpy(best_host, ctx->h_best, (size_t)LK);
+  if (best_fit) std::memcpy(best_fit, ctx->h_best + ((LK + 7) & ~int64_t(7)), sizeof(double));
   return check_timeout(ctx);
 }
 

@@ -570,6 +570,7 @@ cudaError_t launch_seed(pa_ctx* ctx, uint8_t* pop, cudaStream_t st) {
   cudaError_t e = cudaErrorNotSupported;
   for (int C : {16, 8, 4, 2, 1}) {
     if (C > c.L && C > 1) continue;
+    if (ctx->seed_C > 0 && C != ctx->seed_C) continue;  // chosen on an earlier call
     const size_t smem = seed_smem(c.L, c.K, c.kmeans_k, kSeedClusterThreads, C);
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(C, 1, 1);
@@ -583,14 +584,18 @@ cudaError_t launch_seed(pa_ctx* ctx, uint8_t* pop, cudaStream_t st) {
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    int nclusters = 0;
-    if (cudaOccupancyMaxActiveClusters(&nclusters, k_seed, &cfg) != cudaSuccess || nclusters < 1) {
-      (void)cudaGetLastError();
-      continue;
+    if (ctx->seed_C < 0) {
+      int nclusters = 0;
+      if (cudaOccupancyMaxActiveClusters(&nclusters, k_seed, &cfg) != cudaSuccess ||
+          nclusters < 1) {
+        (void)cudaGetLastError();
+        continue;
+      }
     }
     (void)cudaGetLastError();  // drop a stale error of an earlier call
     e = cudaLaunchKernelEx(&cfg, k_seed, a);
     count_launch();
+    if (e == cudaSuccess) ctx->seed_C = C;
     break;
   }
   if (e != cudaSuccess) return e;

@@ -67,11 +67,13 @@ struct pa_ctx {
   void* fit = nullptr;         // [N] float or double
   int32_t generation = 0;
   int solve_C = -1;            // cluster size of the fused solve kernel (-1: not chosen, 0: none)
+  int seed_C = -1;             // cluster size of the seeding kernel (-1: not chosen)
   int wait_check = 0;          // an FP32 evaluation ran since t32.err_flag was last read
   int test_stall = 0;          // PA_FLAG_TEST_STALL_COPIES still pending (one-shot)
   // scratch
   int64_t* scratch_i64 = nullptr;  // small device scratch (flags, argbest)
-  uint8_t* best_row = nullptr;     // [L*K]
+  uint8_t* best_row = nullptr;     // [L*K], then the best fitness (double) 8-byte aligned
+  uint8_t* h_best = nullptr;       // pinned host copy of the same bytes
   // host staging for *_host calls
   uint8_t* stage_pop = nullptr;
   void* stage_fit = nullptr;
