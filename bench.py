@@ -39,7 +39,7 @@ BATCH_LOG2 = 20
 # ncu capture each (profiles/k_solve_L19_K10_N256_G200.md,
 # profiles/k_eval_f32_pilot_2e20_L19_K10.md); set to None when a kernel
 # changes until it is captured again
-TRAFFIC_K_SOLVE = None
+TRAFFIC_K_SOLVE = 146_432
 TRAFFIC_EVAL = 204_982_784
 METRIC = ("chromosome fitness evals/sec and GA gens/sec (L=19,K=10); "
           "p50/p99 solve latency served vs plain")
