@@ -116,6 +116,25 @@ def dist_setup():
     return world, rank, local
 
 
+def max_over_ranks(x, world, device):
+    """The largest x over all ranks (x itself with one rank)."""
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(world, steps, units_per_step, seconds):
+    """Whole-job throughput: every rank processes its own units (its own
+    instance: weak scaling, no data-path collective) and the job takes the
+    slowest rank's time."""
+    return world * steps * units_per_step / seconds
+
+
 def make_instance(seed):
     import numpy as np
 
@@ -203,12 +222,6 @@ def run_ours(args):
         if world > 1:
             torch.distributed.barrier()
 
-    def max_over_ranks(x):
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        return float(t.item())
 
     from paper_2511_20511_gb300 import binding as B
     from paper_2511_20511_gb300 import build as pa_build
@@ -267,9 +280,9 @@ def run_ours(args):
     torch.cuda.synchronize()
     barrier()
     clk = clocks.stop()
-    total_s = max_over_ranks(sum(step_ms) / 1e3)
-    value = world * args.steps * N_POP * (G_GEN + 1) / total_s
-    gens = world * args.steps * G_GEN / total_s
+    total_s = max_over_ranks(sum(step_ms) / 1e3, world, dev)
+    value = job_value(world, args.steps, N_POP * (G_GEN + 1), total_s)
+    gens = job_value(world, args.steps, G_GEN, total_s)
 
     # ---- end to end through host buffers (pinned): fresh instance upload +
     #      solve + best member back to the host, every step
@@ -288,7 +301,7 @@ def run_ours(args):
     t0 = time.perf_counter()
     e2e_ms = timed(e2e_step, args.steps, flush_between=False)
     wall_e2e = time.perf_counter() - t0
-    e2e_total = max_over_ranks(max(sum(e2e_ms) / 1e3, wall_e2e))
+    e2e_total = max_over_ranks(max(sum(e2e_ms) / 1e3, wall_e2e), world, dev)
     h2d = keep[0].nbytes + keep[1].nbytes + keep[2].nbytes
     d2h = best.nbytes + 8
 
@@ -367,7 +380,8 @@ def run_ours(args):
                        "avg_launch_ms": ev_avg * 1e3},
         "roofline": roofline,
         "roofline_eval_batch": roofline_eval,
-        "e2e": {"value": world * args.steps * N_POP * (G_GEN + 1) / e2e_total, "unit": "evals/s",
+        "e2e": {"value": job_value(world, args.steps, N_POP * (G_GEN + 1), e2e_total),
+                "unit": "evals/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "what": "pa_load_instance (pinned host beta + positions) + pa_solve (best row "
                         "and fitness back to host) per step"},
