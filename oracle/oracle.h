@@ -36,7 +36,8 @@ typedef struct {
   double sigma2;  /* noise variance */
 } or_sinr_params;
 
-/* GA parameters (Alg. 1; operators per the reading documented in the design doc). */
+/* GA parameters (Alg. 1): elitism, tournament with replacement, row-wise
+   one-cut crossover, per-row swap mutation. */
 typedef struct {
   int32_t N;          /* population size */
   int32_t E;          /* elites */
