@@ -14,6 +14,9 @@
  *
  * Parity status of every function is listed in its comment; all are pinned
  * by tests under tests/ (see test_oracle_*.py) unless stated otherwise.
+ * Parity unpinned: whether the GA as a whole reproduces the paper's
+ * convergence figures (Fig. 4, 82 s / 116 s) -- the paper's runs, seeds and
+ * data are not available; every function here is pinned.
  */
 #ifndef PA_ORACLE_H
 #define PA_ORACLE_H
