@@ -11,16 +11,20 @@
 //   sinr = M b^2 / (M S2 + (B_j + s2/rho)(S1 + s2/(tau_p rho)))   (Eq. 3 reading)
 // with b = beta[j][j][k], SE = log2(1 + sinr) (Eq. 5), fitness = sum SE (Eq. 6).
 //
-// FP32 kernel (throughput path).  One thread per (chromosome, pilot p).  It
-// walks the L cells; for cell l it reads one row of a BS-minor table --
-// the gains of user inv_l(p) at all BSs, own-cell entry zeroed -- and adds the
-// row into NJ register accumulators (one per BS j).  Total shared-memory
+// FP32 kernels (throughput path).  A thread owns (chromosome, pilot p) and
+// walks the L cells; for cell l it reads one row of a BS-minor table -- the
+// gains of user inv_l(p) at all BSs, own-cell entry zeroed -- and adds the
+// row into register accumulators (one per BS j).  Total shared-memory
 // traffic per chromosome is L*K rows of NJ words: the L^2 K gathers that
 // Eq. 5 needs, each word read once.  The table lives in shared memory for the
 // whole (grid-stride) kernel.  Row stride RS makes every warp access
 // bank-conflict free: lanes that read the same (l, u) row read the same
 // address (broadcast) and distinct u land in distinct banks (float2 loads,
 // RS/2 odd, K <= 16; scalar loads, RS odd, K <= 32).
+//   k_eval_f32_pilot (K <= 16, L <= 24): one thread per (chromosome, pilot)
+//     over all columns; chromosome tiles staged by bulk copies.
+//   k_eval_f32 (other shapes): the columns split in two shares taken by the
+//     two half-warps, chromosomes decoded from global memory.
 //
 // FP64 kernel (parity path).  One thread per user (j, k) of a chromosome,
 // the oracle's operation order exactly: ascending-l sums, separately rounded
