@@ -629,11 +629,13 @@ size_t seed_fill_args(pa_ctx* ctx, void* out, int C) {
 }
 
 int seed_batch_cluster(int n) {
-  // clusters of 16 CTAs while the whole batch stays resident on the GPU
-  // (<= 9 instances on 152 SMs), then 8, 4, 2, 1
-  for (int C : {16, 8, 4, 2})
+  // clusters of 16 CTAs while the whole batch fits the GPU at once (<= 9
+  // instances on 152 SMs), else 8; larger batches run in waves of 4-CTA
+  // clusters (each instance's K-means is a latency chain: splitting its
+  // cells over CTAs shortens it, and the waves keep every SM busy)
+  for (int C : {16, 8})
     if (n * C <= 152) return C;
-  return 1;
+  return 4;
 }
 
 cudaError_t launch_seed_batch(const void* d_args, int n, size_t smem, int C, cudaStream_t st) {
