@@ -240,10 +240,21 @@ def test_random_seed_without_positions(B, oracle):
 @pytest.mark.parametrize("L,K,N,G,mode", [(7, 4, 32, 50, 0), (7, 4, 32, 50, 1),
                                           (19, 10, 256, 200, 1)])
 def test_fp64_trajectory_bit_exact(B, oracle, L, K, N, G, mode):
+    _fp64_trajectory(B, oracle, L, K, N, G, mode)
+
+
+@pytest.mark.parametrize("E", [0, 1, 5, 8, 12, 31])
+def test_fp64_trajectory_elite_counts(B, oracle, E):
+    """Every elite path of the fused solve (none; rounds of a warp argmax for
+    E <= 8; striped search and merge for larger E) against the oracle."""
+    _fp64_trajectory(B, oracle, 7, 4, 48, 30, 1, E=E)
+
+
+def _fp64_trajectory(B, oracle, L, K, N, G, mode, **kw):
     """FP64 mode reproduces the oracle's whole solve: K-means seeding, every
     generation's fitness, selection, crossover and mutation, bit for bit."""
     inst = inputs.instance(L, K, seed=0, dtype=np.float64 if L == 7 else np.float32)
-    cfg = _cfg(B, L, K, B.PA_FP64, mode, M=128.0 if L == 7 else 256.0, N=N, seed=0)
+    cfg = _cfg(B, L, K, B.PA_FP64, mode, M=128.0 if L == 7 else 256.0, N=N, seed=0, **kw)
     ctx = B.pa_create(cfg, inst["beta"], inst["user_xy_mm"], inst["bs_xy_mm"])
     try:
         best = np.zeros((L, K), dtype=np.uint8)
@@ -314,7 +325,8 @@ def test_checkpoint_resume_bit_exact(B):
 
 
 @pytest.mark.parametrize("L,K,N,E,mode", [(19, 10, 256, 2, 1), (7, 4, 32, 2, 0), (37, 16, 130, 5, 1),
-                                          (19, 17, 100, 3, 0), (7, 1, 9, 0, 1)])
+                                          (19, 17, 100, 3, 0), (7, 1, 9, 0, 1), (19, 10, 200, 12, 1),
+                                          (7, 4, 64, 8, 0)])
 def test_fused_generations_equal_per_generation_kernels(B, L, K, N, E, mode):
     """pa_step runs all generations in one cluster launch; the same
     generations driven one kernel pair at a time through pa_eval_population
