@@ -260,6 +260,16 @@ def run_ours(args):
         return run_eval_only(args, B, inputs, ctx, stream, dev, rank)
     if args.only == "stream":
         return run_stream_only(args, B, inputs, dev)
+    if args.only == "batch":
+        insts = c3_instances(B, inputs, 512)
+        batch = B.Batch(insts)
+        for _ in range(args.warmup + args.steps):
+            batch.solve(100)
+        torch.cuda.synchronize()
+        print(json.dumps({"only": "batch", "solves": args.warmup + args.steps}))
+        batch.close()
+        ctx.close()
+        return 0
     if args.only == "solve":
         for _ in range(args.warmup + args.steps):
             ctx.solve(G_GEN)
@@ -684,10 +694,11 @@ def main():
                     help="length of the Poisson arrival window of the serving comparison")
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the 512-instance batched-solve comparison")
-    ap.add_argument("--only", choices=["all", "eval", "solve", "stream"], default="all",
-                    help="eval / solve / stream: run only the 2^20-chromosome evaluation, "
-                         "only the solves, or only the 61x32 streamed evaluation, untimed "
-                         "(for profilers)")
+    ap.add_argument("--only", choices=["all", "eval", "solve", "stream", "batch"],
+                    default="all",
+                    help="eval / solve / stream / batch: run only the 2^20-chromosome "
+                         "evaluation, the solves, the 61x32 streamed evaluation or the "
+                         "512-instance batched solve, untimed (for profilers)")
     args = ap.parse_args()
     if args.warmup < 3:
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)

@@ -27,570 +27,10 @@
 #include <atomic>
 #include <mutex>
 
-#include "pa_eval_device.cuh"
-
-namespace cg = cooperative_groups;
+#include "pa_solve_body.cuh"
 
 namespace pa {
 namespace {
-
-constexpr int kSolveThreads = 1024;
-constexpr int kSmallE = 8;  // elites found by one warp in registers up to this E
-
-struct SolveArgs {
-  const uint8_t* pop_in;  // N*LK, starting population
-  uint8_t* pop_out;       // N*LK, final population
-  void* fit_out;          // N fitness values of the final population
-  uint8_t* best_row;      // LK, or null
-  double* best_fit;       // 1, or null
-  int N, L, K, E, tour;
-  uint64_t pc_thresh, pm_thresh, seed;
-  int gen0, G;
-  int NT;    // members per CTA
-  int MS;    // member record size in shared memory (bytes): X, then INV at XO
-  int XO;    // offset of the inverse permutation inside a record
-  int NTT;   // members per evaluation pass
-  int nblk;  // Philox blocks of draws per child
-  int CH;    // children whose draws are staged at once
-  // FP32 tables
-  const float* tab;
-  const float* own;
-  const float* bn;
-  int RS;
-  int64_t tab_floats;
-  float M32, pc32;
-  // FP64 data
-  const double* beta;
-  const double* bnc;
-  double M64, pc64;
-  int fin;
-};
-
-template <typename FT>
-__device__ __forceinline__ bool better_s(const FT* fit, int a, int b) {
-  const FT fa = fit[a], fb = fit[b];
-  if (fa > fb) return true;
-  if (fa < fb) return false;
-  return a < b;
-}
-
-// "member i with fitness v is better than member b with fitness bv": higher
-// fitness, or not lower (equal or unordered) and a lower index.
-template <typename FT>
-__device__ __forceinline__ bool better_v(FT v, int i, FT bv, int b) {
-  if (v > bv) return true;
-  if (v < bv) return false;
-  return i < b;
-}
-__device__ __forceinline__ float shfl_xor_ft(float v, int off) {
-  return __shfl_xor_sync(0xffffffffu, v, off);
-}
-__device__ __forceinline__ double shfl_xor_ft(double v, int off) {
-  return __shfl_xor_sync(0xffffffffu, v, off);
-}
-
-// The E best members (fitness desc, index asc) of fit[0..N), E <= EMAX, by
-// one warp in E rounds of a warp argmax: round e takes the best member not
-// chosen in rounds 0..e-1.  Each lane keeps the fitness of
-// its members lane, lane+32, ... (up to CACHE of them; larger populations
-// re-read the rest), so every round is a register scan and five shuffles.
-template <typename FT, int EMAX, int CACHE>
-__device__ __forceinline__ void warp_top_e_rounds(const FT* fit, int N, int E, int lane,
-                                                  int* out) {
-  FT vc[CACHE];
-#pragma unroll
-  for (int r = 0; r < CACHE; ++r) vc[r] = lane + 32 * r < N ? fit[lane + 32 * r] : (FT)0;
-  int chosen[EMAX];
-#pragma unroll
-  for (int e = 0; e < EMAX; ++e) {
-    chosen[e] = -1;
-    if (e < E) {
-      int best = -1;
-      FT bv = (FT)0;
-#pragma unroll
-      for (int r = 0; r < CACHE; ++r) {
-        const int i = lane + 32 * r;
-        bool taken = i >= N;
-#pragma unroll
-        for (int f = 0; f < e; ++f) taken |= chosen[f] == i;
-        if (!taken && (best < 0 || better_v(vc[r], i, bv, best))) {
-          best = i;
-          bv = vc[r];
-        }
-      }
-      for (int i = lane + 32 * CACHE; i < N; i += 32) {
-        bool taken = false;
-#pragma unroll
-        for (int f = 0; f < e; ++f) taken |= chosen[f] == i;
-        const FT v = fit[i];
-        if (!taken && (best < 0 || better_v(v, i, bv, best))) {
-          best = i;
-          bv = v;
-        }
-      }
-#pragma unroll
-      for (int off = 16; off > 0; off >>= 1) {
-        const int o = __shfl_xor_sync(0xffffffffu, best, off);
-        const FT ov = shfl_xor_ft(bv, off);
-        if (o >= 0 && (best < 0 || better_v(ov, o, bv, best))) {
-          best = o;
-          bv = ov;
-        }
-      }
-      chosen[e] = best;
-    }
-  }
-  if (lane == 0)
-#pragma unroll
-    for (int e = 0; e < EMAX; ++e)
-      if (e < E) out[e] = chosen[e];
-}
-
-// Tournament over draws dr[0 .. T): candidates uniform with replacement,
-// the best by (fitness desc, index asc) wins.  Every lane computes it.
-template <typename FT>
-__device__ __forceinline__ int tournament_lane(const FT* fit, int N, int T, const uint32_t* dr) {
-  constexpr int kU = 4;  // candidates fetched together
-  int best = -1;
-  FT bv = (FT)0;
-  for (int t0 = 0; t0 < T; t0 += kU) {
-    int c[kU];
-    FT v[kU];
-#pragma unroll
-    for (int u = 0; u < kU; ++u) c[u] = t0 + u < T ? (int)below(dr[t0 + u], (uint32_t)N) : -1;
-#pragma unroll
-    for (int u = 0; u < kU; ++u) v[u] = c[u] >= 0 ? fit[c[u]] : (FT)0;
-#pragma unroll
-    for (int u = 0; u < kU; ++u)
-      if (c[u] >= 0 && (best < 0 || better_v(v[u], c[u], bv, best))) {
-        best = c[u];
-        bv = v[u];
-      }
-  }
-  return best;
-}
-
-// Block-wide best member by (fitness desc, index asc), skipping excluded[0..nex).
-template <typename FT>
-__device__ int block_best_s(const FT* fit, int N, const int* excluded, int nex, int* red) {
-  int best = -1;
-  for (int i = threadIdx.x; i < N; i += blockDim.x) {
-    bool skip = false;
-    for (int e = 0; e < nex; ++e) skip |= (excluded[e] == i);
-    if (skip) continue;
-    if (best < 0 || better_s(fit, i, best)) best = i;
-  }
-  for (int off = 16; off > 0; off >>= 1) {
-    const int o = __shfl_down_sync(0xffffffffu, best, off);
-    if (o >= 0 && (best < 0 || better_s(fit, o, best))) best = o;
-  }
-  __syncthreads();
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = best;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    int b = -1;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-      const int o = red[w];
-      if (o >= 0 && (b < 0 || better_s(fit, o, b))) b = o;
-    }
-    red[32] = b;
-  }
-  __syncthreads();
-  const int r = red[32];
-  __syncthreads();
-  return r;
-}
-
-__device__ __forceinline__ void swap2(uint8_t* row, int K, uint32_t ui, uint32_t uj) {
-  if (K < 2) return;
-  const int i = (int)below(ui, (uint32_t)K);
-  const int jj = (int)below(uj, (uint32_t)(K - 1));
-  const int j = jj + (jj >= i ? 1 : 0);
-  const uint8_t t = row[i];
-  row[i] = row[j];
-  row[j] = t;
-}
-
-// 32-bit word w of a child: bytes below `split` from parent A, the rest from
-// parent B (row-wise crossover cut at a byte offset).
-__device__ __forceinline__ uint32_t merge_word(uint32_t a, uint32_t b, int w, int64_t split) {
-  const int64_t lo = 4 * (int64_t)w;
-  if (lo + 4 <= split) return a;
-  if (lo >= split) return b;
-  const int na = (int)(split - lo);  // 1..3 bytes from A
-  const uint32_t mask = (1u << (8 * na)) - 1u;
-  return (a & mask) | (b & ~mask);
-}
-
-// Remote 32-bit load from another CTA's shared memory (distributed shared
-// memory): `addr` is a shared::cluster address from mapa.
-__device__ __forceinline__ uint32_t ld_dsmem(uint32_t addr) {
-  uint32_t v;
-  asm volatile("ld.shared::cluster.u32 %0, [%1];" : "=r"(v) : "r"(addr));
-  return v;
-}
-__device__ __forceinline__ uint32_t dsmem_addr(const void* local, int rank) {
-  uint32_t a = (uint32_t)__cvta_generic_to_shared(local), r;
-  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
-  return r;
-}
-
-// Column pairs per thread in the fused FP32 evaluation: the largest divisor
-// of NJ/2 not above MAXNP; JS = NJ/2 / NP threads share a (member, pilot).
-// More threads per pilot finish an evaluation pass sooner (one instance on a
-// 16-CTA cluster is latency-bound: MAXNP 2); fewer, longer threads issue
-// fewer index and address instructions per table word (batched instances
-// with many members per CTA are issue-bound: MAXNP 5).  The sums are the
-// same whatever the split.
-constexpr int kSoloMaxNP = 2;
-constexpr int kBatchMaxNP = 5;
-__host__ __device__ constexpr int fused_np(int NJ, int maxnp) {
-  int np = maxnp < NJ / 2 ? maxnp : NJ / 2;
-  while (np > 1 && (NJ / 2) % np != 0) --np;
-  return np < 1 ? 1 : np;
-}
-__host__ __device__ constexpr int fused_js(int NJ, int maxnp) {
-  return (NJ / 2) / fused_np(NJ, maxnp);
-}
-
-// Member record in shared memory (MS bytes): the chromosome X (L*K bytes,
-// pilot of each user) at offset 0 and its inverse INV (L*K bytes, user of
-// each pilot, row by row) at offset XO.  Crossover takes whole rows, so the
-// child's INV rows are its parents' INV rows; a swap mutation updates both.
-template <typename FT, int NJ, int VEC, bool FIN, int MAXNP>
-__device__ __forceinline__ void solve_body(const SolveArgs& a, unsigned char* smem, int* elites,
-                                           cg::cluster_group& cluster) {
-  const int rank = (int)cluster.block_rank();
-  const int C = (int)cluster.num_blocks();
-  const int tid = threadIdx.x;
-  const int L = a.L, K = a.K, N = a.N, NT = a.NT, MS = a.MS, XO = a.XO;
-  const int LK = L * K;
-  constexpr bool F64 = sizeof(FT) == 8;
-  constexpr int JS = F64 ? 1 : fused_js(NJ, MAXNP);
-  constexpr int NPR = NJ / 2;  // column pairs per (member, pilot)
-
-  // ---- carve shared memory
-  unsigned char* p = smem;
-  float* T = nullptr;
-  float* OWN = nullptr;
-  float* BN = nullptr;
-  if (!F64) {
-    T = reinterpret_cast<float*>(p);
-    p += 4 * a.tab_floats;
-    OWN = reinterpret_cast<float*>(p);
-    p += 4 * ((LK + 3) & ~3);
-    BN = reinterpret_cast<float*>(p);
-    p += 4 * ((L + 3) & ~3);
-  }
-  // double buffers are addressed as offsets from the shared-memory base
-  const int fit_off0 = (int)(p - smem);
-  p += sizeof(FT) * ((N + 1) & ~1);
-  const int fit_off1 = (int)(p - smem);
-  p += sizeof(FT) * ((N + 1) & ~1);
-  auto FITp = [&](int b) { return reinterpret_cast<FT*>(smem + (b ? fit_off1 : fit_off0)); };
-  double* SE = reinterpret_cast<double*>(p);  // FP64: NTT*LK per-user SE
-  float* PART = reinterpret_cast<float*>(p);  // FP32: NTT*K*NPR per-(pilot, pair) SE
-  p += F64 ? 8 * (size_t)a.NTT * LK : 4 * (size_t)((a.NTT * K * NPR + 3) & ~3);
-  const int pop_off0 = (int)(p - smem);
-  p += (size_t)NT * MS;
-  const int pop_off1 = (int)(p - smem);
-  p += (size_t)NT * MS;
-  auto POPp = [&](int b) { return smem + (b ? pop_off1 : pop_off0); };
-  uint32_t* DR = reinterpret_cast<uint32_t*>(p);  // [CH][nblk*8] draws of staged children
-  p += (size_t)a.CH * a.nblk * 32;
-  FT* CV = reinterpret_cast<FT*>(p);  // [32][E] elite candidates (value)
-  int* CI = reinterpret_cast<int*>(p + sizeof(FT) * 32 * 64);  // [32][E] (index)
-
-  const int base_n = rank * NT;
-  const int nvalid = max(0, min(NT, N - base_n));
-
-  // ---- stage tables and own members (X and its inverse)
-  if (!F64) {
-    const float4* s4 = reinterpret_cast<const float4*>(a.tab);
-    float4* d4 = reinterpret_cast<float4*>(T);
-    for (int64_t i = tid; i < a.tab_floats / 4; i += blockDim.x) d4[i] = __ldg(s4 + i);
-    for (int i = tid; i < LK; i += blockDim.x) OWN[i] = __ldg(a.own + i);
-    if (FIN)
-      for (int i = tid; i < L; i += blockDim.x) BN[i] = __ldg(a.bn + i);
-  }
-  for (int i = tid; i < NT * MS; i += blockDim.x) POPp(0)[i] = 0;
-  __syncthreads();
-  for (int i = tid; i < nvalid * LK; i += blockDim.x) {
-    const int c = i / LK, r = i - c * LK;
-    POPp(0)[c * MS + r] = a.pop_in[(int64_t)base_n * LK + i];
-  }
-  __syncthreads();
-  for (int i = tid; i < nvalid * L; i += blockDim.x) {
-    const int c = i / L, l = i - c * L;
-    const uint8_t* x = POPp(0) + c * MS + l * K;
-    uint8_t* inv = POPp(0) + c * MS + XO + l * K;
-    for (int k = 0; k < K; ++k) {
-      const int q = x[k];
-      if (q < K) inv[q] = (uint8_t)k;
-    }
-  }
-  __syncthreads();
-  const F32Smem sm{T, OWN, BN, L, K, a.RS, a.M32, a.pc32};
-
-  int cur = 0;
-  const int lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
-  const int T_ = a.tour, nblk = a.nblk, E = a.E;
-  const int nwords = MS >> 2;
-  // FP32 evaluation roles: q = member*K + pilot, column-pair share h.  Each
-  // half-warp takes 16 consecutive q with one share h, so the 16 rows it
-  // reads in a step (distinct users, RS/2 odd; equal users read the same
-  // address) fall in distinct banks
-  const int q = (tid / (16 * JS)) * 16 + (tid & 15), h = (tid >> 4) % JS;
-  const bool one_chunk = nvalid <= a.CH;
-  const int n_elite_here = max(0, min(E - base_n, nvalid));
-  for (int g = 0;; ++g) {
-    FT* fit = FITp(g & 1);
-    const unsigned char* popc = POPp(cur);
-    // ---- 1. evaluate own members, broadcast their fitness.  When all
-    //         children fit in one draw chunk, the threads the evaluation
-    //         leaves idle generate this generation's draws meanwhile (draws
-    //         do not depend on fitness).
-    bool drawn = false;
-    for (int c0 = 0; c0 < nvalid; c0 += a.NTT) {
-      const int nv = min(a.NTT, nvalid - c0);
-      if (!F64) {
-        const int eval_threads = ((nv * K + 15) / 16) * 16 * JS;  // threads up to the last q
-        if (q < nv * K) {
-          const int c = q / K, pp = q - c * K;
-          eval_pilot_f32<NJ, VEC, FIN, JS>(sm, popc + (c0 + c) * MS + XO + pp, K, h,
-                                           PART + q * NPR + h * (NPR / JS));
-        } else if (c0 == 0 && one_chunk && g < a.G && eval_threads + 32 <= (int)blockDim.x &&
-                   tid >= ((eval_threads + 31) & ~31)) {
-          const int t0 = (eval_threads + 31) & ~31;
-          gen_child_draws_from(DR, base_n, nvalid, nblk, a.seed, (uint64_t)(a.gen0 + g), E,
-                               tid - t0, blockDim.x - t0);
-        }
-        if (c0 == 0 && one_chunk && eval_threads + 32 <= (int)blockDim.x) drawn = true;
-        __syncthreads();
-        for (int c = warp; c < nv; c += nwarps) {
-          const float f = member_sum_bounded<16 * NPR>(PART + c * K * NPR, K * NPR, lane);
-          const int n = base_n + c0 + c;
-          if (lane < C) cluster.map_shared_rank(fit, lane)[n] = (FT)f;
-        }
-      } else {
-        for (int i = tid; i < nv * LK; i += blockDim.x) {
-          const int c = i / LK, u = i - c * LK, j = u / K, k = u - j * K;
-          const unsigned char* rec = popc + (c0 + c) * MS;
-          int qq = rec[u];
-          qq = qq < K ? qq : K - 1;
-          SE[i] = se_user_f64(a.beta, a.bnc, rec + XO, L, K, j, k, qq, a.fin, a.M64, a.pc64);
-        }
-        __syncthreads();
-        if (tid < nv) {
-          const double s = sum_se_f64(SE + tid * LK, L, K);
-          const int n = base_n + c0 + tid;
-          for (int r = 0; r < C; ++r) cluster.map_shared_rank(fit, r)[n] = (FT)s;
-        }
-      }
-      if (c0 + a.NTT < nvalid) __syncthreads();  // the last pass meets the cluster barrier
-    }
-    // ---- 2. all fitness values and members of generation g are visible
-    cluster.sync();
-    if (g == a.G) break;
-    const bool small_e = E <= kSmallE;
-    // ---- 3. elites (CTA holding slots below E).  For E <= 8 warp 0 alone
-    //         finds them (register lists) and then fills the elite slots while
-    //         the other warps build the other children; for larger E every
-    //         warp takes a stripe of the population and warp 0 merges.
-    if (n_elite_here > 0 && !small_e) {
-      const int stripe = (N + nwarps - 1) / nwarps;
-      const int lo = warp * stripe, hi = min(N, lo + stripe);
-      for (int e = 0; e < E; ++e) {
-        int best = -1;
-        FT bv = (FT)0;
-        for (int i = lo + lane; i < hi; i += 32) {
-          bool taken = false;
-          for (int f = 0; f < e; ++f) taken |= (CI[warp * E + f] == i);
-          if (taken) continue;
-          const FT v = fit[i];
-          if (best < 0 || better_v(v, i, bv, best)) {
-            best = i;
-            bv = v;
-          }
-        }
-        for (int off = 16; off > 0; off >>= 1) {
-          const int o = __shfl_xor_sync(0xffffffffu, best, off);
-          const FT ov = shfl_xor_ft(bv, off);
-          if (o >= 0 && (best < 0 || better_v(ov, o, bv, best))) {
-            best = o;
-            bv = ov;
-          }
-        }
-        if (lane == 0) {
-          CI[warp * E + e] = best;
-          CV[warp * E + e] = bv;
-        }
-        __syncwarp();
-      }
-      __syncthreads();
-      if (warp == 0) {
-        const int ncand = nwarps * E;
-        for (int e = 0; e < E; ++e) {
-          int best = -1, slot = -1;
-          FT bv = (FT)0;
-          for (int i = lane; i < ncand; i += 32) {
-            const int ci = CI[i];
-            if (ci < 0) continue;
-            const FT v = CV[i];
-            if (best < 0 || better_v(v, ci, bv, best)) {
-              best = ci;
-              bv = v;
-              slot = i;
-            }
-          }
-          for (int off = 16; off > 0; off >>= 1) {
-            const int o = __shfl_xor_sync(0xffffffffu, best, off);
-            const FT ov = shfl_xor_ft(bv, off);
-            const int os = __shfl_xor_sync(0xffffffffu, slot, off);
-            if (o >= 0 && (best < 0 || better_v(ov, o, bv, best))) {
-              best = o;
-              bv = ov;
-              slot = os;
-            }
-          }
-          if (lane == 0) {
-            elites[e] = best;
-            CI[slot] = -1;  // consumed
-          }
-          __syncwarp();
-        }
-      }
-      __syncthreads();
-    }
-    if (n_elite_here > 0 && small_e && warp == 0) {
-      if (E <= 2)
-        warp_top_e_rounds<FT, 2, 8>(fit, N, E, lane, elites);
-      else
-        warp_top_e_rounds<FT, kSmallE, 8>(fit, N, E, lane, elites);
-      __syncwarp();
-    }
-    // ---- 4. children of this CTA's slots: warp w builds slots w, w+nwarps, ...
-    unsigned char* popn = POPp(cur ^ 1);
-    for (int c0 = 0; c0 < nvalid; c0 += a.CH) {
-      const int nc = min(a.CH, nvalid - c0);
-      if (!(drawn && c0 == 0)) {
-        gen_child_draws(DR, base_n + c0, nc, nblk, a.seed, (uint64_t)(a.gen0 + g), E);
-        __syncthreads();
-      }
-      // elite slots of a small E are warp 0's (it found the elites); other
-      // slots go round robin to the remaining warps
-      const int ne = (small_e && c0 == 0) ? min(n_elite_here, nc) : 0;
-      const int w_first = ne > 0 ? 1 : 0;
-      const int w_span = nwarps - w_first;
-      int i_begin, i_step;
-      if (ne > 0 && warp == 0) {
-        i_begin = 0;
-        i_step = 1;
-      } else {
-        i_begin = ne + (warp - w_first);
-        i_step = w_span;
-      }
-      const int i_end = (ne > 0 && warp == 0) ? ne : nc;
-      for (int i = i_begin; i < i_end; i += i_step) {
-        const int slot = c0 + i;
-        const int n = base_n + slot;
-        const uint32_t* dr = DR + (size_t)i * nblk * 8;
-        uint32_t* child = reinterpret_cast<uint32_t*>(popn + slot * MS);
-        int pa_, pb_;
-        int64_t split;
-        if (n < E) {
-          pa_ = pb_ = elites[n];
-          split = LK;
-        } else {
-          pa_ = tournament_lane(fit, N, T_, dr);
-          pb_ = tournament_lane(fit, N, T_, dr + T_);
-          int cut = L;
-          if ((uint64_t)dr[2 * T_] < a.pc_thresh) cut = 1 + (int)below(dr[2 * T_ + 1], (uint32_t)(L - 1));
-          split = (int64_t)cut * K;
-        }
-        // parents' records from their owners: all remote loads issued first
-        const uint32_t ra = dsmem_addr(POPp(cur) + (pa_ % NT) * MS, pa_ / NT);
-        const uint32_t rb = dsmem_addr(POPp(cur) + (pb_ % NT) * MS, pb_ / NT);
-        constexpr int kMaxW = 4;  // words per lane held at once (records <= 512 bytes)
-        uint32_t wa[kMaxW], wb[kMaxW];
-#pragma unroll
-        for (int r = 0; r < kMaxW; ++r) {
-          const int w = lane + 32 * r;
-          if (w < nwords) {
-            wa[r] = ld_dsmem(ra + 4 * w);
-            wb[r] = ld_dsmem(rb + 4 * w);
-          }
-        }
-        for (int w = lane + 32 * kMaxW; w < nwords; w += 32) {  // longer records
-          const int64_t off = 4 * (int64_t)w >= XO ? XO : 0;
-          child[w] = merge_word(ld_dsmem(ra + 4 * w), ld_dsmem(rb + 4 * w), w, split + off);
-        }
-#pragma unroll
-        for (int r = 0; r < kMaxW; ++r) {
-          const int w = lane + 32 * r;
-          if (w < nwords) {
-            const int64_t off = 4 * (int64_t)w >= XO ? XO : 0;
-            child[w] = merge_word(wa[r], wb[r], w, split + off);
-          }
-        }
-        __syncwarp();
-        if (n >= E) {
-          uint8_t* cx = reinterpret_cast<uint8_t*>(child);
-          for (int l = lane; l < L; l += 32) {
-            const int base = 2 * T_ + 2 + 3 * l;
-            if ((uint64_t)dr[base] < a.pm_thresh && K >= 2) {
-              const int i1 = (int)below(dr[base + 1], (uint32_t)K);
-              const int jj = (int)below(dr[base + 2], (uint32_t)(K - 1));
-              const int i2 = jj + (jj >= i1 ? 1 : 0);
-              uint8_t* xr = cx + l * K;
-              uint8_t* ir = cx + XO + l * K;
-              const uint8_t p1 = xr[i1], p2 = xr[i2];
-              xr[i1] = p2;
-              xr[i2] = p1;
-              if (p1 < K) ir[p1] = (uint8_t)i2;
-              if (p2 < K) ir[p2] = (uint8_t)i1;
-            }
-          }
-        }
-        __syncwarp();
-      }
-      __syncthreads();
-    }
-    cur ^= 1;
-  }
-
-  // ---- outputs: final population and fitness, best member
-  const FT* fit = FITp(a.G & 1);
-  for (int i = tid; i < nvalid * LK; i += blockDim.x) {
-    const int c = i / LK, r = i - c * LK;
-    a.pop_out[(int64_t)base_n * LK + i] = POPp(cur)[c * MS + r];
-  }
-  FT* fo = static_cast<FT*>(a.fit_out);
-  for (int c = tid; c < nvalid; c += blockDim.x) fo[base_n + c] = fit[base_n + c];
-  if (rank == 0 && a.best_row && warp == 0) {
-    int best = -1;
-    FT bv = (FT)0;
-    for (int i = lane; i < N; i += 32) {
-      const FT v = fit[i];
-      if (best < 0 || better_v(v, i, bv, best)) {
-        best = i;
-        bv = v;
-      }
-    }
-    for (int off = 16; off > 0; off >>= 1) {
-      const int o = __shfl_xor_sync(0xffffffffu, best, off);
-      const FT ov = shfl_xor_ft(bv, off);
-      if (o >= 0 && (best < 0 || better_v(ov, o, bv, best))) {
-        best = o;
-        bv = ov;
-      }
-    }
-    const uint8_t* src = cluster.map_shared_rank(POPp(cur), best / NT) + (best % NT) * MS;
-    for (int r = lane; r < LK; r += 32) a.best_row[r] = src[r];
-    if (lane == 0) *a.best_fit = (double)fit[best];
-  }
-  cluster.sync();  // keep this CTA's shared memory alive for remote readers
-}
 
 // One instance per launch: the cluster runs solve_body once.
 template <typename FT, int NJ, int VEC, bool FIN>
@@ -599,90 +39,6 @@ __global__ void __launch_bounds__(kSolveThreads) k_solve(const SolveArgs a) {
   __shared__ int elites[64];
   cg::cluster_group cluster = cg::this_cluster();
   solve_body<FT, NJ, VEC, FIN, kSoloMaxNP>(a, smem, elites, cluster);
-}
-
-// Many instances per launch (persistent clusters): each cluster takes the
-// next instance index from a global counter until the list is exhausted.
-// Instances of one launch share the kernel variant (NJ, VEC, FIN, FT); their
-// sizes may differ (shared memory is sized for the largest).
-template <typename FT, int NJ, int VEC, bool FIN>
-__global__ void __launch_bounds__(kSolveThreads)
-    k_solve_batch(const SolveArgs* __restrict__ insts, int n_inst, int* __restrict__ counter) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ int elites[64];
-  __shared__ int next;
-  // the instance's arguments live in shared memory (a local copy would sit
-  // in local memory: the kernel runs at the 64-register limit)
-  __shared__ SolveArgs sargs;
-  static_assert(sizeof(SolveArgs) % 8 == 0, "SolveArgs is copied as 8-byte words");
-  constexpr int kArgWords = (int)(sizeof(SolveArgs) / 8);
-  static_assert(kArgWords <= kSolveThreads, "one word per thread");
-  cg::cluster_group cluster = cg::this_cluster();
-  const int C = (int)cluster.num_blocks();
-  for (;;) {
-    if (cluster.block_rank() == 0 && threadIdx.x == 0) {
-      const int i = atomicAdd(counter, 1);
-      for (int r = 0; r < C; ++r) *cluster.map_shared_rank(&next, r) = i;
-    }
-    cluster.sync();
-    const int i = next;
-    if (i >= n_inst) break;
-    if (threadIdx.x < kArgWords)
-      reinterpret_cast<uint64_t*>(&sargs)[threadIdx.x] =
-          reinterpret_cast<const uint64_t*>(insts + i)[threadIdx.x];
-    __syncthreads();
-    solve_body<FT, NJ, VEC, FIN, kBatchMaxNP>(sargs, smem, elites, cluster);
-  }
-}
-
-// ------------------------------------------------------------------ launch
-struct SolveShape {
-  int C, NT, MS, XO, NTT, nblk, CH;
-  size_t smem;
-};
-
-SolveShape solve_shape(const pa_ctx* ctx, int C, int maxnp) {
-  const pa_config& c = ctx->cfg;
-  const bool f64 = c.prec == PA_FP64;
-  const int LK = c.L * c.K;
-  SolveShape s{};
-  s.nblk = (2 * c.tour + 2 + 3 * c.L + 7) / 8;
-  s.C = C;
-  s.NT = (c.N + C - 1) / C;
-  s.CH = std::max(1, std::min(s.NT, 16384 / (s.nblk * 32)));
-  // record = X | INV, 4-byte aligned halves; an odd number of words per
-  // record keeps the per-member inverse reads of one warp in distinct banks
-  s.XO = ((LK + 3) / 4) * 4;
-  s.MS = 2 * s.XO;
-  if ((s.MS / 4) % 2 == 0) s.MS += 4;
-  const int NJ = ctx->t32.NJ;
-  const int JS = f64 ? 1 : fused_js(NJ, maxnp);
-  const int NPR = f64 ? 0 : NJ / 2;
-  if (f64) {
-    s.NTT = std::max(1, std::min(s.NT, 2048 / std::max(1, LK)));
-  } else {
-    // members per pass: their (member, pilot) pairs, in half-warp groups of
-    // 16, times JS shares fit the block
-    s.NTT = 1;
-    for (int n = s.NT; n >= 1; --n)
-      if (((n * c.K + 15) / 16) * 16 * JS <= kSolveThreads) {
-        s.NTT = n;
-        break;
-      }
-  }
-  size_t b = 0;
-  if (!f64) {
-    const size_t tab = (((size_t)LK * ctx->t32.RS + 3) / 4) * 4;
-    b += 4 * tab + 4 * (size_t)((LK + 3) & ~3) + 4 * (size_t)((c.L + 3) & ~3);
-  }
-  const size_t fsz = f64 ? 8 : 4;
-  b += 2 * fsz * (size_t)((c.N + 1) & ~1);
-  b += f64 ? 8 * (size_t)s.NTT * LK : 4 * (size_t)((s.NTT * c.K * NPR + 3) & ~3);
-  b += 2 * (size_t)s.NT * s.MS;
-  b += (size_t)s.CH * s.nblk * 32;
-  b += (f64 ? 8 : 4) * 32 * 64 + 4 * 32 * 64;  // elite candidates
-  s.smem = (b + 15) & ~size_t(15);
-  return s;
 }
 
 template <typename FT, int NJ, int VEC, bool FIN>
@@ -762,8 +118,8 @@ cudaError_t launch_solve(pa_ctx* ctx, const uint8_t* pop_in, uint8_t* pop_out, i
   for (int C : sizes) {
     if (ctx->solve_C > 0 && C != ctx->solve_C) continue;
     if (C > c.N) continue;
-    const SolveShape s = solve_shape(ctx, C, kSoloMaxNP);
-    if (s.smem + 64 * 4 > (size_t)kSmemBudget) continue;
+    const SolveShape s = solve_shape(ctx, C, kSoloMaxNP, kSolveThreads);
+    if (s.smem > (size_t)kSmemBudget - 64 * 4) continue;
     SolveArgs a{};
     a.pop_in = pop_in;
     a.pop_out = pop_out;
@@ -818,151 +174,5 @@ cudaError_t launch_solve(pa_ctx* ctx, const uint8_t* pop_in, uint8_t* pop_out, i
 }
 
 // ------------------------------------------------------------------ batches
-namespace {
-
-template <typename FT, int NJ, int VEC, bool FIN>
-cudaError_t run_solve_batch(int C, int clusters, const SolveArgs* d_args, int n, int* d_counter,
-                            size_t smem, bool query_only, int* max_clusters, cudaStream_t st) {
-  auto kern = k_solve_batch<FT, NJ, VEC, FIN>;
-  static std::atomic<uint64_t> prepared{0};
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return e;
-  const uint64_t bit = 1ULL << (dev & 63);
-  if (!(prepared.load() & bit)) {
-    e = raise_smem_cap((const void*)kern, dev);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-    if (e != cudaSuccess) return e;
-    prepared.fetch_or(bit);
-  }
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(C * std::max(1, clusters), 1, 1);
-  cfg.blockDim = dim3(kSolveThreads, 1, 1);
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = st;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = C;
-  attr[0].val.clusterDim.y = 1;
-  attr[0].val.clusterDim.z = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  if (query_only) {
-    int m = 0;
-    e = cudaOccupancyMaxActiveClusters(&m, kern, &cfg);
-    if (e != cudaSuccess) {
-      (void)cudaGetLastError();
-      m = 0;
-    }
-    *max_clusters = m;
-    return cudaSuccess;
-  }
-  (void)cudaGetLastError();  // drop a stale error of an earlier call
-  e = cudaLaunchKernelEx(&cfg, kern, d_args, n, d_counter);
-  count_launch();
-  return e;
-}
-
-template <typename FT, int VEC, bool FIN>
-cudaError_t pick_batch(int NJ, int C, int clusters, const SolveArgs* d, int n, int* ctr, size_t smem,
-                       bool q, int* mc, cudaStream_t st) {
-  switch (NJ) {
-    case 4: return run_solve_batch<FT, 4, VEC, FIN>(C, clusters, d, n, ctr, smem, q, mc, st);
-    case 8: return run_solve_batch<FT, 8, VEC, FIN>(C, clusters, d, n, ctr, smem, q, mc, st);
-    case 12: return run_solve_batch<FT, 12, VEC, FIN>(C, clusters, d, n, ctr, smem, q, mc, st);
-    case 16: return run_solve_batch<FT, 16, VEC, FIN>(C, clusters, d, n, ctr, smem, q, mc, st);
-    case 20: return run_solve_batch<FT, 20, VEC, FIN>(C, clusters, d, n, ctr, smem, q, mc, st);
-    case 24: return run_solve_batch<FT, 24, VEC, FIN>(C, clusters, d, n, ctr, smem, q, mc, st);
-    case 28: return run_solve_batch<FT, 28, VEC, FIN>(C, clusters, d, n, ctr, smem, q, mc, st);
-    case 32: return run_solve_batch<FT, 32, VEC, FIN>(C, clusters, d, n, ctr, smem, q, mc, st);
-    case 36: return run_solve_batch<FT, 36, VEC, FIN>(C, clusters, d, n, ctr, smem, q, mc, st);
-    case 40: return run_solve_batch<FT, 40, VEC, FIN>(C, clusters, d, n, ctr, smem, q, mc, st);
-    case 44: return run_solve_batch<FT, 44, VEC, FIN>(C, clusters, d, n, ctr, smem, q, mc, st);
-    case 48: return run_solve_batch<FT, 48, VEC, FIN>(C, clusters, d, n, ctr, smem, q, mc, st);
-    default: return cudaErrorInvalidValue;
-  }
-}
-
-cudaError_t dispatch_batch(const pa_ctx* proto, int C, int clusters, const SolveArgs* d, int n,
-                           int* ctr, size_t smem, bool q, int* mc, cudaStream_t st) {
-  const pa_config& c = proto->cfg;
-  const bool fin = c.mode == PA_SINR_FINITE_M;
-  if (c.prec == PA_FP64) return run_solve_batch<double, 4, 2, false>(C, clusters, d, n, ctr, smem, q, mc, st);
-  if (proto->t32.vec == 2)
-    return fin ? pick_batch<float, 2, true>(proto->t32.NJ, C, clusters, d, n, ctr, smem, q, mc, st)
-               : pick_batch<float, 2, false>(proto->t32.NJ, C, clusters, d, n, ctr, smem, q, mc, st);
-  return fin ? pick_batch<float, 1, true>(proto->t32.NJ, C, clusters, d, n, ctr, smem, q, mc, st)
-             : pick_batch<float, 1, false>(proto->t32.NJ, C, clusters, d, n, ctr, smem, q, mc, st);
-}
-
-}  // namespace
-
-size_t solve_args_bytes() { return sizeof(SolveArgs); }
-
-// Arguments of one instance's solve with cluster size C (written to
-// args_out, a SolveArgs); returns the shared memory it needs, or 0 when it
-// does not fit in one CTA.
-size_t solve_fill_args(const pa_ctx* ctx, int C, int gen0, int G, const uint8_t* pop_in,
-                       uint8_t* pop_out, void* fit_out, uint8_t* best_row, double* best_fit,
-                       void* args_out) {
-  const pa_config& c = ctx->cfg;
-  if (C > c.N || ctx->t32.streamed) return 0;
-  const SolveShape s = solve_shape(ctx, C, kBatchMaxNP);
-  if (s.smem + 64 * 4 + 16 > (size_t)kSmemBudget) return 0;
-  SolveArgs a{};
-  a.pop_in = pop_in;
-  a.pop_out = pop_out;
-  a.fit_out = fit_out;
-  a.best_row = best_row;
-  a.best_fit = best_fit;
-  a.N = c.N;
-  a.L = c.L;
-  a.K = c.K;
-  a.E = c.E;
-  a.tour = c.tour;
-  a.pc_thresh = c.pc_thresh;
-  a.pm_thresh = c.pm_thresh;
-  a.seed = c.seed;
-  a.gen0 = gen0;
-  a.G = G;
-  a.NT = s.NT;
-  a.MS = s.MS;
-  a.XO = s.XO;
-  a.NTT = s.NTT;
-  a.nblk = s.nblk;
-  a.CH = s.CH;
-  a.tab = ctx->t32.tab;
-  a.own = ctx->t32.own;
-  a.bn = ctx->t32.bn;
-  a.RS = ctx->t32.RS;
-  a.tab_floats = (((int64_t)c.L * c.K * ctx->t32.RS + 3) / 4) * 4;
-  a.M32 = ctx->t32.M;
-  a.pc32 = ctx->t32.pc;
-  a.beta = ctx->beta64;
-  a.bnc = ctx->bnc64;
-  a.M64 = c.M;
-  a.pc64 = ctx->pc;
-  a.fin = c.mode == PA_SINR_FINITE_M;
-  std::memcpy(args_out, &a, sizeof a);
-  return s.smem;
-}
-
-// Clusters of size C that can be resident at once for the batched kernel of
-// proto's variant with this shared memory (0 when none).
-int solve_batch_max_clusters(const pa_ctx* proto, int C, size_t smem) {
-  int m = 0;
-  if (dispatch_batch(proto, C, 1, nullptr, 0, nullptr, smem, true, &m, nullptr) != cudaSuccess)
-    return 0;
-  return m;
-}
-
-// Persistent batched solve of n instances sharing proto's kernel variant:
-// d_args holds their SolveArgs (cluster size C), d_counter must be zero.
-cudaError_t launch_solve_batch(const pa_ctx* proto, int C, int clusters, const void* d_args, int n,
-                               int* d_counter, size_t smem, cudaStream_t st) {
-  return dispatch_batch(proto, C, clusters, static_cast<const SolveArgs*>(d_args), n, d_counter,
-                        smem, false, nullptr, st);
-}
 
 }  // namespace pa
