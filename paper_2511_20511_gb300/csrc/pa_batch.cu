@@ -35,7 +35,6 @@ struct pa_batch {
   struct Group {
     std::vector<int> members;
     int C = 0;
-    int threads = 1024;  // CTA size of the group's batched kernel
     int clusters = 0;
     size_t smem = 0;
     std::vector<unsigned char> h_args;
@@ -96,7 +95,7 @@ void destroy_batch(pa_batch* b) {
 
 // (Re)build one group's argument records for cluster size C and G
 // generations; 0 on success, else the status.
-pa_status build_group_args(pa_batch* b, pa_batch::Group& g, int C, int G, int threads) {
+pa_status build_group_args(pa_batch* b, pa_batch::Group& g, int C, int G) {
   const size_t ab = pa::solve_args_bytes();
   std::vector<unsigned char> h(ab * g.members.size());
   size_t smem = 0;
@@ -105,11 +104,11 @@ pa_status build_group_args(pa_batch* b, pa_batch::Group& g, int C, int G, int th
     pa_ctx* c = b->ctx[i];
     const size_t s = pa::solve_fill_args(c, C, 0, G, c->pop[0], c->pop[1], c->fit,
                                          b->d_best + b->best_off[i], b->d_bestfit + i,
-                                         h.data() + m * ab, threads);
+                                         h.data() + m * ab);
     if (s == 0) return PA_EUNSUPPORTED;
     smem = std::max(smem, s);
   }
-  const int maxc = pa::solve_batch_max_clusters(b->ctx[g.members[0]], C, smem, threads);
+  const int maxc = pa::solve_batch_max_clusters(b->ctx[g.members[0]], C, smem);
   if (maxc < 1) return PA_EUNSUPPORTED;
   if (!g.d_args) {
     pa_status st = bcuda(b, cudaMalloc(&g.d_args, h.size()), "cudaMalloc batch args");
@@ -120,7 +119,6 @@ pa_status build_group_args(pa_batch* b, pa_batch::Group& g, int C, int G, int th
   if (st != PA_OK) return st;
   g.h_args.swap(h);
   g.C = C;
-  g.threads = threads;
   g.smem = smem;
   g.clusters = std::min<int>((int)g.members.size(), maxc);
   return PA_OK;
@@ -150,8 +148,7 @@ pa_status run_groups(pa_batch* b, cudaStream_t st) {
     s = bcuda(b, cudaStreamWaitEvent(g.side, b->fork, 0), "fork wait");
     if (s != PA_OK) return s;
     s = bcuda(b, pa::launch_solve_batch(b->ctx[g.members[0]], g.C, g.clusters, g.d_args,
-                                        (int)g.members.size(), b->d_counters + k, g.smem, g.side,
-                                        g.threads),
+                                        (int)g.members.size(), b->d_counters + k, g.smem, g.side),
               "batched solve kernel");
     if (s != PA_OK) return s;
     s = bcuda(b, cudaEventRecord(g.done, g.side), "join");
@@ -279,12 +276,8 @@ pa_status pa_batch_create(int32_t n, const pa_config* cfgs, const double* const*
     for (int C = C0 * 2; C <= 16; C *= 2) order.push_back(C);
     for (int C = C0 / 2; C >= 1; C /= 2) order.push_back(C);
     pa_status gs = PA_EUNSUPPORTED;
-    const int t0 = pa::batch_threads_default(b->ctx[g.members[0]]);
-    for (int threads : {t0, 1024}) {
-      for (int C : order) {
-        gs = build_group_args(b, g, C, 1, threads);
-        if (gs != PA_EUNSUPPORTED) break;
-      }
+    for (int C : order) {
+      gs = build_group_args(b, g, C, 1);
       if (gs != PA_EUNSUPPORTED) break;
     }
     if (gs != PA_OK) st = bfail(b, gs, "an instance of the batch does not fit the solve kernel");
@@ -331,13 +324,10 @@ pa_status pa_batch_tune(pa_batch* b, int32_t generations, int32_t* chosen) {
   cudaEventCreate(&e1);
   for (size_t k = 0; k < b->groups.size() && st == PA_OK; ++k) {
     auto& g = b->groups[k];
-    int best_C = g.C, best_T = g.threads;
+    int best_C = g.C;
     float best_ms = -1.f;
-    const int t0 = pa::batch_threads_default(b->ctx[g.members[0]]);
-    for (int cand = 0; cand < 10; ++cand) {
-      const int C = 1 << (cand % 5), threads = cand < 5 ? t0 : 1024;
-      if (cand >= 5 && t0 == 1024) break;
-      pa_status gs = build_group_args(b, g, C, generations, threads);
+    for (int C : {1, 2, 4, 8, 16}) {
+      pa_status gs = build_group_args(b, g, C, generations);
       if (gs == PA_EUNSUPPORTED) continue;
       if (gs != PA_OK) {
         st = gs;
@@ -349,7 +339,7 @@ pa_status pa_batch_tune(pa_batch* b, int32_t generations, int32_t* chosen) {
         cudaEventRecord(e0, b->stream);
         cudaError_t e = pa::launch_solve_batch(b->ctx[g.members[0]], g.C, g.clusters, g.d_args,
                                                (int)g.members.size(), b->d_counters + k, g.smem,
-                                               b->stream, g.threads);
+                                               b->stream);
         cudaEventRecord(e1, b->stream);
         st = bcuda(b, e, "batched solve kernel");
         if (st == PA_OK) st = bcuda(b, cudaEventSynchronize(e1), "tune sync");
@@ -360,10 +350,9 @@ pa_status pa_batch_tune(pa_batch* b, int32_t generations, int32_t* chosen) {
       if (best_ms < 0.f || ms < best_ms) {
         best_ms = ms;
         best_C = C;
-        best_T = threads;
       }
     }
-    if (st == PA_OK) st = build_group_args(b, g, best_C, 1, best_T);
+    if (st == PA_OK) st = build_group_args(b, g, best_C, 1);
     if (chosen && st == PA_OK) chosen[k] = best_C;
   }
   cudaEventDestroy(e0);
@@ -398,7 +387,7 @@ pa_status pa_batch_solve(pa_batch* b, int32_t generations, uint8_t* best_host, d
       b->graph = nullptr;
     }
     for (auto& g : b->groups) {
-      st = build_group_args(b, g, g.C, generations, g.threads);
+      st = build_group_args(b, g, g.C, generations);
       if (st != PA_OK) return bfail(b, st, "rebuilding batch arguments failed");
     }
     cudaGraph_t graph = nullptr;

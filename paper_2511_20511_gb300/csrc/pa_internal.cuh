@@ -117,12 +117,10 @@ cudaError_t launch_solve(pa_ctx* ctx, const uint8_t* pop_in, uint8_t* pop_out, i
 size_t solve_args_bytes();
 size_t solve_fill_args(const pa_ctx* ctx, int C, int gen0, int G, const uint8_t* pop_in,
                        uint8_t* pop_out, void* fit_out, uint8_t* best_row, double* best_fit,
-                       void* args_out, int threads = 1024);
-int solve_batch_max_clusters(const pa_ctx* proto, int C, size_t smem, int threads = 1024);
+                       void* args_out);
+int solve_batch_max_clusters(const pa_ctx* proto, int C, size_t smem);
 cudaError_t launch_solve_batch(const pa_ctx* proto, int C, int clusters, const void* d_args, int n,
-                               int* d_counter, size_t smem, cudaStream_t st, int threads = 1024);
-// CTA size of the batched kernel for an instance (1024 threads)
-int batch_threads_default(const pa_ctx* ctx);
+                               int* d_counter, size_t smem, cudaStream_t st);
 // pa_ga.cu: seed many instances at once (a cluster of C CTAs each) from n
 // seed argument records (seed_args_bytes() each, filled by seed_fill_args
 // for that C) in device memory; smem = the largest seed_fill_args value

@@ -94,9 +94,8 @@ cudaError_t run_solve_batch(int C, int clusters, const SolveArgs* d_args, int n,
 }
 
 template <typename FT, int VEC, bool FIN>
-cudaError_t pick_batch(int NJ, int threads, int C, int clusters, const SolveArgs* d, int n,
-                       int* ctr, size_t smem, bool q, int* mc, cudaStream_t st) {
-  if (threads != kSolveThreads) return cudaErrorInvalidValue;
+cudaError_t pick_batch(int NJ, int C, int clusters, const SolveArgs* d, int n, int* ctr,
+                       size_t smem, bool q, int* mc, cudaStream_t st) {
   constexpr int T = kSolveThreads;
   switch (NJ) {
     case 4: return run_solve_batch<FT, 4, VEC, FIN, T>(C, clusters, d, n, ctr, smem, q, mc, st);
@@ -116,22 +115,19 @@ cudaError_t pick_batch(int NJ, int threads, int C, int clusters, const SolveArgs
 }
 
 
-cudaError_t dispatch_batch(const pa_ctx* proto, int threads, int C, int clusters,
-                           const SolveArgs* d, int n, int* ctr, size_t smem, bool q, int* mc,
-                           cudaStream_t st) {
+cudaError_t dispatch_batch(const pa_ctx* proto, int C, int clusters, const SolveArgs* d, int n,
+                           int* ctr, size_t smem, bool q, int* mc, cudaStream_t st) {
   const pa_config& c = proto->cfg;
   const bool fin = c.mode == PA_SINR_FINITE_M;
-  if (c.prec == PA_FP64) {
-    if (threads != kSolveThreads) return cudaErrorInvalidValue;
+  if (c.prec == PA_FP64)
     return run_solve_batch<double, 4, 2, false, kSolveThreads>(C, clusters, d, n, ctr, smem, q,
                                                                mc, st);
-  }
   const int NJ = proto->t32.NJ;
   if (proto->t32.vec == 2)
-    return fin ? pick_batch<float, 2, true>(NJ, threads, C, clusters, d, n, ctr, smem, q, mc, st)
-               : pick_batch<float, 2, false>(NJ, threads, C, clusters, d, n, ctr, smem, q, mc, st);
-  return fin ? pick_batch<float, 1, true>(NJ, threads, C, clusters, d, n, ctr, smem, q, mc, st)
-             : pick_batch<float, 1, false>(NJ, threads, C, clusters, d, n, ctr, smem, q, mc, st);
+    return fin ? pick_batch<float, 2, true>(NJ, C, clusters, d, n, ctr, smem, q, mc, st)
+               : pick_batch<float, 2, false>(NJ, C, clusters, d, n, ctr, smem, q, mc, st);
+  return fin ? pick_batch<float, 1, true>(NJ, C, clusters, d, n, ctr, smem, q, mc, st)
+             : pick_batch<float, 1, false>(NJ, C, clusters, d, n, ctr, smem, q, mc, st);
 }
 
 }  // namespace
@@ -143,11 +139,10 @@ size_t solve_args_bytes() { return sizeof(SolveArgs); }
 // does not fit in one CTA.
 size_t solve_fill_args(const pa_ctx* ctx, int C, int gen0, int G, const uint8_t* pop_in,
                        uint8_t* pop_out, void* fit_out, uint8_t* best_row, double* best_fit,
-                       void* args_out, int threads) {
+                       void* args_out) {
   const pa_config& c = ctx->cfg;
   if (C > c.N || ctx->t32.streamed) return 0;
-  if (threads != kSolveThreads) return 0;
-  const SolveShape s = solve_shape(ctx, C, kBatchMaxNP, threads);
+  const SolveShape s = solve_shape(ctx, C, kBatchMaxNP, kSolveThreads);
   if (s.smem > (size_t)kSmemBudget - 64 * 4 - 16) return 0;
   SolveArgs a{};
   a.pop_in = pop_in;
@@ -189,10 +184,9 @@ size_t solve_fill_args(const pa_ctx* ctx, int C, int gen0, int G, const uint8_t*
 
 // Clusters of size C that can be resident at once for the batched kernel of
 // proto's variant with this shared memory (0 when none).
-int solve_batch_max_clusters(const pa_ctx* proto, int C, size_t smem, int threads) {
+int solve_batch_max_clusters(const pa_ctx* proto, int C, size_t smem) {
   int m = 0;
-  if (dispatch_batch(proto, threads, C, 1, nullptr, 0, nullptr, smem, true, &m, nullptr) !=
-      cudaSuccess)
+  if (dispatch_batch(proto, C, 1, nullptr, 0, nullptr, smem, true, &m, nullptr) != cudaSuccess)
     return 0;
   return m;
 }
@@ -200,11 +194,9 @@ int solve_batch_max_clusters(const pa_ctx* proto, int C, size_t smem, int thread
 // Persistent batched solve of n instances sharing proto's kernel variant:
 // d_args holds their SolveArgs (cluster size C), d_counter must be zero.
 cudaError_t launch_solve_batch(const pa_ctx* proto, int C, int clusters, const void* d_args, int n,
-                               int* d_counter, size_t smem, cudaStream_t st, int threads) {
-  return dispatch_batch(proto, threads, C, clusters, static_cast<const SolveArgs*>(d_args), n,
-                        d_counter, smem, false, nullptr, st);
+                               int* d_counter, size_t smem, cudaStream_t st) {
+  return dispatch_batch(proto, C, clusters, static_cast<const SolveArgs*>(d_args), n, d_counter,
+                        smem, false, nullptr, st);
 }
-
-int batch_threads_default(const pa_ctx*) { return kSolveThreads; }
 
 }  // namespace pa
