@@ -96,3 +96,38 @@ def test_status_strings_and_create_reason(B):
     assert b"E must be" in B.lib().pa_last_error(None)
     with pytest.raises(B.PaError, match="E must be"):
         B.pa_create(cfg, np.ones((7, 7, 4)))
+
+
+def test_null_and_invalid_handles_rejected(B):
+    """Every entry point taking a handle rejects NULL (and invalid sizes)
+    with PA_EINVAL before touching a GPU; destroy functions ignore NULL."""
+    lib = B.lib()
+    i32 = C.c_int32(0)
+    u64 = C.c_uint64(0)
+    assert lib.pa_eval_population(None, None, 1, None) == B.PA_EINVAL
+    assert lib.pa_eval_population_host(None, None, 1, None) == B.PA_EINVAL
+    assert lib.pa_ga_step(None, None, None, 0, None) == B.PA_EINVAL
+    assert lib.pa_kmeans_seed(None, None, None) == B.PA_EINVAL
+    assert lib.pa_step(None, 1) == B.PA_EINVAL
+    assert lib.pa_solve(None, 1, None, None) == B.PA_EINVAL
+    assert lib.pa_get_population(None, None, None, None) == B.PA_EINVAL
+    assert lib.pa_set_population(None, None, 0) == B.PA_EINVAL
+    assert lib.pa_set_seed(None, 1) == B.PA_EINVAL
+    assert lib.pa_set_stream(None, None) == B.PA_EINVAL
+    assert lib.pa_solve_cluster_ctas(None, C.byref(i32)) == B.PA_EINVAL
+    assert lib.pa_load_instance(None, None, None, None) == B.PA_EINVAL
+    lib.pa_destroy(None)
+    # batches and servers
+    out = C.c_void_p()
+    assert lib.pa_batch_create(0, None, None, None, None, None, C.byref(out)) == B.PA_EINVAL
+    assert lib.pa_batch_solve(None, 1, None, None) == B.PA_EINVAL
+    assert lib.pa_batch_tune(None, 1, None) == B.PA_EINVAL
+    lib.pa_batch_destroy(None)
+    cfg = B.pa_config_default(7, 4)
+    assert lib.pa_server_create(C.byref(cfg), 0, 1, 1 << 30, None, C.byref(out)) == B.PA_EINVAL
+    assert lib.pa_server_create(C.byref(cfg), 10, 0, 1 << 30, None, C.byref(out)) == B.PA_EINVAL
+    assert lib.pa_server_create(C.byref(cfg), 10, 1, 0, None, C.byref(out)) == B.PA_EINVAL
+    assert lib.pa_server_submit(None, 0, 7, 4, 0, None, None, None) == B.PA_EINVAL
+    assert lib.pa_server_poll(None, 0, None, None, 0, None, C.byref(i32), None, None) == B.PA_EINVAL
+    assert lib.pa_server_stats(None, C.byref(u64), C.byref(i32), None) == B.PA_EINVAL
+    lib.pa_server_destroy(None)
