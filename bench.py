@@ -10,9 +10,13 @@ generations and the best-member selection, all through the C ABI.
 
 Printed (rank 0, one JSON line): chromosome fitness evaluations per second
 over the whole job (value), GA generations per second, per-solve latency
-percentiles, an end-to-end figure through host buffers, the population-wide
-evaluation kernel on 2^20 chromosomes with its roofline, and the CPU oracle
-as a reported baseline.
+percentiles, an end-to-end figure through host buffers, the roofline of the
+step's dominant kernel (the fused solve) and of the population-wide
+evaluation kernel on 2^20 chromosomes, the 512-instance batched solve, the
+61-cell streamed evaluation and solve, the serving comparison (Poisson
+arrivals, continuous batching vs one plain solve at a time, plus an
+overload point), and the CPU oracle as a reported baseline.  `--only eval |
+solve | stream | batch` runs one part untimed, for profilers.
 
 Under torchrun each rank solves its own instance (seed = rank): the units
 are independent, so there is no data-path collective ("weak" scaling).
