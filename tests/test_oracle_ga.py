@@ -168,3 +168,75 @@ def test_solve_reaches_exhaustive_optimum_on_tiny_instances(oracle, L, K, seed):
     opt, _, _ = oracle.exhaustive(beta, sp)
     assert r["best_fit"] <= opt
     assert r["best_fit"] == pytest.approx(opt, rel=1e-12)
+
+
+def _chi2_pvalue(counts, expect):
+    from scipy import stats
+
+    counts = np.asarray(counts, dtype=np.float64)
+    expect = np.asarray(expect, dtype=np.float64)
+    chi2 = float(np.sum((counts - expect) ** 2 / expect))
+    return float(stats.chi2.sf(chi2, df=len(counts) - 1))
+
+
+def _unique_row_population(N, L, K, seed):
+    """A population in which no row occurs twice anywhere (so that a child's
+    rows name their parents): N*L distinct permutations drawn without
+    replacement."""
+    import itertools
+
+    perms = np.array(list(itertools.permutations(range(K))), dtype=np.uint8)
+    pick = np.random.default_rng(seed).choice(len(perms), N * L, replace=False)
+    return perms[pick].reshape(N, L, K)
+
+
+def test_crossover_cut_uniform(oracle):
+    """Always crossover, no mutation, tournament of one: the cut c is uniform
+    on 1..L-1 (Sec. 6.1 single-point crossover, at a row boundary).  The
+    child's row 0 names parent a, its row L-1 parent b; with a != b the first
+    row taken from b is the cut.  A cut drawn from 0..L-2 or 1..L-2 fails."""
+    L, K, N = 8, 6, 30
+    pop = _unique_row_population(N, L, K, seed=40)
+    where = {pop[n, l].tobytes(): n for n in range(N) for l in range(L)}
+    fit = np.random.default_rng(2).random(N)
+    gp = oracle.ga_params(N, 0, 1, FULL, 0, seed=12)
+    counts = np.zeros(L - 1)
+    for g in range(300):
+        nxt = oracle.ga_step(pop, fit, gp, gen=g)
+        for ch in nxt:
+            a = where[ch[0].tobytes()]
+            b = where[ch[L - 1].tobytes()]
+            if a == b:
+                assert (ch == pop[a]).all()
+                continue
+            c = next(l for l in range(L) if (ch[l] == pop[b][l]).all())
+            assert (ch[:c] == pop[a][:c]).all() and (ch[c:] == pop[b][c:]).all()
+            counts[c - 1] += 1
+    assert (counts > 0).all()
+    assert _chi2_pvalue(counts, np.full(L - 1, counts.sum() / (L - 1))) > 1e-4
+
+
+def test_swap_positions_uniform_pairs(oracle):
+    """Every row mutated, no crossover, identical members: each child row is
+    the base row with one transposition, and the unordered position pair is
+    uniform over the K(K-1)/2 pairs (first position uniform on 0..K-1, the
+    second uniform on the other K-1).  A second position that can equal the
+    first, or never reaches K-1, fails."""
+    L, K, N = 10, 5, 64
+    base = inputs.random_population(1, L, K, seed=3)[0]
+    pop = np.repeat(base[None], N, axis=0)
+    fit = np.zeros(N)
+    gp = oracle.ga_params(N, 0, 2, 0, FULL, seed=21)
+    pairs = {(i, j): t for t, (i, j) in enumerate((i, j) for i in range(K) for j in range(i + 1, K))}
+    counts = np.zeros(len(pairs))
+    for g in range(50):
+        nxt = oracle.ga_step(pop, fit, gp, gen=g)
+        for ch in nxt:
+            for l in range(L):
+                diff = np.flatnonzero(ch[l] != base[l])
+                assert len(diff) == 2
+                i, j = int(diff[0]), int(diff[1])
+                assert ch[l][i] == base[l][j] and ch[l][j] == base[l][i]
+                counts[pairs[(i, j)]] += 1
+    assert counts.sum() == 50 * N * L
+    assert _chi2_pvalue(counts, np.full(len(pairs), counts.sum() / len(pairs))) > 1e-4

@@ -116,3 +116,51 @@ def test_kmeans_empty_cluster_keeps_centroid(oracle):
     assert (lab == np.argmin(d, axis=1)).all()
     # an emptied cluster's centroid is one of the means it held earlier, never NaN
     assert np.isfinite(cx[empty]).all() and np.isfinite(cy[empty]).all()
+
+
+def _chi2_pvalue(counts, expect):
+    from scipy import stats
+
+    counts = np.asarray(counts, dtype=np.float64)
+    expect = np.asarray(expect, dtype=np.float64)
+    chi2 = float(np.sum((counts - expect) ** 2 / expect))
+    return float(stats.chi2.sf(chi2, df=len(counts) - 1))
+
+
+@pytest.mark.parametrize("K", [3, 4])
+def test_random_row_uniform_over_all_permutations(oracle, K):
+    """Random rows (Fisher-Yates from the top, j uniform on 0..i): every one
+    of the K! permutations equally likely.  Sattolo's variant (j < i) makes
+    only cyclic permutations and a shortened loop misses permutations, so
+    both fail here."""
+    import itertools
+
+    L, N = 10, 2400  # 24,000 rows
+    pop = oracle.seed_population(L, K, N, 0, seed=123)
+    perms = {p: i for i, p in enumerate(itertools.permutations(range(K)))}
+    counts = np.zeros(len(perms))
+    for row in pop.reshape(-1, K):
+        counts[perms[tuple(int(v) for v in row)]] += 1
+    assert counts.sum() == N * L
+    assert (counts > 0).all()
+    assert _chi2_pvalue(counts, np.full(len(perms), N * L / len(perms))) > 1e-4
+
+
+def test_kmeans_initial_centroids_uniform_ordered_pairs(oracle):
+    """The partial Fisher-Yates draw of k = 2 initial centroids among U = 6
+    points: every ordered pair of distinct points has probability 1/30.  A
+    draw that never reaches the last index, or allows a repeat, fails."""
+    U, k = 6, 2
+    fx = np.arange(U, dtype=np.int64) * 1000
+    fy = np.zeros(U, dtype=np.int64)
+    counts = np.zeros((U, U))
+    seeds = range(6000)
+    for seed in seeds:
+        # one assignment pass: the returned centroids are the initial ones
+        _, cx0, _, _ = oracle.kmeans(fx, fy, k, max_iter=1, seed=seed)
+        a, b = int(round(cx0[0] / 1000)), int(round(cx0[1] / 1000))
+        counts[a, b] += 1
+    assert np.trace(counts) == 0  # distinct points
+    off = counts[~np.eye(U, dtype=bool)]
+    assert (off > 0).all()
+    assert _chi2_pvalue(off, np.full(U * (U - 1), len(seeds) / (U * (U - 1)))) > 1e-4
