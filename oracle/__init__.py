@@ -18,11 +18,14 @@ _lib = None
 
 ASYMPTOTIC = 0
 FINITE_M = 1
+OBJ_SUM_SE = 0
+OBJ_MIN_SINR = 1
 
 
 class SinrParams(C.Structure):
     _fields_ = [("mode", C.c_int32), ("tau_p", C.c_int32), ("M", C.c_double),
-                ("rho", C.c_double), ("sigma2", C.c_double)]
+                ("rho", C.c_double), ("sigma2", C.c_double), ("objective", C.c_int32),
+                ("pad0", C.c_int32)]
 
 
 class GaParams(C.Structure):
@@ -70,6 +73,18 @@ def _declare(L):
                            _p(C.c_int32), _p(C.c_int32), C.c_int32, C.c_int32, C.c_int32,
                            C.c_int32, _p(C.c_uint8), _p(C.c_double), _p(C.c_uint8),
                            _p(C.c_double), _p(C.c_double)]
+    L.or_pop_kmeans.argtypes = [_p(C.c_uint8), C.c_int32, C.c_int32, C.c_int32, C.c_int32,
+                                C.c_int32, C.c_uint64, C.c_int32, _p(C.c_int32),
+                                _p(C.c_int32)]
+    L.or_pop_kmeans.restype = C.c_int32
+    L.or_island_step.argtypes = [_p(C.c_uint8), _p(C.c_double), C.c_int32, C.c_int32,
+                                 _p(GaParams), C.c_int32, _p(C.c_int32), C.c_int32,
+                                 _p(C.c_uint8)]
+    L.or_solve_islands.argtypes = [_p(C.c_double), C.c_int32, C.c_int32, _p(SinrParams),
+                                   _p(GaParams), _p(C.c_int32), _p(C.c_int32), C.c_int32,
+                                   C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int32,
+                                   C.c_int32, _p(C.c_uint8), _p(C.c_double), _p(C.c_uint8),
+                                   _p(C.c_double), _p(C.c_double), _p(C.c_int32)]
     L.or_exhaustive.argtypes = [_p(C.c_double), C.c_int32, C.c_int32, _p(SinrParams),
                                 C.c_int32, _p(C.c_uint8), _p(C.c_int64)]
     L.or_exhaustive.restype = C.c_double
@@ -97,8 +112,9 @@ def _i64(a):
     return np.ascontiguousarray(a, dtype=np.int64)
 
 
-def sinr_params(mode=ASYMPTOTIC, tau_p=1, M=0.0, rho=1.0, sigma2=1.0):
-    return SinrParams(int(mode), int(tau_p), float(M), float(rho), float(sigma2))
+def sinr_params(mode=ASYMPTOTIC, tau_p=1, M=0.0, rho=1.0, sigma2=1.0, objective=OBJ_SUM_SE):
+    return SinrParams(int(mode), int(tau_p), float(M), float(rho), float(sigma2),
+                      int(objective), 0)
 
 
 def ga_params(N, E=2, tour=3, pc_thresh=0, pm_thresh=0, seed=0):
@@ -233,6 +249,58 @@ def solve(beta, sp, gp, G, user_xy_mm=None, bs_xy_mm=None, kmeans_k=None, kmeans
                    _ptr(pop, C.c_uint8), _ptr(fit, C.c_double), _ptr(best, C.c_uint8),
                    C.byref(best_fit), _ptr(hist, C.c_double))
     return dict(pop=pop, fit=fit, best=best, best_fit=best_fit.value, hist_best=hist)
+
+
+# ---------------------------------------------------------------- islands (Alg. 2)
+def pop_kmeans(pop, C_islands, max_iter=100, seed=0, gen=0, with_init=False):
+    """K-means of the population's chromosomes into C islands: (labels,
+    passes), plus the initial centroid members with with_init."""
+    pop = _u8(pop)
+    N, L, K = pop.shape
+    label = np.zeros(N, dtype=np.int32)
+    init = np.zeros(int(C_islands), dtype=np.int32)
+    passes = lib().or_pop_kmeans(_ptr(pop, C.c_uint8), N, L, K, int(C_islands), int(max_iter),
+                                 int(seed), int(gen), _ptr(label, C.c_int32),
+                                 _ptr(init, C.c_int32))
+    if with_init:
+        return label, int(passes), init
+    return label, int(passes)
+
+
+def island_step(pop, fit, gp, gen, label, C_islands):
+    pop = _u8(pop)
+    fit = _f64(fit)
+    label = _i32(label)
+    n, L, K = pop.shape
+    assert gp.N == n and label.shape == (n,)
+    nxt = np.zeros_like(pop)
+    lib().or_island_step(_ptr(pop, C.c_uint8), _ptr(fit, C.c_double), L, K, C.byref(gp),
+                         int(gen), _ptr(label, C.c_int32), int(C_islands), _ptr(nxt, C.c_uint8))
+    return nxt
+
+
+def solve_islands(beta, sp, gp, G, C_islands, R=3, iters=100, user_xy_mm=None, bs_xy_mm=None,
+                  kmeans_k=None, kmeans_max_iter=100, n_seeded=None):
+    beta = _f64(beta)
+    L, _, K = beta.shape
+    N = gp.N
+    kmeans_k = K if kmeans_k is None else kmeans_k
+    n_seeded = (N + 1) // 2 if n_seeded is None else n_seeded
+    u = None if user_xy_mm is None else _i32(user_xy_mm)
+    b = None if bs_xy_mm is None else _i32(bs_xy_mm)
+    pop = np.zeros((N, L, K), dtype=np.uint8)
+    fit = np.zeros(N)
+    best = np.zeros((L, K), dtype=np.uint8)
+    best_fit = C.c_double(0.0)
+    hist = np.zeros(G + 1)
+    label = np.zeros(N, dtype=np.int32)
+    lib().or_solve_islands(_ptr(beta, C.c_double), L, K, C.byref(sp), C.byref(gp),
+                           _ptr(u, C.c_int32), _ptr(b, C.c_int32), kmeans_k, kmeans_max_iter,
+                           n_seeded, G, int(C_islands), int(R), int(iters), _ptr(pop, C.c_uint8),
+                           _ptr(fit, C.c_double), _ptr(best, C.c_uint8), C.byref(best_fit),
+                           _ptr(hist, C.c_double), _ptr(label, C.c_int32))
+    return dict(pop=pop, fit=fit, best=best, best_fit=best_fit.value, hist_best=hist,
+                label=label)
 
 
 def exhaustive(beta, sp=None, all_rows=False):

@@ -64,7 +64,7 @@ static uint32_t below(uint32_t u, uint32_t n) {
 }
 
 /* Stream tags. */
-enum { TAG_SEED = 1, TAG_KMEANS = 2, TAG_GA = 3 };
+enum { TAG_SEED = 1, TAG_KMEANS = 2, TAG_GA = 3, TAG_ISLAND = 4 };
 
 /* ------------------------------------------------------------------------ */
 /* log2 by the series ln m = 2 * sum_{n>=0} s^(2n+1) / (2n+1), s=(m-1)/(m+1) */
@@ -129,6 +129,8 @@ static double beta_at(const double* beta, int32_t L, int32_t K, int32_t j, int32
  *     B_j  = sum_l sum_k beta[j][l][k]                           (all users)
  *     sinr = M beta_jjk^2 / (M S2 + (B_j + sigma2/rho) (S1 + sigma2/(tau_p rho)))
  *   SE = log2(1 + sinr)  (Eq. 5),   fitness = sum_j (sum_k SE)   (Eq. 6).
+ * The max-min objective of Sec. 2 instead takes fitness = the smallest sinr
+ * over all users (j ascending, k ascending; a minimum has no rounding).
  */
 double or_fitness(const double* beta, int32_t L, int32_t K, const uint8_t* X,
                   const or_sinr_params* sp, double* sinr_out, double* se_out) {
@@ -138,6 +140,7 @@ double or_fitness(const double* beta, int32_t L, int32_t K, const uint8_t* X,
   const double nc = sp->sigma2 / sp->rho;
   const double pc = sp->sigma2 / ((double)sp->tau_p * sp->rho);
   double fitness = 0.0;
+  double min_sinr = INFINITY;
   for (int32_t j = 0; j < L; ++j) {
     double b_j = 0.0;
     if (finite) {
@@ -168,11 +171,12 @@ double or_fitness(const double* beta, int32_t L, int32_t K, const uint8_t* X,
       if (sinr_out) sinr_out[j * K + k] = sinr;
       if (se_out) se_out[j * K + k] = se;
       cell_sum = cell_sum + se;
+      if (sinr < min_sinr) min_sinr = sinr;
     }
     fitness = fitness + cell_sum;
   }
   free(inv);
-  return fitness;
+  return sp->objective == OR_OBJ_MIN_SINR ? min_sinr : fitness;
 }
 
 void or_fitness_batch(const double* beta, int32_t L, int32_t K, const uint8_t* pop,
@@ -431,17 +435,14 @@ static int32_t argbest(const double* fit, int32_t N) {
   return best;
 }
 
-void or_solve(const double* beta, int32_t L, int32_t K, const or_sinr_params* sp,
-              const or_ga_params* gp, const int32_t* user_xy_mm, const int32_t* bs_xy_mm,
-              int32_t kmeans_k, int32_t kmeans_max_iter, int32_t n_seeded, int32_t G,
-              uint8_t* pop_out, double* fit_out, uint8_t* best_out, double* best_fit,
-              double* hist_best) {
+/* Initial population of a solve: K-means seeding with positions, else all
+ * random rows. */
+static void initial_population(int32_t L, int32_t K, const or_ga_params* gp,
+                               const int32_t* user_xy_mm, const int32_t* bs_xy_mm,
+                               int32_t kmeans_k, int32_t kmeans_max_iter, int32_t n_seeded,
+                               uint8_t* pop) {
   const int32_t N = gp->N;
-  const int64_t LK = (int64_t)L * K;
   const int32_t U = L * K;
-  uint8_t* pop = (uint8_t*)malloc((size_t)(N * LK));
-  uint8_t* nxt = (uint8_t*)malloc((size_t)(N * LK));
-  double* fit = (double*)malloc(sizeof(double) * (size_t)N);
   if (user_xy_mm != NULL && bs_xy_mm != NULL) {
     int64_t* fx = (int64_t*)malloc(sizeof(int64_t) * (size_t)U);
     int64_t* fy = (int64_t*)malloc(sizeof(int64_t) * (size_t)U);
@@ -459,6 +460,19 @@ void or_solve(const double* beta, int32_t L, int32_t K, const or_sinr_params* sp
   } else {
     or_seed_population(L, K, NULL, NULL, NULL, NULL, NULL, N, 0, gp->seed, pop);
   }
+}
+
+void or_solve(const double* beta, int32_t L, int32_t K, const or_sinr_params* sp,
+              const or_ga_params* gp, const int32_t* user_xy_mm, const int32_t* bs_xy_mm,
+              int32_t kmeans_k, int32_t kmeans_max_iter, int32_t n_seeded, int32_t G,
+              uint8_t* pop_out, double* fit_out, uint8_t* best_out, double* best_fit,
+              double* hist_best) {
+  const int32_t N = gp->N;
+  const int64_t LK = (int64_t)L * K;
+  uint8_t* pop = (uint8_t*)malloc((size_t)(N * LK));
+  uint8_t* nxt = (uint8_t*)malloc((size_t)(N * LK));
+  double* fit = (double*)malloc(sizeof(double) * (size_t)N);
+  initial_population(L, K, gp, user_xy_mm, bs_xy_mm, kmeans_k, kmeans_max_iter, n_seeded, pop);
   for (int32_t g = 0; g < G; ++g) {
     or_fitness_batch(beta, L, K, pop, N, sp, fit);
     if (hist_best) hist_best[g] = fit[argbest(fit, N)];
@@ -477,6 +491,201 @@ void or_solve(const double* beta, int32_t L, int32_t K, const or_sinr_params* sp
   free(pop);
   free(nxt);
   free(fit);
+}
+
+/* ------------------------------------------------------------------------ */
+/* PK-means GA (Sec. 4.3, Alg. 2): the population is partitioned by K-means */
+/* and every cluster (island) evolves on its own; K-means is re-applied     */
+/* every R generations (Sec. 6.1: every three).                             */
+/* ------------------------------------------------------------------------ */
+
+/* Chromosome n as one-hot pilot indicators e(n)[u][p] = (X_n[u] == p), one
+ * K-vector per user u = l*K + k.  Centroid c of m_c members has per-user
+ * pilot counts cnt_c[u][p] (centroid = cnt_c / m_c).  Then
+ *   m_c^2 * ||e(n) - cnt_c/m_c||^2 = LK m_c^2 - 2 m_c S(n,c) + Q_c,
+ *   S(n,c) = sum_u cnt_c[u][X_n[u]],   Q_c = sum_u sum_p cnt_c[u][p]^2,
+ * an integer; two distances compare exactly by cross-multiplying with the
+ * other cluster's m^2 (every factor below 2^37 when N, LK <= 4096, so every
+ * product fits in 63 bits). */
+static int64_t scaled_dist(const int64_t* cnt_c, int64_t m_c, int64_t q_c, const uint8_t* X,
+                           int32_t LK, int32_t K) {
+  int64_t S = 0;
+  for (int32_t u = 0; u < LK; ++u) S += cnt_c[(int64_t)u * K + X[u]];
+  return (int64_t)LK * m_c * m_c - 2 * m_c * S + q_c;
+}
+
+int32_t or_pop_kmeans(const uint8_t* pop, int32_t N, int32_t L, int32_t K, int32_t C,
+                      int32_t max_iter, uint64_t seed, int32_t gen, int32_t* label,
+                      int32_t* init_out) {
+  const int32_t LK = L * K;
+  const int64_t csz = (int64_t)LK * K;
+  int64_t* cnt = (int64_t*)calloc((size_t)(C * csz), sizeof(int64_t));
+  int64_t* ncnt = (int64_t*)calloc((size_t)(C * csz), sizeof(int64_t));
+  int64_t* m = (int64_t*)calloc((size_t)C, sizeof(int64_t));
+  int64_t* nm = (int64_t*)calloc((size_t)C, sizeof(int64_t));
+  int64_t* q = (int64_t*)calloc((size_t)C, sizeof(int64_t));
+  /* initial centroids: C distinct members by a partial Fisher-Yates shuffle */
+  int32_t* idx = (int32_t*)malloc(sizeof(int32_t) * (size_t)N);
+  for (int32_t i = 0; i < N; ++i) idx[i] = i;
+  for (int32_t c = 0; c < C; ++c) {
+    int32_t j = c + (int32_t)below(or_draw32(seed, 0, (uint64_t)gen, TAG_ISLAND, (uint32_t)c),
+                                   (uint32_t)(N - c));
+    int32_t t = idx[c];
+    idx[c] = idx[j];
+    idx[j] = t;
+    const uint8_t* X = pop + (int64_t)idx[c] * LK;
+    for (int32_t u = 0; u < LK; ++u) cnt[c * csz + (int64_t)u * K + X[u]] = 1;
+    m[c] = 1;
+    if (init_out) init_out[c] = idx[c];
+  }
+  free(idx);
+  for (int32_t n = 0; n < N; ++n) label[n] = -1;
+  int32_t passes = 0;
+  for (int32_t it = 0; it < max_iter; ++it) {
+    for (int32_t c = 0; c < C; ++c) {
+      q[c] = 0;
+      for (int64_t i = 0; i < csz; ++i) q[c] += cnt[c * csz + i] * cnt[c * csz + i];
+    }
+    /* assignment: nearest centroid, ties to the lower cluster index */
+    int64_t changed = 0;
+    for (int32_t n = 0; n < N; ++n) {
+      const uint8_t* X = pop + (int64_t)n * LK;
+      int32_t best = 0;
+      int64_t bd = scaled_dist(cnt, m[0], q[0], X, LK, K);
+      for (int32_t c = 1; c < C; ++c) {
+        int64_t d = scaled_dist(cnt + c * csz, m[c], q[c], X, LK, K);
+        /* d / m_c^2 < bd / m_best^2 */
+        if (d * m[best] * m[best] < bd * m[c] * m[c]) {
+          bd = d;
+          best = c;
+        }
+      }
+      if (label[n] != best) changed++;
+      label[n] = best;
+    }
+    passes++;
+    if (changed == 0 || it == max_iter - 1) break;
+    /* update: the members' counts; an empty cluster keeps its centroid */
+    memset(ncnt, 0, sizeof(int64_t) * (size_t)(C * csz));
+    memset(nm, 0, sizeof(int64_t) * (size_t)C);
+    for (int32_t n = 0; n < N; ++n) {
+      const uint8_t* X = pop + (int64_t)n * LK;
+      for (int32_t u = 0; u < LK; ++u) ncnt[label[n] * csz + (int64_t)u * K + X[u]] += 1;
+      nm[label[n]] += 1;
+    }
+    for (int32_t c = 0; c < C; ++c)
+      if (nm[c] > 0) {
+        memcpy(cnt + c * csz, ncnt + c * csz, sizeof(int64_t) * (size_t)csz);
+        m[c] = nm[c];
+      }
+  }
+  free(cnt);
+  free(ncnt);
+  free(m);
+  free(nm);
+  free(q);
+  return passes;
+}
+
+/* Tournament among the m members of one island (member list mem). */
+static int32_t island_tournament(const double* fit, const int32_t* mem, int32_t m, int32_t tour,
+                                 uint64_t seed, int32_t slot, int32_t gen, uint32_t first) {
+  int32_t best = mem[below(or_draw32(seed, slot, gen, TAG_GA, first), (uint32_t)m)];
+  for (int32_t t = 1; t < tour; ++t) {
+    int32_t c = mem[below(or_draw32(seed, slot, gen, TAG_GA, first + t), (uint32_t)m)];
+    if (better(fit, c, best)) best = c;
+  }
+  return best;
+}
+
+/* Island c owns the slots of its members.  With min(E, m_c) elites per
+ * island and the child draws of slot n exactly as in or_ga_step, one island
+ * holding the whole population is the plain generation. */
+void or_island_step(const uint8_t* pop, const double* fit, int32_t L, int32_t K,
+                    const or_ga_params* gp, int32_t gen, const int32_t* label, int32_t C,
+                    uint8_t* next) {
+  const int32_t N = gp->N, T = gp->tour;
+  const int64_t LK = (int64_t)L * K;
+  int32_t* mem = (int32_t*)malloc(sizeof(int32_t) * (size_t)N);
+  char* taken = (char*)malloc((size_t)N);
+  for (int32_t c = 0; c < C; ++c) {
+    int32_t m = 0;
+    for (int32_t n = 0; n < N; ++n)
+      if (label[n] == c) mem[m++] = n;
+    if (m == 0) continue;
+    const int32_t Ec = gp->E < m ? gp->E : m;
+    /* the island's elites, best first, into its first slots */
+    memset(taken, 0, (size_t)N);
+    for (int32_t e = 0; e < Ec; ++e) {
+      int32_t best = -1;
+      for (int32_t i = 0; i < m; ++i)
+        if (!taken[mem[i]] && (best < 0 || better(fit, mem[i], best))) best = mem[i];
+      taken[best] = 1;
+      memcpy(next + mem[e] * LK, pop + best * LK, (size_t)LK);
+    }
+    for (int32_t i = Ec; i < m; ++i) {
+      const int32_t n = mem[i];
+      uint8_t* child = next + n * LK;
+      int32_t a = island_tournament(fit, mem, m, T, gp->seed, n, gen, 0);
+      int32_t b = island_tournament(fit, mem, m, T, gp->seed, n, gen, (uint32_t)T);
+      uint32_t u_cross = or_draw32(gp->seed, n, gen, TAG_GA, (uint32_t)(2 * T));
+      uint32_t u_cut = or_draw32(gp->seed, n, gen, TAG_GA, (uint32_t)(2 * T + 1));
+      int32_t cut = L;
+      if ((uint64_t)u_cross < gp->pc_thresh) cut = 1 + (int32_t)below(u_cut, (uint32_t)(L - 1));
+      for (int32_t l = 0; l < L; ++l) {
+        const uint8_t* src = (l < cut) ? pop + a * LK : pop + b * LK;
+        memcpy(child + l * K, src + l * K, (size_t)K);
+      }
+      for (int32_t l = 0; l < L; ++l) {
+        uint32_t base = (uint32_t)(2 * T + 2 + 3 * l);
+        uint32_t u_mut = or_draw32(gp->seed, n, gen, TAG_GA, base);
+        uint32_t ui = or_draw32(gp->seed, n, gen, TAG_GA, base + 1);
+        uint32_t uj = or_draw32(gp->seed, n, gen, TAG_GA, base + 2);
+        if ((uint64_t)u_mut < gp->pm_thresh) swap_two(child + l * K, K, ui, uj);
+      }
+    }
+  }
+  free(mem);
+  free(taken);
+}
+
+void or_solve_islands(const double* beta, int32_t L, int32_t K, const or_sinr_params* sp,
+                      const or_ga_params* gp, const int32_t* user_xy_mm, const int32_t* bs_xy_mm,
+                      int32_t kmeans_k, int32_t kmeans_max_iter, int32_t n_seeded, int32_t G,
+                      int32_t C, int32_t R, int32_t iters, uint8_t* pop_out, double* fit_out,
+                      uint8_t* best_out, double* best_fit, double* hist_best,
+                      int32_t* label_out) {
+  const int32_t N = gp->N;
+  const int64_t LK = (int64_t)L * K;
+  uint8_t* pop = (uint8_t*)malloc((size_t)(N * LK));
+  uint8_t* nxt = (uint8_t*)malloc((size_t)(N * LK));
+  double* fit = (double*)malloc(sizeof(double) * (size_t)N);
+  int32_t* label = (int32_t*)malloc(sizeof(int32_t) * (size_t)N);
+  for (int32_t n = 0; n < N; ++n) label[n] = 0;
+  initial_population(L, K, gp, user_xy_mm, bs_xy_mm, kmeans_k, kmeans_max_iter, n_seeded, pop);
+  for (int32_t g = 0; g < G; ++g) {
+    /* Alg. 2: apply K-means (every R generations) and compute fitness */
+    or_fitness_batch(beta, L, K, pop, N, sp, fit);
+    if (hist_best) hist_best[g] = fit[argbest(fit, N)];
+    if (g % R == 0) or_pop_kmeans(pop, N, L, K, C, iters, gp->seed, g, label, NULL);
+    /* every island evolves on its own slots; the union is the population */
+    or_island_step(pop, fit, L, K, gp, g, label, C, nxt);
+    uint8_t* t = pop;
+    pop = nxt;
+    nxt = t;
+  }
+  or_fitness_batch(beta, L, K, pop, N, sp, fit);
+  int32_t b = argbest(fit, N);
+  if (hist_best) hist_best[G] = fit[b];
+  if (pop_out) memcpy(pop_out, pop, (size_t)(N * LK));
+  if (fit_out) memcpy(fit_out, fit, sizeof(double) * (size_t)N);
+  if (best_out) memcpy(best_out, pop + b * LK, (size_t)LK);
+  if (best_fit) *best_fit = fit[b];
+  if (label_out) memcpy(label_out, label, sizeof(int32_t) * (size_t)N);
+  free(pop);
+  free(nxt);
+  free(fit);
+  free(label);
 }
 
 /* ------------------------------------------------------------------------ */

@@ -12,8 +12,9 @@
  *   X[l*K + k]             pilot of user k of cell l; each row l is a
  *                          permutation of 0..K-1 (Sec. 4.1 chromosome)
  *
- * Parity status of every function is listed in its comment; all are pinned
- * by tests under tests/ (see test_oracle_*.py) unless stated otherwise.
+ * Every function is pinned by the tests under tests/ (test_oracle_*.py):
+ * hand-computed values, closed forms, invariants, brute force, scikit-learn's
+ * Lloyd iteration, numpy's Philox, chi-square tests of the random draws.
  * Parity unpinned: whether the GA as a whole reproduces the paper's
  * convergence figures (Fig. 4, 82 s / 116 s) -- the paper's runs, seeds and
  * data are not available; every function here is pinned.
@@ -30,13 +31,20 @@ extern "C" {
 /* SINR model selector. */
 enum { OR_ASYMPTOTIC = 0, OR_FINITE_M = 1 };
 
-/* Parameters of the SINR model.  Only read in OR_FINITE_M mode except mode. */
+/* Objective: the sum SE of Eq. 7, or the smallest per-user SINR (the
+   max-min SIR objective stated in Sec. 2). */
+enum { OR_OBJ_SUM_SE = 0, OR_OBJ_MIN_SINR = 1 };
+
+/* Parameters of the SINR model.  Only read in OR_FINITE_M mode except mode
+   and objective. */
 typedef struct {
   int32_t mode;   /* OR_ASYMPTOTIC (Eq. 4-5) or OR_FINITE_M (Eq. 3 reading) */
   int32_t tau_p;  /* pilot length */
   double M;       /* BS antennas */
   double rho;     /* transmit SNR scale (power / noise unit) */
   double sigma2;  /* noise variance */
+  int32_t objective; /* OR_OBJ_SUM_SE or OR_OBJ_MIN_SINR */
+  int32_t pad0;
 } or_sinr_params;
 
 /* GA parameters (Alg. 1): elitism, tournament with replacement, row-wise
@@ -60,7 +68,8 @@ uint32_t or_draw32(uint64_t seed, uint64_t slot, uint64_t gen, uint64_t tag, uin
 /* log2 by the atanh series (Abramowitz & Stegun 4.1.27), x >= 1. */
 double or_log2_det(double x);
 
-/* Fitness of one chromosome: sum-SE, Eq. 6 with per-user SE of Eq. 5.
+/* Fitness of one chromosome: sum-SE, Eq. 6 with per-user SE of Eq. 5
+ * (OR_OBJ_SUM_SE), or the smallest per-user SINR (OR_OBJ_MIN_SINR, Sec. 2).
  * sinr_out / se_out (optional, L*K) receive the per-user values. */
 double or_fitness(const double* beta, int32_t L, int32_t K, const uint8_t* X,
                   const or_sinr_params* sp, double* sinr_out, double* se_out);
@@ -96,6 +105,39 @@ void or_solve(const double* beta, int32_t L, int32_t K, const or_sinr_params* sp
               int32_t kmeans_k, int32_t kmeans_max_iter, int32_t n_seeded, int32_t G,
               uint8_t* pop_out, double* fit_out, uint8_t* best_out, double* best_fit,
               double* hist_best);
+
+/* ---- PK-means GA (Alg. 2): islands of the population found by K-means.
+ * A chromosome is represented by its one-hot pilot indicators (one K-vector
+ * per user), so the squared distance between two chromosomes is twice the
+ * number of users whose pilots differ, and a centroid holds, per user, the
+ * fraction of the cluster's members giving that user each pilot.  Integer
+ * arithmetic throughout (requires N <= 4096, L*K <= 4096). */
+
+/* Lloyd's K-means of the N chromosomes into C clusters (Alg. 2 "Apply
+ * K-means"); initial centroids are C distinct members drawn by a partial
+ * Fisher-Yates shuffle keyed by generation gen (init_out, optional, C:
+ * their indices).  label (N) out; returns the number of assignment passes. */
+int32_t or_pop_kmeans(const uint8_t* pop, int32_t N, int32_t L, int32_t K, int32_t C,
+                      int32_t max_iter, uint64_t seed, int32_t gen, int32_t* label,
+                      int32_t* init_out);
+
+/* One generation of the island GA (Alg. 2 loop body): each cluster c of
+ * label evolves on its own slots -- elites, tournaments over its members,
+ * crossover, mutation -- with the draws of or_ga_step. */
+void or_island_step(const uint8_t* pop, const double* fit, int32_t L, int32_t K,
+                    const or_ga_params* gp, int32_t gen, const int32_t* label, int32_t C,
+                    uint8_t* next);
+
+/* Whole island solve: seeding as or_solve, then G generations, the
+ * population re-clustered into C islands every R generations (Sec. 6.1:
+ * every three) with at most iters passes.  label_out (N, optional): the
+ * last clustering. */
+void or_solve_islands(const double* beta, int32_t L, int32_t K, const or_sinr_params* sp,
+                      const or_ga_params* gp, const int32_t* user_xy_mm, const int32_t* bs_xy_mm,
+                      int32_t kmeans_k, int32_t kmeans_max_iter, int32_t n_seeded, int32_t G,
+                      int32_t C, int32_t R, int32_t iters, uint8_t* pop_out, double* fit_out,
+                      uint8_t* best_out, double* best_fit, double* hist_best,
+                      int32_t* label_out);
 
 /* Exhaustive search (EX-PA): row 0 fixed to the identity unless all_rows. */
 double or_exhaustive(const double* beta, int32_t L, int32_t K, const or_sinr_params* sp,
