@@ -40,9 +40,7 @@ sys.path.insert(0, ROOT)
 L, K, TAU_P, M_ANT, N_POP, G_GEN, KMEANS_K = 19, 10, 10, 256.0, 256, 200, 10
 BATCH_LOG2 = 20
 # DRAM bytes (read + write) per launch of the two roofline kernels, from one
-# ncu capture each (profiles/k_solve_L19_K10_N256_G200.md,
-# profiles/k_eval_f32_pilot_2e20_L19_K10.md); set to None when a kernel
-# changes until it is captured again
+# ncu capture of each; None while a kernel has changed since its capture
 TRAFFIC_K_SOLVE = 146_432
 TRAFFIC_EVAL = 204_982_784
 METRIC = ("chromosome fitness evals/sec and GA gens/sec (L=19,K=10); "
@@ -156,9 +154,58 @@ def oracle_solve_step(inst, seed):
                         kmeans_k=KMEANS_K)
 
 
+def host_cpu():
+    """Host core count and CPU model (lscpu), for the CPU baseline record."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return {"nproc": os.cpu_count(), "model": model}
+
+
+def oracle_eval_all_cores(inst, seconds=6.0):
+    """The oracle's fitness evaluation (FP64, unchanged arithmetic) over
+    chromosomes split across every host core: one thread per core, each
+    calling the C oracle on its own chunk (ctypes releases the GIL during the
+    call).  Returns (evals/s, threads, chromosomes evaluated, seconds)."""
+    import concurrent.futures as cf
+
+    import numpy as np
+
+    import oracle
+    from paper_2511_20511_gb300 import inputs
+
+    threads = os.cpu_count() or 1
+    sp = oracle.sinr_params(oracle.FINITE_M, TAU_P, M_ANT, inst["rho"], 1.0)
+    chunk = 2048
+    pops = [inputs.random_population(chunk, L, K, seed=50 + t) for t in range(threads)]
+    oracle.fitness_batch(inst["beta"], pops[0][:8], sp)  # build + warm
+
+    def work(t):
+        n = 0
+        t_end = time.perf_counter() + seconds
+        while time.perf_counter() < t_end:
+            oracle.fitness_batch(inst["beta"], pops[t], sp)
+            n += chunk
+        return n
+
+    t0 = time.perf_counter()
+    with cf.ThreadPoolExecutor(max_workers=threads) as ex:
+        total = sum(ex.map(work, range(threads)))
+    dt = time.perf_counter() - t0
+    return total / dt, threads, total, dt
+
+
 def cpu_baseline(target_s=12.0):
-    """The oracle as it stands, single thread, on a bounded sample: whole
-    solves of the benchmark instance repeated for about target_s seconds."""
+    """The oracle as it stands on a bounded sample: whole solves of the
+    benchmark instance on one core for about target_s seconds (the solve is
+    one dependent chain), and the population evaluation alone on every host
+    core (chromosomes are independent) for about half that."""
     inst = make_instance(0)
     oracle_solve_step(inst, 0)  # build + warm
     t0 = time.perf_counter()
@@ -170,10 +217,17 @@ def cpu_baseline(target_s=12.0):
         if dt >= target_s:
             break
     evals = reps * N_POP * (G_GEN + 1)
+    ev_rate, threads, n_ev, ev_s = oracle_eval_all_cores(inst, seconds=target_s / 2)
     return {"value": evals / dt, "unit": "evals/s", "cores": 1, "kind": "oracle",
             "sample": f"{reps} whole solves of the benchmark instance (N=256, G=200), "
                       f"{dt:.1f} s, FP64 plain C, single thread",
-            "gens_per_s": reps * G_GEN / dt}
+            "gens_per_s": reps * G_GEN / dt,
+            "host": host_cpu(),
+            "eval_all_cores": {"value": ev_rate, "unit": "evals/s", "cores": threads,
+                               "kind": "oracle",
+                               "sample": f"{n_ev} random chromosomes of the benchmark instance "
+                                         f"evaluated in {ev_s:.1f} s, FP64 plain C, one "
+                                         f"thread per host core"}}
 
 
 # ---------------------------------------------------------------- reference arm
@@ -562,8 +616,7 @@ def run_serving(B, inputs, rate=2000.0, seconds=2.0, G=40, N=64, tick=20, budget
     arr = arr[arr < seconds]
     n = len(arr)
     shapes = [(int(rng.choice([7, 19])), int(rng.choice([8, 16]))) for _ in range(n)]
-    insts = [inputs.instance(L, K, seed=10_000 + i, dtype=np.float32)
-             for i, (L, K) in enumerate(shapes)]
+    insts = make_serving_instances(shapes)
     base = B.pa_config_default(7, 8, mode=B.PA_SINR_FINITE_M, M=256.0, N=N,
                                rho=insts[0]["rho"])
 
@@ -645,6 +698,31 @@ def run_serving(B, inputs, rate=2000.0, seconds=2.0, G=40, N=64, tick=20, budget
             "timing": "host wall clock; arrivals replayed in real time"}
 
 
+def _serving_instance(job):
+    """One serving request's instance (runs in a worker process)."""
+    import numpy as np
+
+    from paper_2511_20511_gb300 import inputs
+
+    i, L, K = job
+    return inputs.instance(L, K, seed=10_000 + i, dtype=np.float32)
+
+
+def make_serving_instances(shapes):
+    """The fresh instance of every request (seed 10000 + request id), built on
+    all host cores by spawned worker processes before the replay starts."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+
+    jobs = [(i, L, K) for i, (L, K) in enumerate(shapes)]
+    workers = max(1, min(os.cpu_count() or 1, 32))
+    if len(jobs) < 256 or workers == 1:
+        return [_serving_instance(j) for j in jobs]
+    with cf.ProcessPoolExecutor(max_workers=workers,
+                                mp_context=mp.get_context("spawn")) as ex:
+        return list(ex.map(_serving_instance, jobs, chunksize=128))
+
+
 def run_stream_only(args, B, inputs, dev):
     """Only the 61-cell, 32-user streamed evaluation of 2^17 chromosomes (for
     profilers)."""
@@ -694,8 +772,9 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--serve-tick", type=int, default=20,
                     help="generations per scheduling tick of the serving comparison")
-    ap.add_argument("--serve-seconds", type=float, default=2.0,
-                    help="length of the Poisson arrival window of the serving comparison")
+    ap.add_argument("--serve-seconds", type=float, default=10.0,
+                    help="length of the Poisson arrival window of the serving comparison "
+                         "(the configured workload: 10 s at 2000 requests/s)")
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the 512-instance batched-solve comparison")
     ap.add_argument("--only", choices=["all", "eval", "solve", "stream", "batch"],

@@ -16,7 +16,8 @@
  *                          (Sec. 4.1: one row per cell, each row a
  *                          permutation of 0..K-1).  Row-major, no padding.
  *   fitness                float32 (PA_FP32 contexts) or float64 (PA_FP64),
- *                          one value per chromosome: sum SE of Eq. 6.
+ *                          one value per chromosome: sum SE of Eq. 6, or
+ *                          the smallest per-user SINR (PA_OBJ_MIN_SINR).
  *   "device" pointers      CUDA global memory on the context's device.
  *   "host" pointers        ordinary (pageable or pinned) host memory.
  *   Ownership              the caller owns every buffer it passes; the
@@ -68,6 +69,13 @@ enum {
                              M b^2 / (M S2 + (B_j + s2/rho)(S1 + s2/(tau_p rho))) */
 };
 
+/* Objective maximised by the GA. */
+enum {
+  PA_OBJ_SUM_SE = 0,  /* Eq. 7: sum over users of log2(1 + SINR) (Eq. 5-6)    */
+  PA_OBJ_MIN_SINR = 1 /* Sec. 2: the smallest per-user SINR (max-min), with the
+                         SINR of the chosen mode (not passed through log2)     */
+};
+
 /*
  * Configuration.  Fill with pa_config_default() and override fields.
  * Layout is fixed (128 bytes, natural alignment).
@@ -91,7 +99,13 @@ typedef struct {
   int32_t kmeans_max_iter; /* assignment passes (>= 1)                     */
   int32_t n_seeded; /* members built from the K-means assignment (0..N)   */
   int32_t flags;    /* 0, or PA_FLAG_TEST_STALL_COPIES                      */
-  int64_t reserved[4]; /* must be 0                                        */
+  int32_t objective;   /* PA_OBJ_SUM_SE or PA_OBJ_MIN_SINR                  */
+  int32_t islands;     /* 0 or 1: one population (Alg. 1); C in 2..64: the
+                          PK-means GA of Alg. 2 with C islands (N <= 4096)  */
+  int32_t recluster;   /* islands: generations between re-clusterings of
+                          the population (>= 1; Sec. 6.1: every three)      */
+  int32_t island_iter; /* islands: K-means passes per re-clustering (>= 1)  */
+  int64_t reserved[2]; /* must be 0                                        */
 } pa_config;
 
 /*
@@ -105,11 +119,12 @@ typedef struct {
 #define PA_FLAG_TEST_STALL_COPIES 1
 
 /*
- * Defaults for an L-cell, K-user layout: FP32, asymptotic SINR (the
- * objective of Eq. 7), tau_p = K, M = 256, rho = 10 / 500^-3.8 (10 dB at a
+ * Defaults for an L-cell, K-user layout: FP32, asymptotic SINR, sum-SE
+ * objective (Eq. 7), tau_p = K, M = 256, rho = 10 / 500^-3.8 (10 dB at a
  * 500 m cell edge without shadowing), sigma2 = 1, N = 256, E = 2, tour = 3,
  * p_c = 0.9 (Table 1), p_m = 0.05 per row, seed 0, kmeans_k = K,
- * kmeans_max_iter = 100, n_seeded = (N + 1) / 2.
+ * kmeans_max_iter = 100, n_seeded = (N + 1) / 2, islands = 0 (one
+ * population), recluster = 3 and island_iter = 100 (used once islands >= 2).
  * Returns PA_EINVAL if cfg is NULL.
  */
 pa_status pa_config_default(pa_config* cfg, int32_t L, int32_t K);
@@ -189,13 +204,21 @@ pa_status pa_ga_step(pa_ctx* ctx, const uint8_t* pop_dev, const void* fit_dev,
  */
 pa_status pa_kmeans_seed(pa_ctx* ctx, int32_t* labels_host, double* centroids_host);
 
-/* Run `generations` GA generations on the resident population.  Async. */
+/*
+ * Run `generations` GA generations on the resident population.  Async.
+ * With cfg.islands = C >= 2 every generation is one of Alg. 2: before the
+ * generations whose counter is a multiple of cfg.recluster (and before the
+ * first one after seeding, pa_set_population or pa_load_instance) the
+ * population is re-clustered into C islands (pa_island_cluster), then each
+ * island evolves on its own slots (pa_island_step).
+ */
 pa_status pa_step(pa_ctx* ctx, int32_t generations);
 
 /*
- * Whole solve (Alg. 1): seed (pa_kmeans_seed), `generations` generations,
- * final evaluation, best member by (fitness desc, index asc).  best_host:
- * L*K bytes; best_fit: its fitness.  Synchronous.
+ * Whole solve (Alg. 1, or Alg. 2 with cfg.islands >= 2): seed
+ * (pa_kmeans_seed), `generations` generations, final evaluation, best member
+ * by (fitness desc, index asc).  best_host: L*K bytes; best_fit: its
+ * fitness.  Synchronous.
  */
 pa_status pa_solve(pa_ctx* ctx, int32_t generations, uint8_t* best_host, double* best_fit);
 
@@ -213,6 +236,48 @@ pa_status pa_set_population(pa_ctx* ctx, const uint8_t* pop_host, int32_t genera
 
 /* Device pointers of the resident population and its fitness buffer. */
 pa_status pa_population_device(pa_ctx* ctx, uint8_t** pop_dev, void** fit_dev);
+
+/* ------------------------------------------------------------------------
+ * PK-means GA (Sec. 4.3, Alg. 2): the population is partitioned by K-means
+ * into C = cfg.islands clusters ("islands") that evolve independently.  A
+ * chromosome is represented by its one-hot pilot indicators (one K-vector
+ * per user): the squared distance of two chromosomes is twice the number of
+ * users whose pilots differ, and a centroid holds each user's pilot
+ * frequencies over the cluster's members.  Distances are compared exactly
+ * in integer arithmetic.  Requires a context created with islands >= 2.
+ * ------------------------------------------------------------------------ */
+
+/*
+ * K-means of the N chromosomes of pop_dev (device, N*L*K bytes) into
+ * cfg.islands clusters: initial centroids are distinct members drawn by a
+ * partial Fisher-Yates shuffle keyed by (seed, generation); at most
+ * cfg.island_iter Lloyd passes; ties go to the lower cluster; an emptied
+ * cluster keeps its centroid.  labels_dev: device, N int32 (cluster of each
+ * member).  passes_host (optional): the number of assignment passes; when
+ * given the call synchronises, otherwise it is asynchronous.
+ */
+pa_status pa_island_cluster(pa_ctx* ctx, const uint8_t* pop_dev, int32_t generation,
+                            int32_t* labels_dev, int32_t* passes_host);
+
+/*
+ * One generation of Alg. 2 from population pop_dev and its fitness fit_dev
+ * (device, N values) with the clustering labels_dev (device, N int32 in
+ * 0..C-1; other values are clamped into that range) into next_dev (device,
+ * must not overlap pop_dev).  Island c owns the slots of its members: its
+ * min(E, m_c) best members (fitness desc, index asc) go unchanged to its
+ * lowest slots, every other slot gets a child of two tournaments among the
+ * island's members, crossover and mutation with the draws pa_ga_step uses
+ * for that slot -- so a single island is exactly pa_ga_step.  Asynchronous.
+ */
+pa_status pa_island_step(pa_ctx* ctx, const uint8_t* pop_dev, const void* fit_dev,
+                         const int32_t* labels_dev, int32_t generation, uint8_t* next_dev);
+
+/*
+ * Island of every member of the resident population (host, N int32), from
+ * the last re-clustering of pa_step / pa_solve (all -1 before the first).
+ * Synchronous.
+ */
+pa_status pa_get_islands(pa_ctx* ctx, int32_t* labels_host);
 
 /*
  * Check that every row of n chromosomes (device) is a permutation of
@@ -282,46 +347,80 @@ const char* pa_batch_last_error(const pa_batch* b);
 /* ------------------------------------------------------------------------
  * Continuous-batching server.  Requests (one instance each) are queued by
  * pa_server_submit; each pa_server_poll runs one scheduling tick: queued
- * requests are admitted into resident slots of their (L, K) class while
- * the device memory of the slots stays within the budget, newly admitted
- * slots are seeded (one launch), every active slot advances by up to `tick`
- * generations (one persistent launch per kernel variant; populations stay
- * resident between ticks), and requests that reach `generations` are
- * returned.  A request's result equals pa_solve's for the same instance,
- * configuration and seed.  Not thread safe.
+ * requests are admitted, in arrival order, into resident slots of their
+ * (L, K) class while the device memory of the slots stays within the budget
+ * (idle slots of other classes are destroyed when the next request needs
+ * their memory), newly admitted slots are seeded (one launch), every active
+ * slot advances by up to `tick` generations (one persistent launch per
+ * kernel variant; populations stay resident between ticks), and requests
+ * that reach `generations` are queued as completions.  A request's result
+ * equals pa_solve's for the same instance, configuration and seed.  A
+ * request whose admission fails (its slot cannot be created or loaded)
+ * completes with that status; the others are not affected.  Not thread
+ * safe.
  * ------------------------------------------------------------------------ */
 typedef struct pa_server pa_server;
 
 /* Create a server: base supplies every configuration field except L, K,
  * tau_p and kmeans_k (set from each request: tau_p = kmeans_k = K) and seed
  * (per request).  budget_bytes bounds the device memory of all slots.
- * stream: cudaStream_t or NULL (a stream of its own). */
+ * stream: cudaStream_t or NULL (a stream of its own).  PA_EINVAL for an
+ * invalid base; PA_EUNSUPPORTED for islands >= 2 (islands run per
+ * generation, outside the batched solve kernel). */
 pa_status pa_server_create(const pa_config* base, int32_t generations, int32_t tick,
                            uint64_t budget_bytes, void* stream, pa_server** out);
 
 /* Destroy a server and its slots (NULL is ignored). */
 void pa_server_destroy(pa_server* s);
 
-/* Queue a request: beta (L*L*K float64), user_xy_mm (L*K*2), bs_xy_mm (L*2)
- * host arrays, copied before returning; id is returned on completion. */
+/*
+ * Queue a request: beta (L*L*K float64, finite and > 0), user_xy_mm (L*K*2),
+ * bs_xy_mm (L*2) host arrays, copied before returning; id is returned on
+ * completion.  Checked here, before anything is queued: PA_EINVAL for an
+ * invalid shape or invalid values (as pa_create would reject them),
+ * PA_EUNSUPPORTED for a shape the batched solve kernel cannot run, PA_EBUSY
+ * when one slot of this shape alone needs more device memory than the
+ * budget.  PA_ENOMEM if the host copy cannot be made.
+ */
 pa_status pa_server_submit(pa_server* s, int64_t id, int32_t L, int32_t K, uint64_t seed,
                            const double* beta, const int32_t* user_xy_mm,
                            const int32_t* bs_xy_mm);
 
 /*
- * One scheduling tick (synchronous).  Up to max_done finished requests are
- * returned: done_ids[i], their best member at done_best + i*best_stride
- * (L*K bytes) and its fitness done_fit[i] (each output optional);
+ * One scheduling tick (synchronous), then up to max_done completions are
+ * returned in completion order (the rest wait for later polls): done_ids[i],
+ * done_status[i] (PA_OK, or why the request failed), their best member at
+ * done_best + i*best_stride (L*K bytes; zeros for a failed request) and its
+ * fitness done_fit[i] (NaN for a failed request) -- each output optional;
  * *n_done = how many.  n_active / n_pending (optional): slots still running
- * and requests still queued after the tick.
+ * and requests still queued after the tick.  An error status means the tick
+ * itself failed (a CUDA error): completions already queued stay queued.
  */
-pa_status pa_server_poll(pa_server* s, int32_t max_done, int64_t* done_ids, uint8_t* done_best,
-                         int64_t best_stride, double* done_fit, int32_t* n_done,
-                         int32_t* n_active, int32_t* n_pending);
+pa_status pa_server_poll(pa_server* s, int32_t max_done, int64_t* done_ids, int32_t* done_status,
+                         uint8_t* done_best, int64_t best_stride, double* done_fit,
+                         int32_t* n_done, int32_t* n_active, int32_t* n_pending);
 
-/* Device bytes held by slots, number of slots, requests completed. */
+/*
+ * Withdraw request `id`: removed from the queue, or its slot released (the
+ * slot stays resident for the next request of its class), or its unreturned
+ * completion dropped.  No GPU work is in flight between polls, so this is
+ * immediate.  PA_EINVAL when no queued, running or unreturned request has
+ * this id.
+ */
+pa_status pa_server_cancel(pa_server* s, int64_t id);
+
+/* Device bytes held by slots, number of slots, requests completed (with or
+ * without an error). */
 pa_status pa_server_stats(const pa_server* s, uint64_t* used_bytes, int32_t* n_slots,
                           int64_t* completed);
+
+/*
+ * Testing the admission failure path without a device fault: the next
+ * `count` admissions fail as if their slot could not be created (status
+ * PA_ECUDA, nothing runs on the GPU for them).  The paper has no
+ * counterpart.
+ */
+pa_status pa_server_inject_admission_failures(pa_server* s, int32_t count);
 
 /* Last error message of a server ("" if none). */
 const char* pa_server_last_error(const pa_server* s);
@@ -335,14 +434,15 @@ const char* pa_server_last_error(const pa_server* s);
  * Fitness evaluation that allocates nothing.  The paper has no counterpart:
  * this entry point exists for callers that cannot allocate device memory --
  * a real-time scheduling loop that must not take cudaMalloc's implicit
- * synchronisation, a framework that hands out all device memory from its own
- * pool, or code running while a stream is captured.  It computes exactly what
+ * device-wide synchronisation and unbounded latency, or a framework that
+ * hands out all device memory from its own pool.  It computes exactly what
  * pa_create + pa_eval_population + pa_destroy compute for the same cfg and
  * beta, without a context: the instance copy and the prepared tables go to a
  * file-scope device array of PA_NOALLOC_SCRATCH_BYTES bytes that every GPU
  * holds from library load to process exit.
- *   cfg      configuration (as for pa_create; only the instance and SINR
- *            fields matter; prec selects the fitness type)
+ *   cfg      configuration: must pass the same validation as for pa_create
+ *            (every field, the GA ones included); the instance, SINR and
+ *            objective fields and prec (the fitness type) are the ones used
  *   beta     host, L*L*K float64 gains (as for pa_create)
  *   pop_dev  device, n*L*K bytes;  fit_dev  device, n float32 / float64
  *   stream   cudaStream_t or NULL
@@ -353,8 +453,8 @@ const char* pa_server_last_error(const pa_server* s);
  * make that first call before any stream capture.  All calls share the array
  * and leave their data in it; each call rewrites what it reads, but calls
  * whose GPU work overlaps (unordered streams, concurrent host threads on one
- * device) race and give undefined results.  Synchronises the stream before
- * returning (the host beta is copied asynchronously).
+ * device) race and give undefined results.  Copies beta from host memory and
+ * synchronises the stream before returning.
  */
 pa_status pa_eval_population_noalloc(const pa_config* cfg, const double* beta,
                                      const uint8_t* pop_dev, int64_t n, void* fit_dev,
@@ -364,7 +464,9 @@ pa_status pa_eval_population_noalloc(const pa_config* cfg, const double* beta,
 const char* pa_status_str(pa_status s);
 
 /* Last error message of a context ("" if none).  With ctx == NULL: the
- * reason for the calling thread's last failed pa_create. */
+ * reason for the calling thread's last failed pa_create, pa_batch_create,
+ * pa_server_create or pa_eval_population_noalloc (each of these clears it
+ * when it starts). */
 const char* pa_last_error(const pa_ctx* ctx);
 
 /* Number of CUDA kernels this library has launched in this process (all

@@ -18,6 +18,7 @@ PA_OK, PA_EINVAL, PA_ENOMEM, PA_ECUDA, PA_ETIMEOUT, PA_EUNSUPPORTED, PA_EBUSY = 
 PA_FLAG_TEST_STALL_COPIES = 1
 PA_FP32, PA_FP64 = 0, 1
 PA_SINR_ASYMPTOTIC, PA_SINR_FINITE_M = 0, 1
+PA_OBJ_SUM_SE, PA_OBJ_MIN_SINR = 0, 1
 
 
 class pa_config(C.Structure):
@@ -26,7 +27,9 @@ class pa_config(C.Structure):
                 ("prec", C.c_int32), ("N", C.c_int32), ("E", C.c_int32), ("tour", C.c_int32),
                 ("pc_thresh", C.c_uint64), ("pm_thresh", C.c_uint64), ("seed", C.c_uint64),
                 ("kmeans_k", C.c_int32), ("kmeans_max_iter", C.c_int32),
-                ("n_seeded", C.c_int32), ("flags", C.c_int32), ("reserved", C.c_int64 * 4)]
+                ("n_seeded", C.c_int32), ("flags", C.c_int32), ("objective", C.c_int32),
+                ("islands", C.c_int32), ("recluster", C.c_int32), ("island_iter", C.c_int32),
+                ("reserved", C.c_int64 * 2)]
 
 
 assert C.sizeof(pa_config) == 128
@@ -60,6 +63,11 @@ _SIGS = {
     "pa_population_device": (C.c_int, [C.c_void_p, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p)]),
     "pa_validate_population": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64,
                                          C.POINTER(C.c_int64)]),
+    "pa_island_cluster": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p,
+                                    C.POINTER(C.c_int32)]),
+    "pa_island_step": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32,
+                                 C.c_void_p]),
+    "pa_get_islands": (C.c_int, [C.c_void_p, C.c_void_p]),
     "pa_status_str": (C.c_char_p, [C.c_int]),
     "pa_last_error": (C.c_char_p, [C.c_void_p]),
     "pa_kernel_launches": (C.c_uint64, []),
@@ -78,9 +86,11 @@ _SIGS = {
     "pa_server_destroy": (None, [C.c_void_p]),
     "pa_server_submit": (C.c_int, [C.c_void_p, C.c_int64, C.c_int32, C.c_int32, C.c_uint64,
                                    C.c_void_p, C.c_void_p, C.c_void_p]),
-    "pa_server_poll": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_int64,
-                                 C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
-                                 C.POINTER(C.c_int32)]),
+    "pa_server_poll": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p,
+                                 C.c_int64, C.c_void_p, C.POINTER(C.c_int32),
+                                 C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
+    "pa_server_cancel": (C.c_int, [C.c_void_p, C.c_int64]),
+    "pa_server_inject_admission_failures": (C.c_int, [C.c_void_p, C.c_int32]),
     "pa_server_stats": (C.c_int, [C.c_void_p, C.POINTER(C.c_uint64), C.POINTER(C.c_int32),
                                   C.POINTER(C.c_int64)]),
     "pa_server_last_error": (C.c_char_p, [C.c_void_p]),
@@ -270,6 +280,26 @@ def pa_validate_population(ctx, pop, n=None):
     return bad.value
 
 
+def pa_island_cluster(ctx, pop, generation, labels):
+    """K-means of a device population into islands (labels: device int32 N);
+    returns the number of assignment passes."""
+    passes = C.c_int32(0)
+    _check(lib().pa_island_cluster(ctx, _dev_ptr(pop), int(generation), _dev_ptr(labels),
+                                   C.byref(passes)), ctx)
+    return passes.value
+
+
+def pa_island_step(ctx, pop, fit, labels, generation, next_pop):
+    _check(lib().pa_island_step(ctx, _dev_ptr(pop), _dev_ptr(fit), _dev_ptr(labels),
+                                int(generation), _dev_ptr(next_pop)), ctx)
+
+
+def pa_get_islands(ctx, n):
+    out = np.zeros(n, dtype=np.int32)
+    _check(lib().pa_get_islands(ctx, _host_ptr(out)), ctx)
+    return out
+
+
 # ------------------------------------------------------------------ convenience
 class Context:
     """Owns one pa_ctx.  Methods mirror the C entry points."""
@@ -455,6 +485,7 @@ class Server:
         self.handle = out
         self.max_done = max_done
         self._ids = np.zeros(max_done, dtype=np.int64)
+        self._st = np.zeros(max_done, dtype=np.int32)
         self._best = np.zeros((max_done, self.MAX_LK), dtype=np.uint8)
         self._fit = np.zeros(max_done, dtype=np.float64)
 
@@ -470,14 +501,29 @@ class Server:
         self._scheck(lib().pa_server_submit(self.handle, int(rid), int(L), int(K), int(seed),
                                             _host_ptr(b), _host_ptr(u), _host_ptr(s)))
 
-    def poll(self):
+    def poll(self, max_done=None, with_status=False):
+        """One tick; returns ([(id, best row bytes, fitness[, status]) ...],
+        active slots, queued requests)."""
+        md = self.max_done if max_done is None else min(int(max_done), self.max_done)
         nd, na, npd = C.c_int32(0), C.c_int32(0), C.c_int32(0)
-        self._scheck(lib().pa_server_poll(self.handle, self.max_done, _host_ptr(self._ids),
-                                          _host_ptr(self._best), self.MAX_LK, _host_ptr(self._fit),
-                                          C.byref(nd), C.byref(na), C.byref(npd)))
+        self._scheck(lib().pa_server_poll(self.handle, md, _host_ptr(self._ids),
+                                          _host_ptr(self._st), _host_ptr(self._best), self.MAX_LK,
+                                          _host_ptr(self._fit), C.byref(nd), C.byref(na),
+                                          C.byref(npd)))
         k = nd.value
-        return ([(int(self._ids[i]), self._best[i], float(self._fit[i])) for i in range(k)],
-                na.value, npd.value)
+        if with_status:
+            out = [(int(self._ids[i]), self._best[i].copy(), float(self._fit[i]),
+                    int(self._st[i])) for i in range(k)]
+        else:
+            out = [(int(self._ids[i]), self._best[i].copy(), float(self._fit[i]))
+                   for i in range(k)]
+        return out, na.value, npd.value
+
+    def cancel(self, rid):
+        self._scheck(lib().pa_server_cancel(self.handle, int(rid)))
+
+    def inject_admission_failures(self, count):
+        self._scheck(lib().pa_server_inject_admission_failures(self.handle, int(count)))
 
     def stats(self):
         u, ns, c = C.c_uint64(0), C.c_int32(0), C.c_int64(0)

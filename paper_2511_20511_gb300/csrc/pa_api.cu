@@ -151,6 +151,10 @@ pa_status pa_config_default(pa_config* c, int32_t L, int32_t K) {
   c->kmeans_k = K;
   c->kmeans_max_iter = 100;
   c->n_seeded = (c->N + 1) / 2;
+  c->objective = PA_OBJ_SUM_SE;
+  c->islands = 0;
+  c->recluster = 3;
+  c->island_iter = 100;
   return PA_OK;
 }
 
@@ -179,7 +183,17 @@ static pa_status validate_config(const pa_config* c, std::string* why) {
   if (c->kmeans_max_iter < 1) return bad("kmeans_max_iter must be >= 1");
   if (c->n_seeded < 0 || c->n_seeded > c->N) return bad("n_seeded must be in [0, N]");
   if ((c->flags & ~PA_FLAG_TEST_STALL_COPIES) != 0) return bad("unknown flags");
-  for (int i = 0; i < 4; ++i)
+  if (c->objective != PA_OBJ_SUM_SE && c->objective != PA_OBJ_MIN_SINR)
+    return bad("unknown objective");
+  if (c->islands < 0 || c->islands > pa::kMaxIslands) return bad("islands must be in [0, 64]");
+  if (c->recluster < 0 || c->island_iter < 0) return bad("recluster and island_iter must be >= 0");
+  if (c->islands >= 2) {
+    if (c->N > pa::kMaxIslandN) return bad("islands need N <= 4096");
+    if (c->islands > c->N) return bad("islands must be <= N");
+    if (c->recluster < 1 || c->island_iter < 1)
+      return bad("islands need recluster >= 1 and island_iter >= 1");
+  }
+  for (int i = 0; i < 2; ++i)
     if (c->reserved[i] != 0) return bad("reserved fields must be 0");
   return PA_OK;
 }
@@ -205,6 +219,14 @@ static void free_ctx(pa_ctx* c) {
   cudaFreeHost(c->h_best);
   cudaFree(c->stage_pop);
   cudaFree(c->stage_fit);
+  cudaFree(c->isl_label);
+  for (pa::IslandLists* il : {&c->isl_res, &c->isl_usr}) {
+    cudaFree(il->off);
+    cudaFree(il->list);
+    cudaFree(il->pos);
+  }
+  cudaFree(c->isl_cnt);
+  cudaFree(c->isl_passes);
   delete c;
 }
 
@@ -294,6 +316,22 @@ pa_status pa_create(const pa_config* cfg, const double* beta, const int32_t* use
     // best row, then its fitness at the next 8-byte boundary (one copy back)
     if (!chk(cudaMalloc(&c->best_row, best_bytes(LK)), "cudaMalloc best")) break;
     if (!chk(cudaMallocHost(&c->h_best, best_bytes(LK)), "cudaMallocHost best")) break;
+    if (cfg->islands >= 2) {
+      const size_t n4 = sizeof(int32_t) * cfg->N;
+      if (!chk(cudaMalloc(&c->isl_label, n4), "cudaMalloc islands")) break;
+      if (!chk(cudaMemset(c->isl_label, 0xFF, n4), "memset islands")) break;
+      bool ok = true;
+      for (pa::IslandLists* il : {&c->isl_res, &c->isl_usr})
+        ok = ok && chk(cudaMalloc(&il->list, n4), "cudaMalloc islands") &&
+             chk(cudaMalloc(&il->pos, n4), "cudaMalloc islands") &&
+             chk(cudaMalloc(&il->off, sizeof(int32_t) * (cfg->islands + 1)), "cudaMalloc islands");
+      if (!ok) break;
+      if (!chk(cudaMalloc(&c->isl_passes, sizeof(int32_t)), "cudaMalloc islands")) break;
+      if (!pa::island_cnt_in_smem(cfg->N, L, K, cfg->islands) &&
+          !chk(cudaMalloc(&c->isl_cnt, sizeof(int32_t) * (size_t)cfg->islands * LK * K),
+               "cudaMalloc island counts"))
+        break;
+    }
     st = upload_instance(c, beta, user_xy_mm, bs_xy_mm, bmax);
     if (st != PA_OK) break;
     if (!chk(cudaStreamSynchronize(c->stream), "prepare sync")) break;
@@ -320,6 +358,7 @@ pa_status pa_load_instance(pa_ctx* ctx, const double* beta, const int32_t* user_
   if (st != PA_OK) return st;
   ctx->cur = 0;
   ctx->generation = 0;
+  ctx->isl_valid = 0;
   return PA_OK;
 }
 
@@ -428,6 +467,7 @@ pa_status pa_kmeans_seed(pa_ctx* ctx, int32_t* labels_host, double* centroids_ho
     return fail(ctx, PA_EINVAL, "no positions: K-means outputs unavailable");
   ctx->cur = 0;
   ctx->generation = 0;
+  ctx->isl_valid = 0;
   PA_TRY(ctx, pa::launch_seed(ctx, ctx->pop[0], ctx->stream), "seed kernel");
   const int64_t LK = (int64_t)ctx->cfg.L * ctx->cfg.K;
   if (labels_host)
@@ -450,6 +490,30 @@ pa_status pa_kmeans_seed(pa_ctx* ctx, int32_t* labels_host, double* centroids_ho
 static pa_status run_generations(pa_ctx* ctx, int32_t generations, bool* final_evaluated) {
   *final_evaluated = false;
   if (generations == 0) return PA_OK;
+  if (ctx->cfg.islands >= 2) {
+    // Alg. 2: fitness; every `recluster` generations (and whenever the
+    // labels do not belong to this population) K-means into islands and
+    // their member lists; then one island generation
+    for (int32_t g = 0; g < generations; ++g) {
+      uint8_t* cur = ctx->pop[ctx->cur];
+      uint8_t* nxt = ctx->pop[ctx->cur ^ 1];
+      PA_TRY(ctx, eval_any(ctx, cur, ctx->cfg.N, ctx->fit), "eval kernel");
+      if (!ctx->isl_valid || ctx->generation % ctx->cfg.recluster == 0) {
+        PA_TRY(ctx, pa::launch_island_kmeans(ctx, cur, ctx->generation, ctx->isl_label,
+                                             ctx->stream),
+               "island K-means kernel");
+        PA_TRY(ctx, pa::launch_island_lists(ctx, ctx->isl_label, ctx->isl_res, ctx->stream),
+               "island lists kernel");
+        ctx->isl_valid = 1;
+      }
+      PA_TRY(ctx, pa::launch_island_step(ctx, cur, ctx->fit, ctx->isl_label, ctx->isl_res,
+                                         ctx->generation, nxt, ctx->stream),
+             "island step kernel");
+      ctx->cur ^= 1;
+      ctx->generation += 1;
+    }
+    return PA_OK;
+  }
   {
     cudaError_t e = pa::launch_solve(ctx, ctx->pop[ctx->cur], ctx->pop[ctx->cur ^ 1],
                                      ctx->generation, generations, ctx->fit, nullptr, nullptr,
@@ -489,9 +553,11 @@ pa_status pa_solve(pa_ctx* ctx, int32_t generations, uint8_t* best_host, double*
   const int64_t LK = (int64_t)ctx->cfg.L * ctx->cfg.K;
   double* best_dev = reinterpret_cast<double*>(ctx->best_row + ((LK + 7) & ~int64_t(7)));
   // fused path: all generations, the final evaluation and the best member
-  // in one cluster launch
-  cudaError_t e = pa::launch_solve(ctx, ctx->pop[0], ctx->pop[1], 0, generations, ctx->fit,
-                                   ctx->best_row, best_dev, ctx->stream);
+  // in one cluster launch (Alg. 1 only; islands run per generation)
+  cudaError_t e = ctx->cfg.islands >= 2
+                      ? cudaErrorNotSupported
+                      : pa::launch_solve(ctx, ctx->pop[0], ctx->pop[1], 0, generations, ctx->fit,
+                                         ctx->best_row, best_dev, ctx->stream);
   if (e == cudaSuccess) {
     ctx->cur = 1;
     ctx->generation = generations;
@@ -566,6 +632,54 @@ pa_status pa_set_population(pa_ctx* ctx, const uint8_t* pop_host, int32_t genera
   if (bad >= 0) return fail(ctx, PA_EINVAL, "population row is not a permutation");
   ctx->cur ^= 1;
   ctx->generation = generation;
+  ctx->isl_valid = 0;
+  return PA_OK;
+}
+
+pa_status pa_island_cluster(pa_ctx* ctx, const uint8_t* pop_dev, int32_t generation,
+                            int32_t* labels_dev, int32_t* passes_host) {
+  if (!ctx) return PA_EINVAL;
+  if (ctx->cfg.islands < 2) return fail(ctx, PA_EINVAL, "context created without islands");
+  if (!pop_dev || !labels_dev) return fail(ctx, PA_EINVAL, "null buffer");
+  if (generation < 0) return fail(ctx, PA_EINVAL, "generation must be >= 0");
+  PA_TRY(ctx, pa::launch_island_kmeans(ctx, pop_dev, generation, labels_dev, ctx->stream),
+         "island K-means kernel");
+  if (passes_host) {
+    PA_TRY(ctx, cudaMemcpyAsync(passes_host, ctx->isl_passes, sizeof(int32_t),
+                                cudaMemcpyDeviceToHost, ctx->stream),
+           "copy passes");
+    PA_TRY(ctx, cudaStreamSynchronize(ctx->stream), "sync");
+  }
+  return PA_OK;
+}
+
+pa_status pa_island_step(pa_ctx* ctx, const uint8_t* pop_dev, const void* fit_dev,
+                         const int32_t* labels_dev, int32_t generation, uint8_t* next_dev) {
+  if (!ctx) return PA_EINVAL;
+  if (ctx->cfg.islands < 2) return fail(ctx, PA_EINVAL, "context created without islands");
+  if (!pop_dev || !fit_dev || !labels_dev || !next_dev) return fail(ctx, PA_EINVAL, "null buffer");
+  if (generation < 0) return fail(ctx, PA_EINVAL, "generation must be >= 0");
+  const size_t bytes = (size_t)ctx->cfg.N * ctx->cfg.L * ctx->cfg.K;
+  const uint8_t* a0 = pop_dev;
+  const uint8_t* b0 = next_dev;
+  if (a0 < b0 + bytes && b0 < a0 + bytes) return fail(ctx, PA_EINVAL, "buffers overlap");
+  // the caller's labels get member lists of their own: the resident
+  // population's islands stay as they are
+  PA_TRY(ctx, pa::launch_island_lists(ctx, labels_dev, ctx->isl_usr, ctx->stream),
+         "island lists kernel");
+  PA_TRY(ctx, pa::launch_island_step(ctx, pop_dev, fit_dev, labels_dev, ctx->isl_usr, generation,
+                                     next_dev, ctx->stream),
+         "island step kernel");
+  return PA_OK;
+}
+
+pa_status pa_get_islands(pa_ctx* ctx, int32_t* labels_host) {
+  if (!ctx || !labels_host) return PA_EINVAL;
+  if (ctx->cfg.islands < 2) return fail(ctx, PA_EINVAL, "context created without islands");
+  PA_TRY(ctx, cudaMemcpyAsync(labels_host, ctx->isl_label, sizeof(int32_t) * ctx->cfg.N,
+                              cudaMemcpyDeviceToHost, ctx->stream),
+         "copy islands");
+  PA_TRY(ctx, cudaStreamSynchronize(ctx->stream), "sync");
   return PA_OK;
 }
 

@@ -166,12 +166,19 @@ extern "C" {
 pa_status pa_batch_create(int32_t n, const pa_config* cfgs, const double* const* betas,
                           const int32_t* const* user_xy_mm, const int32_t* const* bs_xy_mm,
                           void* stream, pa_batch** out) {
+  pa::set_thread_error("");
   if (!out) return PA_EINVAL;
   *out = nullptr;
   if (n < 1 || !cfgs || !betas) {
     pa::set_thread_error("n >= 1, cfgs and betas are required");
     return PA_EINVAL;
   }
+  for (int i = 0; i < n; ++i)
+    if (cfgs[i].islands >= 2) {
+      pa::set_thread_error("instance " + std::to_string(i) +
+                           ": batches run one population per instance (islands <= 1)");
+      return PA_EUNSUPPORTED;
+    }
   pa_batch* b = new (std::nothrow) pa_batch();
   if (!b) return PA_ENOMEM;
   b->n = n;

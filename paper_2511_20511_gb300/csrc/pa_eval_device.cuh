@@ -160,13 +160,16 @@ __device__ __forceinline__ float lg2_ftz(float x) {
   return r;
 }
 
-// SE of one user from its pilot's sums at its own BS j (Eq. 4-5, or the
-// finite-M reading of Eq. 3): s2 = sum_{l != j} of squared gains, s1 = sum
-// over l != j of gains, b = own gain, bn = B_j + s2/rho (scaled).  Every FP32
-// kernel takes this exact sequence of roundings.
+// Objective value of one user from its pilot's sums at its own BS j (Eq.
+// 4-5, or the finite-M reading of Eq. 3): s2 = sum_{l != j} of squared gains,
+// s1 = sum over l != j of gains, b = own gain, bn = B_j + s2/rho (scaled).
+// minobj false: SE = log2(1 + SINR) (Eq. 5, summed by the sum-SE objective
+// of Eq. 7); true: the SINR itself (the max-min objective of Sec. 2).  Every
+// FP32 kernel takes this exact sequence of roundings (the intrinsics fix
+// where a multiply-add is fused).
 template <bool FIN>
 __device__ __forceinline__ float se_pilot_f32(float s2, float s1, float b, float bn, float M,
-                                              float pc) {
+                                              float pc, bool minobj) {
   const float b2 = b * b;
   float num, den;
   if (FIN) {
@@ -176,7 +179,16 @@ __device__ __forceinline__ float se_pilot_f32(float s2, float s1, float b, float
     num = b2;
     den = s2;
   }
-  return lg2_ftz(1.f + num * rcp_ftz(den));
+  const float r = rcp_ftz(den);
+  return minobj ? __fmul_rn(num, r) : lg2_ftz(__fmaf_rn(num, r, 1.f));
+}
+
+// Combine two users' values of one (pilot, column pair) entry: a sum for the
+// sum-SE objective (starting from 0), a minimum for the max-min objective
+// (starting from +inf, so that padding columns leave the entry unchanged).
+__device__ __forceinline__ float pair_init(bool minobj) { return minobj ? __int_as_float(0x7f800000) : 0.f; }
+__device__ __forceinline__ float pair_add(float acc, float v, bool minobj) {
+  return minobj ? fminf(acc, v) : acc + v;
 }
 
 // Threads per (member, pilot) of the batch FP32 evaluation: two for float2
@@ -195,7 +207,7 @@ struct PilotSplit {
 // summed over (pilot, pair) in one fixed order whatever JS is.
 template <int NJ, int VEC, bool FIN, int JS>
 __device__ __forceinline__ void eval_pilot_f32(const F32Smem& s, const uint8_t* invp, int stride,
-                                               int h, float* pair_se) {
+                                               int h, float* pair_se, bool minobj) {
   static_assert(NJ % (2 * JS) == 0, "NJ must split into JS shares of column pairs");
   constexpr int NP = NJ / 2 / JS;
   float2 acc2[NP];
@@ -227,14 +239,15 @@ __device__ __forceinline__ void eval_pilot_f32(const F32Smem& s, const uint8_t* 
   for (int c = 0; c < NP; ++c) {
     const float s2[2] = {acc2[c].x, acc2[c].y};
     const float s1[2] = {FIN ? acc1[c].x : 0.f, FIN ? acc1[c].y : 0.f};
-    float ps = 0.f;
+    float ps = pair_init(minobj);
 #pragma unroll
     for (int hh = 0; hh < 2; ++hh) {
       const int j = s.jbase + 2 * (c0 + c) + hh;
       if (j < L) {
         const int u = invp[j * stride];
-        ps += se_pilot_f32<FIN>(s2[hh], s1[hh], s.OWN[j * K + u], FIN ? s.BN[j] : 0.f, s.M,
-                                s.pc);
+        ps = pair_add(ps, se_pilot_f32<FIN>(s2[hh], s1[hh], s.OWN[j * K + u], FIN ? s.BN[j] : 0.f,
+                                            s.M, s.pc, minobj),
+                      minobj);
       }
     }
     pair_se[c] = ps;
@@ -265,6 +278,36 @@ __device__ __forceinline__ float member_sum_bounded(const float* part, int n, in
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
   return s;
+}
+
+// The max-min objective's counterparts of member_sum / member_sum_bounded:
+// the smallest of the member's entries (a minimum is exact in any order).
+__device__ __forceinline__ float member_min(const float* part, int n, int lane) {
+  float s = __int_as_float(0x7f800000);
+  for (int i = lane; i < n; i += 32) s = fminf(s, part[i]);
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) s = fminf(s, __shfl_xor_sync(0xffffffffu, s, off));
+  return s;
+}
+
+template <int NMAX>
+__device__ __forceinline__ float member_min_bounded(const float* part, int n, int lane) {
+  static_assert(NMAX % 32 == 0, "whole rounds of 32 entries");
+  float s = __int_as_float(0x7f800000);
+#pragma unroll
+  for (int i0 = 0; i0 < NMAX; i0 += 32)
+    if (i0 + lane < n) s = fminf(s, part[i0 + lane]);
+  for (int i = NMAX + lane; i < n; i += 32) s = fminf(s, part[i]);
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) s = fminf(s, __shfl_xor_sync(0xffffffffu, s, off));
+  return s;
+}
+
+// Member fitness under either objective.
+template <int NMAX>
+__device__ __forceinline__ float member_value_bounded(const float* part, int n, int lane,
+                                                      bool minobj) {
+  return minobj ? member_min_bounded<NMAX>(part, n, lane) : member_sum_bounded<NMAX>(part, n, lane);
 }
 
 // ----------------------------------------------------------------- FP64
@@ -303,12 +346,12 @@ __device__ __forceinline__ double log2_series(double x) {
   return __dadd_rn((double)e, __dmul_rn(ln_m, 1.44269504088896340736));
 }
 
-// SE of user k of cell j with pilot p in one member (FP64, the oracle's
+// SINR of user k of cell j with pilot p in one member (FP64, the oracle's
 // operation order): inv[l*K + q] = user of cell l holding pilot q.
-__device__ __forceinline__ double se_user_f64(const double* __restrict__ beta,
-                                              const double* __restrict__ bnc, const uint8_t* inv,
-                                              int L, int K, int j, int k, int p, int fin,
-                                              double M, double pc) {
+__device__ __forceinline__ double sinr_user_f64(const double* __restrict__ beta,
+                                                const double* __restrict__ bnc, const uint8_t* inv,
+                                                int L, int K, int j, int k, int p, int fin,
+                                                double M, double pc) {
   const double* bj = beta + (size_t)j * L * K;
   double s2 = 0.0, s1 = 0.0;
   for (int l = 0; l < L; ++l) {
@@ -326,7 +369,17 @@ __device__ __forceinline__ double se_user_f64(const double* __restrict__ beta,
   } else {
     sinr = __ddiv_rn(own2, s2);
   }
-  return log2_series(__dadd_rn(1.0, sinr));
+  return sinr;
+}
+
+// Objective value of that user: SE = log2(1 + SINR) (Eq. 5) for the sum-SE
+// objective, the SINR itself for the max-min objective.
+__device__ __forceinline__ double value_user_f64(const double* __restrict__ beta,
+                                                 const double* __restrict__ bnc,
+                                                 const uint8_t* inv, int L, int K, int j, int k,
+                                                 int p, int fin, double M, double pc, int minobj) {
+  const double sinr = sinr_user_f64(beta, bnc, inv, L, K, j, k, p, fin, M, pc);
+  return minobj ? sinr : log2_series(__dadd_rn(1.0, sinr));
 }
 
 // Eq. 6 sum of one member's per-user SE (se[j*K + k]) in the oracle's order:
@@ -339,6 +392,15 @@ __device__ __forceinline__ double sum_se_f64(const double* se, int L, int K) {
     fitness = __dadd_rn(fitness, cell);
   }
   return fitness;
+}
+
+// Member fitness from its per-user values: the Eq. 6 sum, or the smallest
+// value (max-min objective).
+__device__ __forceinline__ double member_value_f64(const double* v, int L, int K, int minobj) {
+  if (!minobj) return sum_se_f64(v, L, K);
+  double m = v[0];
+  for (int i = 1; i < L * K; ++i) m = fmin(m, v[i]);
+  return m;
 }
 
 }  // namespace pa

@@ -48,6 +48,7 @@ struct F32Args {
   int L, K, RS, NT, NTK;
   int64_t tab_floats;  // padded to a multiple of 4
   float M, pc;
+  int obj;             // PA_OBJ_MIN_SINR: smallest SINR instead of the SE sum
 };
 
 template <int NJ, int VEC, bool FIN>
@@ -90,10 +91,14 @@ __global__ void __launch_bounds__(512) k_eval_f32(const F32Args a) {
     const int nvalid = (int)((a.n - n0) < NT ? (a.n - n0) : NT);
     decode_members(a.pop + n0 * LK, LK, nvalid, NT, L, K, INV);
     __syncthreads();
-    if (active) eval_pilot_f32<NJ, VEC, FIN, JS>(sm, invp, NTK, h, PART + q * (NJ / 2) + h * (NJ / 2 / JS));
+    if (active)
+      eval_pilot_f32<NJ, VEC, FIN, JS>(sm, invp, NTK, h, PART + q * (NJ / 2) + h * (NJ / 2 / JS),
+                                       a.obj);
     __syncthreads();
     for (int c = tid >> 5; c < nvalid; c += blockDim.x >> 5) {
-      const float f = member_sum(PART + c * K * (NJ / 2), K * (NJ / 2), lane);
+      const float* part = PART + c * K * (NJ / 2);
+      const float f = a.obj ? member_min(part, K * (NJ / 2), lane)
+                            : member_sum(part, K * (NJ / 2), lane);
       if (lane == 0) a.fit[n0 + c] = f;
     }
   }
@@ -129,6 +134,7 @@ struct PilotArgs {
   int xbytes;     // shared bytes of one chromosome buffer
   int stall;      // testing: announce the bulk copies but never issue them
   float M, pc;
+  int obj;        // PA_OBJ_MIN_SINR: smallest SINR instead of the SE sum
 };
 
 template <int NJ, bool FIN>
@@ -268,13 +274,17 @@ __global__ void __launch_bounds__(kPilotThreads, 4) k_eval_f32_pilot(const Pilot
         if ((q & 1) == 0) uw = iw[q >> 1];  // users of cells 2q .. 2q+3
         const float s2[2] = {acc2[q].x, acc2[q].y};
         const float s1[2] = {FIN ? acc1[q].x : 0.f, FIN ? acc1[q].y : 0.f};
-        float pse = 0.f;
+        const bool mo = a.obj != 0;
+        float pse = pair_init(mo);
 #pragma unroll
         for (int hh = 0; hh < 2; ++hh) {
           const int j = 2 * q + hh;
           if (j < L)
-            pse += se_pilot_f32<FIN>(s2[hh], s1[hh], OWN[j * K + ((uw >> (8 * (j & 3))) & 0xff)],
-                                     FIN ? BN[j] : 0.f, a.M, a.pc);
+            pse = pair_add(pse,
+                           se_pilot_f32<FIN>(s2[hh], s1[hh],
+                                             OWN[j * K + ((uw >> (8 * (j & 3))) & 0xff)],
+                                             FIN ? BN[j] : 0.f, a.M, a.pc, mo),
+                           mo);
         }
         ps[q] = pse;
       }
@@ -285,7 +295,8 @@ __global__ void __launch_bounds__(kPilotThreads, 4) k_eval_f32_pilot(const Pilot
     __syncthreads();
     float* fit = a.fit + n0;
     for (int c = warp; c < nvalid; c += kPilotThreads / 32) {
-      const float f = member_sum_bounded<16 * NPAIR>(PART + c * K * NPAIR, K * NPAIR, lane);
+      const float f =
+          member_value_bounded<16 * NPAIR>(PART + c * K * NPAIR, K * NPAIR, lane, a.obj != 0);
       if (lane == 0) fit[c] = f;
     }
   }
@@ -301,6 +312,7 @@ struct F64Args {
   int L, K;
   int fin;
   double M, pc;
+  int obj;  // PA_OBJ_MIN_SINR: smallest SINR instead of the SE sum
 };
 
 __global__ void __launch_bounds__(256) k_eval_f64(const F64Args a) {
@@ -323,10 +335,10 @@ __global__ void __launch_bounds__(256) k_eval_f64(const F64Args a) {
     __syncthreads();
     for (int r = threadIdx.x; r < LK; r += blockDim.x) {
       const int j = r / K, k = r - j * K;
-      SE[r] = se_user_f64(a.beta, a.bnc, INV, L, K, j, k, X[r], a.fin, a.M, a.pc);
+      SE[r] = value_user_f64(a.beta, a.bnc, INV, L, K, j, k, X[r], a.fin, a.M, a.pc, a.obj);
     }
     __syncthreads();
-    if (threadIdx.x == 0) a.fit[n] = sum_se_f64(SE, L, K);
+    if (threadIdx.x == 0) a.fit[n] = member_value_f64(SE, L, K, a.obj);
   }
 }
 
@@ -538,6 +550,7 @@ cudaError_t launch_eval_f32(pa_ctx* ctx, const uint8_t* pop, int64_t n, float* f
     ctx->test_stall = 0;
     a.M = t.M;
     a.pc = t.pc;
+    a.obj = ctx->cfg.objective;
     return fin ? pick_pilot<true>(t.NJ, a, s, ctx->num_sms, st)
                : pick_pilot<false>(t.NJ, a, s, ctx->num_sms, st);
   }
@@ -557,6 +570,7 @@ cudaError_t launch_eval_f32(pa_ctx* ctx, const uint8_t* pop, int64_t n, float* f
   a.tab_floats = (((int64_t)L * K * t.RS + 3) / 4) * 4;
   a.M = t.M;
   a.pc = t.pc;
+  a.obj = ctx->cfg.objective;
   if (t.vec == 2)
     return fin ? pick_nj<2, true>(t.NJ, a, s, ctx->num_sms, st)
                : pick_nj<2, false>(t.NJ, a, s, ctx->num_sms, st);
@@ -578,6 +592,7 @@ cudaError_t launch_eval_f64(const pa_ctx* ctx, const uint8_t* pop, int64_t n, do
   a.fin = ctx->cfg.mode == PA_SINR_FINITE_M;
   a.M = ctx->cfg.M;
   a.pc = ctx->pc;
+  a.obj = ctx->cfg.objective;
   const int LK = a.L * a.K;
   const size_t smem = (size_t)LK * 8 + 2 * (size_t)LK;
   const int threads = LK >= 256 ? 256 : ((LK + 31) / 32) * 32;

@@ -18,7 +18,11 @@ constexpr int kMaxNJ = 48;           // widest per-thread BS vector of the FP32 
 constexpr int kSmemBudget = 227 * 1024;
 
 // Stream tags of the counter-based generator (counter word 3).
-enum : uint32_t { kTagSeed = 1, kTagKmeans = 2, kTagGa = 3 };
+enum : uint32_t { kTagSeed = 1, kTagKmeans = 2, kTagGa = 3, kTagIsland = 4 };
+
+// Islands of the PK-means GA: at most this many clusters and members.
+constexpr int kMaxIslands = 64;
+constexpr int kMaxIslandN = 4096;
 
 // Prepared FP32 tables of one instance (device pointers, owned by ctx).
 struct F32Tables {
@@ -41,6 +45,13 @@ struct F32Tables {
   float* partial = nullptr;  // scratch: per-(member, tile) fitness partials
   int64_t partial_cap = 0;   // members it can hold
   int* err_flag = nullptr;   // set by a kernel whose bounded wait gave up
+};
+
+// Members of a population grouped by island (device arrays).
+struct IslandLists {
+  int32_t* off = nullptr;   // [C+1] first position of each island in list
+  int32_t* list = nullptr;  // [N] members grouped by island, ascending within
+  int32_t* pos = nullptr;   // [N] position of each member within its island
 };
 
 }  // namespace pa
@@ -70,6 +81,13 @@ struct pa_ctx {
   int seed_C = -1;             // cluster size of the seeding kernel (-1: not chosen)
   int wait_check = 0;          // an FP32 evaluation ran since t32.err_flag was last read
   int test_stall = 0;          // PA_FLAG_TEST_STALL_COPIES still pending (one-shot)
+  // islands of the PK-means GA (cfg.islands >= 2)
+  int32_t* isl_label = nullptr;  // [N] island of each member of the resident population
+  pa::IslandLists isl_res;       // member lists of isl_label
+  pa::IslandLists isl_usr;       // member lists of a pa_island_step call's labels
+  int32_t* isl_cnt = nullptr;    // K-means counts in global memory when they exceed shared memory
+  int32_t* isl_passes = nullptr; // [1] assignment passes of the last K-means
+  int isl_valid = 0;             // isl_label belongs to the resident population
   // scratch
   int64_t* scratch_i64 = nullptr;  // small device scratch (flags, argbest)
   uint8_t* best_row = nullptr;     // [L*K], then the best fitness (double) 8-byte aligned
@@ -131,6 +149,15 @@ int seed_batch_cluster(int n);
 cudaError_t launch_seed_batch(const void* d_args, int n, size_t smem, int C, cudaStream_t st);
 cudaError_t launch_validate(const pa_ctx* ctx, const uint8_t* pop, int64_t n, int64_t* first_bad,
                             cudaStream_t st);
+// pa_island.cu: PK-means GA (Alg. 2)
+bool island_cnt_in_smem(int N, int L, int K, int C);
+cudaError_t launch_island_kmeans(const pa_ctx* ctx, const uint8_t* pop, int gen, int32_t* labels,
+                                 cudaStream_t st);
+cudaError_t launch_island_lists(const pa_ctx* ctx, const int32_t* labels, const IslandLists& il,
+                                cudaStream_t st);
+cudaError_t launch_island_step(const pa_ctx* ctx, const uint8_t* pop, const void* fit,
+                               const int32_t* labels, const IslandLists& il, int32_t gen,
+                               uint8_t* next, cudaStream_t st);
 
 // Raise a kernel's dynamic shared-memory cap to what the device allows
 // beside the kernel's static shared memory (call once per kernel and device).

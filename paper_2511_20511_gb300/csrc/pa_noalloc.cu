@@ -5,9 +5,8 @@
 // for the instance (gains, prepared tables, population buffers).  Some
 // callers cannot do that: a real-time scheduler loop that must never hit
 // the implicit device synchronisation and unbounded latency of cudaMalloc,
-// a host framework that owns all device memory through its own pool, or
-// code that runs while a stream is being captured (allocation is not
-// allowed there).  pa_eval_population_noalloc gives them the same result
+// or a host framework that owns all device memory through its own pool.
+// pa_eval_population_noalloc gives them the same result
 // without any allocation: the instance data and the prepared tables live in
 // one file-scope device array, g_noalloc_scratch, of kNoallocBytes bytes
 // that every GPU holds from the moment this library is loaded until the
@@ -61,6 +60,7 @@ extern "C" pa_status pa_eval_population_noalloc(const pa_config* cfg, const doub
                                                 void* stream) {
   using namespace pa;
   std::string why;
+  set_thread_error("");  // a failure of an earlier call must not outlive this one
   if (!cfg || !beta) {
     set_thread_error("cfg and beta are required");
     return PA_EINVAL;

@@ -12,12 +12,22 @@
 //      persistent batched solve launch per kernel variant (populations stay
 //      resident between ticks; a slot reaching G generations also gets its
 //      final evaluation and best member);
-//   4. finished requests are copied back and returned; their slots free up.
+//   4. finished requests are copied back into a completion queue that
+//      polls drain (up to the caller's max_done per poll); their slots
+//      stay resident for the next request of the same class.
 // Requests that arrive while a tick runs join at the next tick, so work of
 // many requests overlaps on the device.  A request's result is exactly what
 // pa_solve gives for the same instance and seed alone: generations run in
 // the same order with the same draws, whatever the tick length or the mix.
+//
+// Liveness: requests are checked at submit (shape, values, a slot of its
+// shape within the budget), so every queued request can eventually be
+// admitted; when the head of the queue needs memory, idle slots (of other
+// classes first) are destroyed; an admission that fails anyway completes
+// that request with the error and the queue moves on.  No C++ exception
+// crosses the C ABI: allocation failures return PA_ENOMEM.
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <deque>
 #include <map>
@@ -30,6 +40,8 @@
 
 namespace pa {
 void set_thread_error(const std::string& msg);
+bool config_ok(const pa_config* c, std::string* why);
+void f32_geometry(int L, int K, int* NJ, int* RS, int* vec);
 }
 
 struct pa_server {
@@ -39,11 +51,12 @@ struct pa_server {
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   struct Slot {
-    pa_ctx* ctx = nullptr;
+    pa_ctx* ctx = nullptr;  // null: destroyed (entry reusable)
     int L = 0, K = 0;
+    size_t bytes = 0;       // device bytes charged to the budget
     int64_t req = -1;
     int gen = 0;
-    bool active = false, fresh = false, done = false;
+    bool active = false, fresh = false, failed = false;
     int64_t best_off = 0;  // offset in the pinned results buffer
   };
   std::vector<Slot> slots;
@@ -56,6 +69,15 @@ struct pa_server {
     std::vector<int32_t> uxy, bxy;
   };
   std::deque<Req> pending;
+  struct Done {
+    int64_t id;
+    pa_status st;
+    int L, K;
+    std::vector<uint8_t> best;
+    double fit;
+  };
+  std::deque<Done> done;   // completions not yet returned by a poll
+  int inject_failures = 0; // testing: admissions still to fail
   // per-tick device/pinned scratch
   void* d_seed_args = nullptr;
   void* h_seed_args = nullptr;
@@ -88,6 +110,33 @@ pa_status scuda(pa_server* s, cudaError_t e, const char* what) {
   if (e == cudaSuccess) return PA_OK;
   return sfail(s, e == cudaErrorMemoryAllocation ? PA_ENOMEM : PA_ECUDA,
                std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+// Configuration of a request's slot.
+pa_config slot_config(const pa_server* s, int L, int K) {
+  pa_config c = s->base;
+  c.L = L;
+  c.K = K;
+  c.tau_p = K;
+  c.kmeans_k = K;
+  return c;
+}
+
+// The batched solve kernel runs this shape for some cluster size (tables in
+// shared memory, member records within one CTA's share).
+bool shape_runs(const pa_config& c) {
+  pa_ctx t;  // geometry only: no device memory behind it
+  t.cfg = c;
+  if (c.prec == PA_FP32) {
+    if (!pa::f32_supported(c.L, c.K, nullptr)) return false;
+    pa::f32_geometry(c.L, c.K, &t.t32.NJ, &t.t32.RS, &t.t32.vec);
+  }
+  unsigned char args[512];
+  if (pa::solve_args_bytes() > sizeof args) return false;
+  for (int C : {16, 8, 4, 2, 1})
+    if (pa::solve_fill_args(&t, C, 0, 1, nullptr, nullptr, nullptr, nullptr, nullptr, args) != 0)
+      return true;
+  return false;
 }
 
 // Device bytes a context of this shape allocates (upper estimate).
@@ -143,6 +192,44 @@ pa_status side_stream(pa_server* s, int k) {
   return PA_OK;
 }
 
+// Queue a completion (a failed one: no best member, NaN fitness).
+void complete(pa_server* s, int64_t id, pa_status st, int L, int K, const uint8_t* best,
+              double fit) {
+  pa_server::Done d;
+  d.id = id;
+  d.st = st;
+  d.L = L;
+  d.K = K;
+  d.best.assign((size_t)L * K, 0);
+  if (best) std::memcpy(d.best.data(), best, (size_t)L * K);
+  d.fit = st == PA_OK ? fit : std::nan("");
+  s->done.push_back(std::move(d));
+  ++s->completed;
+}
+
+// Destroy one idle slot and give its memory back to the budget.
+void evict(pa_server* s, int i) {
+  pa_server::Slot& sl = s->slots[i];
+  pa_destroy(sl.ctx);
+  sl.ctx = nullptr;
+  s->used -= sl.bytes;
+  sl.bytes = 0;
+}
+
+// Destroy idle slots (other classes than `key` first) until `need` more
+// bytes fit the budget; true when they do.
+bool make_room(pa_server* s, size_t need, std::pair<int, int> key) {
+  for (int pass = 0; pass < 2 && s->used + need > s->budget; ++pass)
+    for (auto& kv : s->free_slots) {
+      if ((kv.first == key) != (pass == 1)) continue;
+      while (!kv.second.empty() && s->used + need > s->budget) {
+        evict(s, kv.second.back());
+        kv.second.pop_back();
+      }
+    }
+  return s->used + need <= s->budget;
+}
+
 void destroy_server(pa_server* s) {
   if (!s) return;
   for (auto x : s->side) cudaStreamDestroy(x);
@@ -167,11 +254,21 @@ extern "C" {
 
 pa_status pa_server_create(const pa_config* base, int32_t generations, int32_t tick,
                            uint64_t budget_bytes, void* stream, pa_server** out) {
+  pa::set_thread_error("");
   if (!out) return PA_EINVAL;
   *out = nullptr;
   if (!base || generations < 1 || tick < 1 || budget_bytes == 0) {
     pa::set_thread_error("base config, generations >= 1, tick >= 1 and a budget are required");
     return PA_EINVAL;
+  }
+  std::string why;
+  if (!pa::config_ok(base, &why)) {
+    pa::set_thread_error("base config: " + why);
+    return PA_EINVAL;
+  }
+  if (base->islands >= 2) {
+    pa::set_thread_error("the server runs one population per request (islands <= 1)");
+    return PA_EUNSUPPORTED;
   }
   pa_server* s = new (std::nothrow) pa_server();
   if (!s) return PA_ENOMEM;
@@ -200,12 +297,23 @@ void pa_server_destroy(pa_server* s) {
 
 const char* pa_server_last_error(const pa_server* s) { return s ? s->err.c_str() : ""; }
 
-pa_status pa_server_submit(pa_server* s, int64_t id, int32_t L, int32_t K, uint64_t seed,
-                           const double* beta, const int32_t* user_xy_mm,
-                           const int32_t* bs_xy_mm) {
-  if (!s) return PA_EINVAL;
+static pa_status submit_impl(pa_server* s, int64_t id, int32_t L, int32_t K, uint64_t seed,
+                             const double* beta, const int32_t* user_xy_mm,
+                             const int32_t* bs_xy_mm) {
   if (!beta || !user_xy_mm || !bs_xy_mm)
     return sfail(s, PA_EINVAL, "beta and positions are required");
+  const pa_config c = slot_config(s, L, K);
+  std::string why;
+  if (!pa::config_ok(&c, &why)) return sfail(s, PA_EINVAL, "request: " + why);
+  double bmax = 0.0;
+  if (!pa::instance_ok(c, beta, user_xy_mm, bs_xy_mm, &bmax))
+    return sfail(s, PA_EINVAL, "request: beta must be finite and > 0; positions within int32");
+  if (!shape_runs(c))
+    return sfail(s, PA_EUNSUPPORTED, "request shape does not fit the batched solve kernel");
+  const size_t need = slot_bytes(c);
+  if (need > s->budget)
+    return sfail(s, PA_EBUSY, "one slot of this shape needs " + std::to_string(need) +
+                                  " bytes; the budget is " + std::to_string(s->budget));
   pa_server::Req r;
   r.id = id;
   r.L = L;
@@ -218,49 +326,159 @@ pa_status pa_server_submit(pa_server* s, int64_t id, int32_t L, int32_t K, uint6
   return PA_OK;
 }
 
-pa_status pa_server_poll(pa_server* s, int32_t max_done, int64_t* done_ids, uint8_t* done_best,
-                         int64_t best_stride, double* done_fit, int32_t* n_done,
-                         int32_t* n_active, int32_t* n_pending) {
+pa_status pa_server_submit(pa_server* s, int64_t id, int32_t L, int32_t K, uint64_t seed,
+                           const double* beta, const int32_t* user_xy_mm,
+                           const int32_t* bs_xy_mm) {
+  if (!s) return PA_EINVAL;
+  try {
+    return submit_impl(s, id, L, K, seed, beta, user_xy_mm, bs_xy_mm);
+  } catch (const std::bad_alloc&) {
+    return sfail(s, PA_ENOMEM, "host memory for the request copy");
+  } catch (...) {
+    return sfail(s, PA_ENOMEM, "request copy failed");
+  }
+}
+
+static pa_status tick_impl(pa_server* s);
+
+pa_status pa_server_poll(pa_server* s, int32_t max_done, int64_t* done_ids, int32_t* done_status,
+                         uint8_t* done_best, int64_t best_stride, double* done_fit,
+                         int32_t* n_done, int32_t* n_active, int32_t* n_pending) {
   if (!s || !n_done) return PA_EINVAL;
+  if (max_done < 0 || (done_best && best_stride < 0)) return sfail(s, PA_EINVAL, "bad outputs");
   *n_done = 0;
+  pa_status st;
+  try {
+    st = tick_impl(s);
+  } catch (const std::bad_alloc&) {
+    st = sfail(s, PA_ENOMEM, "host memory during a tick");
+  } catch (...) {
+    st = sfail(s, PA_ENOMEM, "tick failed");
+  }
+  int nd = 0;
+  while (nd < max_done && !s->done.empty()) {
+    const pa_server::Done& d = s->done.front();
+    if (done_ids) done_ids[nd] = d.id;
+    if (done_status) done_status[nd] = d.st;
+    if (done_best) std::memcpy(done_best + (int64_t)nd * best_stride, d.best.data(), d.best.size());
+    if (done_fit) done_fit[nd] = d.fit;
+    s->done.pop_front();
+    ++nd;
+  }
+  *n_done = nd;
+  if (n_active) {
+    int a = 0;
+    for (auto& sl : s->slots) a += sl.active ? 1 : 0;
+    *n_active = a;
+  }
+  if (n_pending) *n_pending = (int32_t)s->pending.size();
+  return st;
+}
+
+pa_status pa_server_cancel(pa_server* s, int64_t id) {
+  if (!s) return PA_EINVAL;
+  for (auto it = s->pending.begin(); it != s->pending.end(); ++it)
+    if (it->id == id) {
+      s->pending.erase(it);
+      return PA_OK;
+    }
+  for (size_t i = 0; i < s->slots.size(); ++i) {
+    pa_server::Slot& sl = s->slots[i];
+    if (sl.ctx && sl.active && sl.req == id) {
+      sl.active = false;
+      sl.fresh = false;
+      sl.req = -1;
+      s->free_slots[std::make_pair(sl.L, sl.K)].push_back((int)i);
+      return PA_OK;
+    }
+  }
+  for (auto it = s->done.begin(); it != s->done.end(); ++it)
+    if (it->id == id) {
+      s->done.erase(it);
+      return PA_OK;
+    }
+  return sfail(s, PA_EINVAL, "no queued, running or unreturned request has this id");
+}
+
+pa_status pa_server_inject_admission_failures(pa_server* s, int32_t count) {
+  if (!s || count < 0) return PA_EINVAL;
+  s->inject_failures = count;
+  return PA_OK;
+}
+
+}  // extern "C"
+
+static pa_status tick_impl(pa_server* s) {
   pa_status st = PA_OK;
-  // ---- 1. admission
+  // ---- 1. admission, in arrival order
   std::vector<int> fresh;
   while (!s->pending.empty()) {
     pa_server::Req& r = s->pending.front();
-    auto key = std::make_pair(r.L, r.K);
+    const auto key = std::make_pair(r.L, r.K);
     auto& fl = s->free_slots[key];
+    const pa_config c = slot_config(s, r.L, r.K);
     int slot = -1;
+    bool created = false;
     if (!fl.empty()) {
       slot = fl.back();
       fl.pop_back();
     } else {
-      pa_config c = s->base;
-      c.L = r.L;
-      c.K = r.K;
-      c.tau_p = r.K;
-      c.kmeans_k = r.K;
       const size_t need = slot_bytes(c);
-      if (s->used + need > s->budget) break;  // wait for memory to free up
+      if (!make_room(s, need, key)) break;  // wait for running slots to finish
       pa_ctx* ctx = nullptr;
-      st = pa_create(&c, r.beta.data(), r.uxy.data(), r.bxy.data(), s->stream, &ctx);
-      if (st != PA_OK) return sfail(s, st, std::string("slot: ") + pa_last_error(nullptr));
-      pa_server::Slot sl;
-      sl.ctx = ctx;
-      sl.L = r.L;
-      sl.K = r.K;
-      s->slots.push_back(sl);
-      slot = (int)s->slots.size() - 1;
+      pa_status cs;
+      std::string why;
+      if (s->inject_failures > 0) {
+        --s->inject_failures;
+        cs = PA_ECUDA;
+        why = "injected admission failure";
+      } else {
+        cs = pa_create(&c, r.beta.data(), r.uxy.data(), r.bxy.data(), s->stream, &ctx);
+        if (cs != PA_OK) why = pa_last_error(nullptr);
+      }
+      if (cs != PA_OK) {  // this request fails; the queue moves on
+        s->err = "slot of request " + std::to_string(r.id) + ": " + why;
+        complete(s, r.id, cs, r.L, r.K, nullptr, 0.0);
+        s->pending.pop_front();
+        continue;
+      }
+      for (size_t i = 0; i < s->slots.size() && slot < 0; ++i)
+        if (!s->slots[i].ctx) slot = (int)i;
+      if (slot < 0) {
+        s->slots.emplace_back();
+        slot = (int)s->slots.size() - 1;
+      }
+      pa_server::Slot& ns = s->slots[slot];
+      ns = pa_server::Slot();
+      ns.ctx = ctx;
+      ns.L = r.L;
+      ns.K = r.K;
+      ns.bytes = need;
       s->used += need;
+      created = true;
     }
     pa_server::Slot& sl = s->slots[slot];
-    sl.ctx->cfg.seed = r.seed;
-    st = pa_load_instance(sl.ctx, r.beta.data(), r.uxy.data(), r.bxy.data());
-    if (st != PA_OK) return sfail(s, st, pa_last_error(sl.ctx));
+    pa_status ls;
+    if (!created && s->inject_failures > 0) {
+      --s->inject_failures;
+      ls = PA_ECUDA;
+      s->err = "injected admission failure";
+    } else {
+      sl.ctx->cfg.seed = r.seed;
+      ls = pa_load_instance(sl.ctx, r.beta.data(), r.uxy.data(), r.bxy.data());
+      if (ls != PA_OK) s->err = pa_last_error(sl.ctx);
+    }
+    if (ls != PA_OK) {  // the slot stays usable for later requests
+      fl.push_back(slot);
+      complete(s, r.id, ls, r.L, r.K, nullptr, 0.0);
+      s->pending.pop_front();
+      continue;
+    }
     sl.req = r.id;
     sl.gen = 0;
     sl.active = true;
     sl.fresh = true;
+    sl.failed = false;
     sl.ctx->cur = 0;
     fresh.push_back(slot);
     s->pending.pop_front();
@@ -290,7 +508,7 @@ pa_status pa_server_poll(pa_server* s, int32_t max_done, int64_t* done_ids, uint
   int n_act = 0;
   for (size_t i = 0; i < s->slots.size(); ++i) {
     const auto& sl = s->slots[i];
-    if (!sl.active) continue;
+    if (!sl.active || !sl.ctx) continue;
     ++n_act;
     const pa_ctx* c = sl.ctx;
     groups[std::make_tuple(c->t32.NJ, c->t32.vec, c->cfg.prec)].push_back((int)i);
@@ -320,13 +538,9 @@ pa_status pa_server_poll(pa_server* s, int32_t max_done, int64_t* done_ids, uint
       }
   st = grow<uint8_t>(s, nullptr, &s->h_best, &s->best_cap, std::max<int64_t>(1, best_total), true);
   if (st != PA_OK) return st;
-  {
-    size_t fcap_before = s->fit_cap;
-    st = grow<double>(s, &s->d_bestfit, &s->h_bestfit, &s->fit_cap,
-                      sizeof(double) * std::max<size_t>(1, finishing.size()), true);
-    (void)fcap_before;
-    if (st != PA_OK) return st;
-  }
+  st = grow<double>(s, &s->d_bestfit, &s->h_bestfit, &s->fit_cap,
+                    sizeof(double) * std::max<size_t>(1, finishing.size()), true);
+  if (st != PA_OK) return st;
   std::map<int, int> fin_index;
   for (size_t k = 0; k < finishing.size(); ++k) fin_index[finishing[k]] = (int)k;
   if (!groups.empty()) {
@@ -367,7 +581,10 @@ pa_status pa_server_poll(pa_server* s, int32_t max_done, int64_t* done_ids, uint
       if (ok && pa::solve_batch_max_clusters(proto, C, smem) < 1) ok = false;
       if (ok) break;
     }
-    if (!ok) return sfail(s, PA_EUNSUPPORTED, "request shape does not fit the solve kernel");
+    if (!ok) {  // cannot happen for shapes checked at submit; fail these requests only
+      for (int i : mem) s->slots[i].failed = true;
+      continue;
+    }
     const int clusters =
         std::min<int>((int)mem.size(), pa::solve_batch_max_clusters(proto, C, smem));
     unsigned char* dargs = static_cast<unsigned char*>(s->d_solve_args) + a_off;
@@ -395,6 +612,7 @@ pa_status pa_server_poll(pa_server* s, int32_t max_done, int64_t* done_ids, uint
   // ---- 4. collect finished requests
   for (int i : finishing) {
     pa_server::Slot& sl = s->slots[i];
+    if (sl.failed) continue;
     st = scuda(s, cudaMemcpyAsync(s->h_best + sl.best_off, sl.ctx->best_row,
                                   (size_t)sl.L * sl.K, cudaMemcpyDeviceToHost, s->stream),
                "copy best");
@@ -411,42 +629,41 @@ pa_status pa_server_poll(pa_server* s, int32_t max_done, int64_t* done_ids, uint
   for (auto& kv : groups)
     for (int i : kv.second) {
       pa_server::Slot& sl = s->slots[i];
+      if (sl.failed) {  // released without a result
+        complete(s, sl.req, PA_EUNSUPPORTED, sl.L, sl.K, nullptr, 0.0);
+        sl.active = false;
+        sl.failed = false;
+        sl.req = -1;
+        s->free_slots[std::make_pair(sl.L, sl.K)].push_back(i);
+        continue;
+      }
       const int g_now = std::min(s->tick, s->G - sl.gen);
       sl.gen += g_now;
       sl.ctx->cur ^= 1;
       sl.ctx->generation = sl.gen;
     }
-  int nd = 0;
   for (size_t k = 0; k < finishing.size(); ++k) {
     pa_server::Slot& sl = s->slots[finishing[k]];
-    if (nd < max_done) {
-      if (done_ids) done_ids[nd] = sl.req;
-      if (done_best)
-        std::memcpy(done_best + (int64_t)nd * best_stride, s->h_best + sl.best_off,
-                    (size_t)sl.L * sl.K);
-      if (done_fit) done_fit[nd] = s->h_bestfit[k];
-      ++nd;
-    }
+    if (!sl.active) continue;  // failed above
+    complete(s, sl.req, PA_OK, sl.L, sl.K, s->h_best + sl.best_off, s->h_bestfit[k]);
     sl.active = false;
     sl.req = -1;
     s->free_slots[std::make_pair(sl.L, sl.K)].push_back(finishing[k]);
-    ++s->completed;
   }
-  *n_done = nd;
-  if (n_active) {
-    int a = 0;
-    for (auto& sl : s->slots) a += sl.active ? 1 : 0;
-    *n_active = a;
-  }
-  if (n_pending) *n_pending = (int32_t)s->pending.size();
   return PA_OK;
 }
+
+extern "C" {
 
 pa_status pa_server_stats(const pa_server* s, uint64_t* used_bytes, int32_t* n_slots,
                           int64_t* completed) {
   if (!s) return PA_EINVAL;
   if (used_bytes) *used_bytes = s->used;
-  if (n_slots) *n_slots = (int32_t)s->slots.size();
+  if (n_slots) {
+    int n = 0;
+    for (auto& sl : s->slots) n += sl.ctx ? 1 : 0;
+    *n_slots = n;
+  }
   if (completed) *completed = s->completed;
   return PA_OK;
 }

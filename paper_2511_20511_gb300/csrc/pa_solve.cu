@@ -154,6 +154,7 @@ cudaError_t launch_solve(pa_ctx* ctx, const uint8_t* pop_in, uint8_t* pop_out, i
     a.M64 = c.M;
     a.pc64 = ctx->pc;
     a.fin = c.mode == PA_SINR_FINITE_M;
+    a.obj = c.objective;
     const bool fin = a.fin;
     const bool chk = ctx->solve_C < 0;
     cudaError_t e;

@@ -178,6 +178,7 @@ size_t solve_fill_args(const pa_ctx* ctx, int C, int gen0, int G, const uint8_t*
   a.M64 = c.M;
   a.pc64 = ctx->pc;
   a.fin = c.mode == PA_SINR_FINITE_M;
+  a.obj = c.objective;
   std::memcpy(args_out, &a, sizeof a);
   return s.smem;
 }

@@ -45,6 +45,7 @@ struct SolveArgs {
   const double* bnc;
   double M64, pc64;
   int fin;
+  int obj;  // PA_OBJ_MIN_SINR: smallest SINR instead of the SE sum
 };
 
 template <typename FT>
@@ -339,7 +340,7 @@ __device__ __forceinline__ void solve_body(const SolveArgs& a, unsigned char* sm
         if (q < nv * K) {
           const int c = q / K, pp = q - c * K;
           eval_pilot_f32<NJ, VEC, FIN, JS>(sm, popc + (c0 + c) * MS + XO + pp, K, h,
-                                           PART + q * NPR + h * (NPR / JS));
+                                           PART + q * NPR + h * (NPR / JS), a.obj != 0);
         } else if (c0 == 0 && one_chunk && g < a.G && eval_threads + 32 <= (int)blockDim.x &&
                    tid >= ((eval_threads + 31) & ~31)) {
           const int t0 = (eval_threads + 31) & ~31;
@@ -349,7 +350,8 @@ __device__ __forceinline__ void solve_body(const SolveArgs& a, unsigned char* sm
         if (c0 == 0 && one_chunk && eval_threads + 32 <= (int)blockDim.x) drawn = true;
         __syncthreads();
         for (int c = warp; c < nv; c += nwarps) {
-          const float f = member_sum_bounded<16 * NPR>(PART + c * K * NPR, K * NPR, lane);
+          const float f =
+              member_value_bounded<16 * NPR>(PART + c * K * NPR, K * NPR, lane, a.obj != 0);
           const int n = base_n + c0 + c;
           if (lane < C) cluster.map_shared_rank(fit, lane)[n] = (FT)f;
         }
@@ -359,11 +361,12 @@ __device__ __forceinline__ void solve_body(const SolveArgs& a, unsigned char* sm
           const unsigned char* rec = popc + (c0 + c) * MS;
           int qq = rec[u];
           qq = qq < K ? qq : K - 1;
-          SE[i] = se_user_f64(a.beta, a.bnc, rec + XO, L, K, j, k, qq, a.fin, a.M64, a.pc64);
+          SE[i] = value_user_f64(a.beta, a.bnc, rec + XO, L, K, j, k, qq, a.fin, a.M64, a.pc64,
+                                 a.obj);
         }
         __syncthreads();
         if (tid < nv) {
-          const double s = sum_se_f64(SE + tid * LK, L, K);
+          const double s = member_value_f64(SE + tid * LK, L, K, a.obj);
           const int n = base_n + c0 + tid;
           for (int r = 0; r < C; ++r) cluster.map_shared_rank(fit, r)[n] = (FT)s;
         }

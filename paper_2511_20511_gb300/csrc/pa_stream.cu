@@ -31,6 +31,7 @@ struct StreamArgs {
   int L, K, RSt, ntile, NTM;
   int64_t tile_floats;
   float M, pc;
+  int obj;  // PA_OBJ_MIN_SINR: smallest SINR instead of the SE sum
 };
 
 constexpr int kStreamThreads = 512;
@@ -92,24 +93,27 @@ __global__ void __launch_bounds__(kStreamThreads) k_eval_f32_stream(const Stream
     __syncthreads();
     if (tid < NTK) {
       const int c = tid / K, p = tid - c * K;
-      eval_pilot_f32<JT, VEC, FIN, 1>(sm, INV + c * KP + p, NTM * KP, 0, PART + tid * NPR);
+      eval_pilot_f32<JT, VEC, FIN, 1>(sm, INV + c * KP + p, NTM * KP, 0, PART + tid * NPR,
+                                      a.obj != 0);
     }
     __syncthreads();
     for (int c = warp; c < nvalid; c += blockDim.x >> 5) {
-      const float f = member_sum_bounded<32 * NPR>(PART + c * K * NPR, K * NPR, lane);
+      const float f =
+          member_value_bounded<32 * NPR>(PART + c * K * NPR, K * NPR, lane, a.obj != 0);
       if (lane == 0) a.partial[(n0 + c) * a.ntile + t] = f;
     }
     __syncthreads();
   }
 }
 
-// fitness[n] = sum over tiles of partial[n][t], in tile order.
+// fitness[n] = sum over tiles of partial[n][t], in tile order (the smallest
+// partial for the max-min objective).
 __global__ void k_stream_reduce(const float* __restrict__ partial, int ntile, int64_t n,
-                                float* __restrict__ fit) {
+                                float* __restrict__ fit, int minobj) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
-    float s = 0.f;
-    for (int t = 0; t < ntile; ++t) s += partial[i * ntile + t];
+    float s = minobj ? __int_as_float(0x7f800000) : 0.f;
+    for (int t = 0; t < ntile; ++t) s = minobj ? fminf(s, partial[i * ntile + t]) : s + partial[i * ntile + t];
     fit[i] = s;
   }
 }
@@ -190,6 +194,7 @@ cudaError_t launch_eval_f32_stream(pa_ctx* ctx, const uint8_t* pop, int64_t n, f
   a.tile_floats = t.tile_floats;
   a.M = t.M;
   a.pc = t.pc;
+  a.obj = ctx->cfg.objective;
   const size_t smem = stream_smem(L, K, t.JT, t.RSt, a.NTM);
   // one block per SM (the tile fills shared memory), spread over the tiles
   const int64_t mtiles = (n + a.NTM - 1) / a.NTM;
@@ -214,7 +219,7 @@ cudaError_t launch_eval_f32_stream(pa_ctx* ctx, const uint8_t* pop, int64_t n, f
   if (e != cudaSuccess) return e;
   const int64_t rb = std::min<int64_t>((n + 255) / 256, (int64_t)ctx->num_sms * 8);
   (void)cudaGetLastError();
-  k_stream_reduce<<<(unsigned)rb, 256, 0, st>>>(t.partial, t.ntile, n, fit);
+  k_stream_reduce<<<(unsigned)rb, 256, 0, st>>>(t.partial, t.ntile, n, fit, a.obj);
   count_launch();
   return cudaGetLastError();
 }

@@ -75,14 +75,14 @@ def instance(L, K, seed=0, R=500.0, alpha=3.8, sigma_db=8.0, d_min=35.0, dtype=n
         while got < K:
             cand = rng.uniform(low=[-R, -SQRT3 / 2 * R], high=[R, SQRT3 / 2 * R], size=(4 * K, 2))
             ok = _in_hex(cand[:, 0], cand[:, 1], R) & (np.hypot(cand[:, 0], cand[:, 1]) >= d_min)
-            for c in cand[ok]:
-                if got == K:
-                    break
-                pos_mm = np.round(c * 1000.0).astype(np.int64) + bs_mm[l]
-                if math.hypot(*(pos_mm - bs_mm[l])) / 1000.0 < d_min:
-                    continue
-                users[l, got] = pos_mm
-                got += 1
+            # candidates in draw order; the quantised position must still be
+            # at least d_min from the BS; the first K - got of them are taken
+            rel = np.round(cand[ok] * 1000.0).astype(np.int64)
+            far = ~(np.hypot(rel[:, 0].astype(np.float64), rel[:, 1].astype(np.float64)) / 1000.0
+                    < d_min)
+            take = rel[far][:K - got]
+            users[l, got:got + len(take)] = take + bs_mm[l]
+            got += len(take)
     # distances from every BS j to every user (l, k), metres
     dx = users[None, :, :, 0] - bs_mm[:, None, None, 0]
     dy = users[None, :, :, 1] - bs_mm[:, None, None, 1]

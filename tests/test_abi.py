@@ -42,6 +42,8 @@ def test_config_defaults(B):
     assert c.pc_thresh == int(np.floor(0.9 * 2**32))
     assert c.pm_thresh == int(np.floor(0.05 * 2**32))
     assert c.kmeans_k == 10 and c.kmeans_max_iter == 100 and c.n_seeded == 128
+    assert c.objective == B.PA_OBJ_SUM_SE and c.islands == 0
+    assert c.recluster == 3 and c.island_iter == 100
     assert c.rho == pytest.approx(10.0 / 500.0 ** -3.8)
 
 
@@ -64,7 +66,9 @@ def _create_status(B, cfg, beta, u=None, b=None):
 @pytest.mark.parametrize("field,value", [("L", 1), ("K", 0), ("K", 65), ("N", 1), ("E", 256),
                                          ("tour", 0), ("kmeans_k", 11), ("kmeans_max_iter", 0),
                                          ("n_seeded", 300), ("flags", 2), ("prec", 7),
-                                         ("mode", 3), ("pc_thresh", 2**32 + 1)])
+                                         ("mode", 3), ("pc_thresh", 2**32 + 1), ("objective", 2),
+                                         ("islands", 65), ("islands", -1), ("island_iter", -1),
+                                         ("recluster", -2)])
 def test_create_rejects_bad_config(B, field, value):
     cfg = B.pa_config_default(19, 10)
     setattr(cfg, field, value)
@@ -128,6 +132,25 @@ def test_null_and_invalid_handles_rejected(B):
     assert lib.pa_server_create(C.byref(cfg), 10, 0, 1 << 30, None, C.byref(out)) == B.PA_EINVAL
     assert lib.pa_server_create(C.byref(cfg), 10, 1, 0, None, C.byref(out)) == B.PA_EINVAL
     assert lib.pa_server_submit(None, 0, 7, 4, 0, None, None, None) == B.PA_EINVAL
-    assert lib.pa_server_poll(None, 0, None, None, 0, None, C.byref(i32), None, None) == B.PA_EINVAL
+    assert lib.pa_server_poll(None, 0, None, None, None, 0, None, C.byref(i32), None,
+                              None) == B.PA_EINVAL
     assert lib.pa_server_stats(None, C.byref(u64), C.byref(i32), None) == B.PA_EINVAL
+    assert lib.pa_server_cancel(None, 1) == B.PA_EINVAL
+    assert lib.pa_server_inject_admission_failures(None, 1) == B.PA_EINVAL
     lib.pa_server_destroy(None)
+    # islands
+    assert lib.pa_island_cluster(None, None, 0, None, None) == B.PA_EINVAL
+    assert lib.pa_island_step(None, None, None, None, 0, None) == B.PA_EINVAL
+    assert lib.pa_get_islands(None, None) == B.PA_EINVAL
+    # a server of islands is refused before any GPU work
+    isl = B.pa_config_default(7, 4, islands=3)
+    assert lib.pa_server_create(C.byref(isl), 10, 1, 1 << 30, None,
+                                C.byref(out)) == B.PA_EUNSUPPORTED
+
+
+def test_create_rejects_bad_island_configs(B):
+    beta = np.ones((7, 7, 4))
+    for kw in (dict(N=5000, islands=5), dict(N=32, islands=33), dict(islands=4, recluster=0),
+               dict(islands=4, island_iter=0)):
+        cfg = B.pa_config_default(7, 4, **kw)
+        assert _create_status(B, cfg, beta) == B.PA_EINVAL, kw

@@ -1,6 +1,7 @@
-"""Batched solves of uneven instances: every instance's result in the batch
-equals its result solved alone (bit for bit), whatever cluster size the
-tuner picks; FP64 instances equal the CPU oracle."""
+"""Batched solves of uneven instances (7, 19 and 37 cells, 4 to 16 users,
+populations up to 128): every instance's result in the batch equals its
+result solved alone (bit for bit), whatever cluster size the tuner picks;
+FP64 instances equal the CPU oracle."""
 import numpy as np
 import pytest
 
@@ -22,12 +23,17 @@ def B():
 
 
 def _mixed(B, n, seed0=0):
+    """Uneven instances: L in {7, 19, 37}, K in {4, 8, 10, 16}, N up to 128;
+    every fourth one (from the second) is a 37-cell instance of 128 members,
+    the group that holds most of the batched workload's gathers."""
     rng = np.random.default_rng(seed0)
     out = []
     for i in range(n):
-        L = int(rng.choice([7, 19]))
+        L = int(rng.choice([7, 19, 37]))
         K = int(rng.choice([4, 8, 10, 16]))
-        N = int(rng.choice([32, 48, 64]))
+        N = int(rng.choice([32, 48, 64, 128]))
+        if i % 4 == 1:
+            L, N = 37, 128
         prec = B.PA_FP64 if i % 5 == 0 else B.PA_FP32
         mode = int(rng.integers(0, 2))
         inst = inputs.instance(L, K, seed=seed0 * 1000 + i, dtype=np.float32)

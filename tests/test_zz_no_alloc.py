@@ -2,13 +2,14 @@
 
 pa_eval_population_noalloc serves callers that cannot allocate device memory
 (a real-time scheduling loop that must not take cudaMalloc's implicit device
-synchronisation, a framework that owns all device memory, code running while
-a stream is captured).  It keeps its instance data in one static device array
-shared by every call, so this test calls it twice in a row on different
-instances and populations and checks each result against pa_create +
-pa_eval_population on the same inputs, at the tolerance of the other parity
-tests (FP32: 1e-5 relative; FP64: identical).  The file runs last so that a
-failure here leaves every other test already run.
+synchronisation, a framework that owns all device memory).  It keeps its
+instance data in one static device array shared by every call, so this test
+calls it twice in a row on different instances and populations and checks
+each result against pa_create + pa_eval_population on the same inputs, at
+the tolerance of the other parity tests (FP32: 1e-5 relative; FP64:
+identical).  The cases cover both FP32 evaluation kernels (K <= 16 and
+K > 16) and a caller stream other than the default one.  The file runs last
+so that a failure here leaves every other test already run.
 """
 import ctypes as C
 
@@ -44,27 +45,35 @@ def _regular(B, cfg, beta, pop):
         B.pa_destroy(ctx)
 
 
-def _noalloc(B, cfg, beta, pop):
+def _noalloc(B, cfg, beta, pop, stream=None):
     fit = torch.full((pop.shape[0],), -1.0, dtype=torch.float64 if cfg.prec else torch.float32,
                      device="cuda")
+    handle = None
+    if stream is not None:
+        stream.wait_stream(torch.cuda.current_stream())  # pop and fit are ready
+        handle = C.c_void_p(stream.cuda_stream)
     st = B.lib().pa_eval_population_noalloc(C.byref(cfg),
                                             np.ascontiguousarray(beta).ctypes.data_as(C.c_void_p),
                                             C.c_void_p(pop.data_ptr()), pop.shape[0],
-                                            C.c_void_p(fit.data_ptr()), None)
+                                            C.c_void_p(fit.data_ptr()), handle)
     assert st == B.PA_OK, B.lib().pa_last_error(None)
+    assert B.lib().pa_last_error(None) == b""
     torch.cuda.synchronize()
     return fit.cpu().numpy()
 
 
 @pytest.mark.parametrize("prec", [0, 1])
 def test_noalloc_matches_regular_two_calls_in_a_row(B, prec):
-    cases = [(19, 10, 1, 5000), (7, 4, 0, 777)]  # (L, K, mode, n): second call overwrites the first
+    # (L, K, mode, n): each call overwrites the array the previous one used;
+    # K = 20 takes the second FP32 kernel; the last call runs on a side stream
+    cases = [(19, 10, 1, 5000), (7, 4, 0, 777), (7, 20, 1, 1500)]
+    side = torch.cuda.Stream()
     results = []
     for L, K, mode, n in cases:
         inst = inputs.instance(L, K, seed=L + prec, dtype=np.float32)
         cfg = B.pa_config_default(L, K, prec=prec, mode=mode, M=256.0, rho=inst["rho"])
         pop = inputs.random_population_torch(n, L, K, seed=n, device="cuda")
-        got = _noalloc(B, cfg, inst["beta"], pop)
+        got = _noalloc(B, cfg, inst["beta"], pop, stream=side if K == 20 else None)
         want = _regular(B, cfg, inst["beta"], pop)
         results.append((got, want))
     for got, want in results:
