@@ -6,6 +6,7 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <vector>
 
 #include "pa_internal.cuh"
 
@@ -200,33 +201,11 @@ static pa_status validate_config(const pa_config* c, std::string* why) {
 
 static void free_ctx(pa_ctx* c) {
   if (!c) return;
-  cudaFree(c->beta64);
-  cudaFree(c->bnc64);
-  cudaFree(c->t32.tab);
-  cudaFree(c->t32.own);
-  cudaFree(c->t32.bn);
+  cudaFree(c->arena);
   cudaFree(c->t32.partial);
-  cudaFree(c->t32.err_flag);
-  cudaFree(c->user_xy);
-  cudaFree(c->bs_xy);
-  cudaFree(c->labels);
-  cudaFree(c->centroids);
-  cudaFree(c->pop[0]);
-  cudaFree(c->pop[1]);
-  cudaFree(c->fit);
-  cudaFree(c->scratch_i64);
-  cudaFree(c->best_row);
   cudaFreeHost(c->h_best);
   cudaFree(c->stage_pop);
   cudaFree(c->stage_fit);
-  cudaFree(c->isl_label);
-  for (pa::IslandLists* il : {&c->isl_res, &c->isl_usr}) {
-    cudaFree(il->off);
-    cudaFree(il->list);
-    cudaFree(il->pos);
-  }
-  cudaFree(c->isl_cnt);
-  cudaFree(c->isl_passes);
   delete c;
 }
 
@@ -276,8 +255,12 @@ pa_status pa_create(const pa_config* cfg, const double* beta, const int32_t* use
     if (!chk(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device),
              "cudaDeviceGetAttribute"))
       break;
-    if (!chk(cudaMalloc(&c->beta64, sizeof(double) * n_beta), "cudaMalloc beta")) break;
-    if (!chk(cudaMalloc(&c->bnc64, sizeof(double) * L), "cudaMalloc bnc")) break;
+    // every device buffer of the context is carved from one allocation
+    // (256-byte aligned parts): creating a context costs one cudaMalloc
+    std::vector<std::pair<void**, size_t>> parts;
+    auto want = [&](auto** p, size_t bytes) { parts.emplace_back((void**)p, bytes); };
+    want(&c->beta64, sizeof(double) * n_beta);
+    want(&c->bnc64, sizeof(double) * L);
     if (cfg->prec == PA_FP32 && !resident) {
       c->t32.streamed = 1;
       c->t32.JT = sJT;
@@ -285,53 +268,58 @@ pa_status pa_create(const pa_config* cfg, const double* beta, const int32_t* use
       c->t32.vec = svec;
       c->t32.ntile = sntile;
       c->t32.tile_floats = ((LK * sRSt + 3) / 4) * 4;
-      if (!chk(cudaMalloc(&c->t32.tab, sizeof(float) * c->t32.tile_floats * sntile), "cudaMalloc tab"))
-        break;
-      if (!chk(cudaMalloc(&c->t32.own, sizeof(float) * LK), "cudaMalloc own")) break;
-      if (!chk(cudaMalloc(&c->t32.bn, sizeof(float) * L), "cudaMalloc bn")) break;
+      want(&c->t32.tab, sizeof(float) * c->t32.tile_floats * sntile);
     } else if (cfg->prec == PA_FP32) {
       int NJ, RS, vec;
       pa::f32_geometry(L, K, &NJ, &RS, &vec);
       c->t32.NJ = NJ;
       c->t32.RS = RS;
       c->t32.vec = vec;
-      const int64_t tab_floats = ((LK * RS + 3) / 4) * 4;
-      if (!chk(cudaMalloc(&c->t32.tab, sizeof(float) * tab_floats), "cudaMalloc tab")) break;
-      if (!chk(cudaMalloc(&c->t32.own, sizeof(float) * LK), "cudaMalloc own")) break;
-      if (!chk(cudaMalloc(&c->t32.bn, sizeof(float) * L), "cudaMalloc bn")) break;
+      want(&c->t32.tab, sizeof(float) * (((LK * RS + 3) / 4) * 4));
     }
     if (cfg->prec == PA_FP32) {
-      if (!chk(cudaMalloc(&c->t32.err_flag, sizeof(int)), "cudaMalloc flag")) break;
-      if (!chk(cudaMemset(c->t32.err_flag, 0, sizeof(int)), "memset flag")) break;
+      want(&c->t32.own, sizeof(float) * LK);
+      want(&c->t32.bn, sizeof(float) * L);
+      want(&c->t32.err_flag, sizeof(int));
     }
-    if (!chk(cudaMalloc(&c->user_xy, sizeof(int32_t) * 2 * LK), "cudaMalloc user_xy")) break;
-    if (!chk(cudaMalloc(&c->bs_xy, sizeof(int32_t) * 2 * L), "cudaMalloc bs_xy")) break;
-    if (!chk(cudaMalloc(&c->labels, sizeof(int32_t) * LK), "cudaMalloc labels")) break;
-    if (!chk(cudaMalloc(&c->centroids, sizeof(double) * 2 * cfg->kmeans_k), "cudaMalloc cent"))
-      break;
-    if (!chk(cudaMalloc(&c->pop[0], (size_t)cfg->N * LK), "cudaMalloc pop0")) break;
-    if (!chk(cudaMalloc(&c->pop[1], (size_t)cfg->N * LK), "cudaMalloc pop1")) break;
-    if (!chk(cudaMalloc(&c->fit, fsz * cfg->N), "cudaMalloc fit")) break;
-    if (!chk(cudaMalloc(&c->scratch_i64, sizeof(int64_t) * 8), "cudaMalloc scratch")) break;
+    want(&c->user_xy, sizeof(int32_t) * 2 * LK);
+    want(&c->bs_xy, sizeof(int32_t) * 2 * L);
+    want(&c->labels, sizeof(int32_t) * LK);
+    want(&c->centroids, sizeof(double) * 2 * cfg->kmeans_k);
+    want(&c->pop[0], (size_t)cfg->N * LK);
+    want(&c->pop[1], (size_t)cfg->N * LK);
+    want(&c->fit, fsz * cfg->N);
+    want(&c->scratch_i64, sizeof(int64_t) * 8);
     // best row, then its fitness at the next 8-byte boundary (one copy back)
-    if (!chk(cudaMalloc(&c->best_row, best_bytes(LK)), "cudaMalloc best")) break;
-    if (!chk(cudaMallocHost(&c->h_best, best_bytes(LK)), "cudaMallocHost best")) break;
+    want(&c->best_row, best_bytes(LK));
     if (cfg->islands >= 2) {
       const size_t n4 = sizeof(int32_t) * cfg->N;
-      if (!chk(cudaMalloc(&c->isl_label, n4), "cudaMalloc islands")) break;
-      if (!chk(cudaMemset(c->isl_label, 0xFF, n4), "memset islands")) break;
-      bool ok = true;
-      for (pa::IslandLists* il : {&c->isl_res, &c->isl_usr})
-        ok = ok && chk(cudaMalloc(&il->list, n4), "cudaMalloc islands") &&
-             chk(cudaMalloc(&il->pos, n4), "cudaMalloc islands") &&
-             chk(cudaMalloc(&il->off, sizeof(int32_t) * (cfg->islands + 1)), "cudaMalloc islands");
-      if (!ok) break;
-      if (!chk(cudaMalloc(&c->isl_passes, sizeof(int32_t)), "cudaMalloc islands")) break;
-      if (!pa::island_cnt_in_smem(cfg->N, L, K, cfg->islands) &&
-          !chk(cudaMalloc(&c->isl_cnt, sizeof(int32_t) * (size_t)cfg->islands * LK * K),
-               "cudaMalloc island counts"))
-        break;
+      want(&c->isl_label, n4);
+      for (pa::IslandLists* il : {&c->isl_res, &c->isl_usr}) {
+        want(&il->list, n4);
+        want(&il->pos, n4);
+        want(&il->off, sizeof(int32_t) * (cfg->islands + 1));
+      }
+      want(&c->isl_passes, sizeof(int32_t));
+      if (!pa::island_cnt_in_smem(cfg->N, L, K, cfg->islands))
+        want(&c->isl_cnt, sizeof(int32_t) * (size_t)cfg->islands * LK * K);
     }
+    size_t total = 0;
+    for (auto& pt : parts) total = ((total + 255) & ~size_t(255)) + pt.second;
+    if (!chk(cudaMalloc(&c->arena, total), "cudaMalloc context")) break;
+    size_t off = 0;
+    for (auto& pt : parts) {
+      off = (off + 255) & ~size_t(255);
+      *pt.first = static_cast<unsigned char*>(c->arena) + off;
+      off += pt.second;
+    }
+    if (cfg->prec == PA_FP32 &&
+        !chk(cudaMemsetAsync(c->t32.err_flag, 0, sizeof(int), c->stream), "memset flag"))
+      break;
+    if (cfg->islands >= 2 &&
+        !chk(cudaMemsetAsync(c->isl_label, 0xFF, sizeof(int32_t) * cfg->N, c->stream),
+             "memset islands"))
+      break;
     st = upload_instance(c, beta, user_xy_mm, bs_xy_mm, bmax);
     if (st != PA_OK) break;
     if (!chk(cudaStreamSynchronize(c->stream), "prepare sync")) break;
@@ -573,6 +561,8 @@ pa_status pa_solve(pa_ctx* ctx, int32_t generations, uint8_t* best_host, double*
     return cuda_check(ctx, e, "solve kernel");
   }
   // the best row and its fitness come back in one copy to pinned memory
+  if ((best_host || best_fit) && !ctx->h_best)
+    PA_TRY(ctx, cudaMallocHost(&ctx->h_best, best_bytes(LK)), "cudaMallocHost best");
   if (best_host || best_fit)
     PA_TRY(ctx, cudaMemcpyAsync(ctx->h_best, ctx->best_row, best_bytes(LK),
                                 cudaMemcpyDeviceToHost, ctx->stream),

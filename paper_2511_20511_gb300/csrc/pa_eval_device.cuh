@@ -347,15 +347,16 @@ __device__ __forceinline__ double log2_series(double x) {
 }
 
 // SINR of user k of cell j with pilot p in one member (FP64, the oracle's
-// operation order): inv[l*K + q] = user of cell l holding pilot q.
+// operation order): inv[l*ls + q*ps] = user of cell l holding pilot q (ls =
+// K, ps = 1 for row-major inverse rows; ls = 1, ps = pitch for pilot-major).
 __device__ __forceinline__ double sinr_user_f64(const double* __restrict__ beta,
                                                 const double* __restrict__ bnc, const uint8_t* inv,
                                                 int L, int K, int j, int k, int p, int fin,
-                                                double M, double pc) {
+                                                double M, double pc, int ls, int ps) {
   const double* bj = beta + (size_t)j * L * K;
   double s2 = 0.0, s1 = 0.0;
   for (int l = 0; l < L; ++l) {
-    const double b = __ldg(bj + l * K + inv[l * K + p]);
+    const double b = __ldg(bj + l * K + inv[l * ls + p * ps]);
     if (fin) s1 = __dadd_rn(s1, b);
     if (l != j) s2 = __dadd_rn(s2, __dmul_rn(b, b));
   }
@@ -377,8 +378,9 @@ __device__ __forceinline__ double sinr_user_f64(const double* __restrict__ beta,
 __device__ __forceinline__ double value_user_f64(const double* __restrict__ beta,
                                                  const double* __restrict__ bnc,
                                                  const uint8_t* inv, int L, int K, int j, int k,
-                                                 int p, int fin, double M, double pc, int minobj) {
-  const double sinr = sinr_user_f64(beta, bnc, inv, L, K, j, k, p, fin, M, pc);
+                                                 int p, int fin, double M, double pc, int minobj,
+                                                 int ls, int ps) {
+  const double sinr = sinr_user_f64(beta, bnc, inv, L, K, j, k, p, fin, M, pc, ls, ps);
   return minobj ? sinr : log2_series(__dadd_rn(1.0, sinr));
 }
 

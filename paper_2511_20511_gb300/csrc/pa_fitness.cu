@@ -335,7 +335,7 @@ __global__ void __launch_bounds__(256) k_eval_f64(const F64Args a) {
     __syncthreads();
     for (int r = threadIdx.x; r < LK; r += blockDim.x) {
       const int j = r / K, k = r - j * K;
-      SE[r] = value_user_f64(a.beta, a.bnc, INV, L, K, j, k, X[r], a.fin, a.M, a.pc, a.obj);
+      SE[r] = value_user_f64(a.beta, a.bnc, INV, L, K, j, k, X[r], a.fin, a.M, a.pc, a.obj, K, 1);
     }
     __syncthreads();
     if (threadIdx.x == 0) a.fit[n] = member_value_f64(SE, L, K, a.obj);

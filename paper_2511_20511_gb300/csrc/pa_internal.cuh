@@ -88,10 +88,11 @@ struct pa_ctx {
   int32_t* isl_cnt = nullptr;    // K-means counts in global memory when they exceed shared memory
   int32_t* isl_passes = nullptr; // [1] assignment passes of the last K-means
   int isl_valid = 0;             // isl_label belongs to the resident population
+  void* arena = nullptr;  // the one device allocation the buffers below are carved from
   // scratch
   int64_t* scratch_i64 = nullptr;  // small device scratch (flags, argbest)
   uint8_t* best_row = nullptr;     // [L*K], then the best fitness (double) 8-byte aligned
-  uint8_t* h_best = nullptr;       // pinned host copy of the same bytes
+  uint8_t* h_best = nullptr;       // pinned host copy of the same bytes (first pa_solve)
   // host staging for *_host calls
   uint8_t* stage_pop = nullptr;
   void* stage_fit = nullptr;
@@ -226,7 +227,8 @@ struct DrawStream {
 };
 
 // Draws of a GA generation for nc consecutive child slots n0 .. n0+nc-1:
-// DR[c*nblk*8 + d] = draw d of slot n0+c (the same values DrawStream gives),
+// DR[c*nblk*8 + d] = draw d of slot n0+c (the same values DrawStream gives;
+// DR 16-byte aligned),
 // one Philox block per thread (threads t0, t0 + tstride, ...).  Slots below
 // E (elites) take no draws and are skipped.
 __device__ __forceinline__ void gen_child_draws_from(uint32_t* DR, int n0, int nc, int nblk,
@@ -237,12 +239,14 @@ __device__ __forceinline__ void gen_child_draws_from(uint32_t* DR, int n0, int n
     const int n = n0 + c;
     if (n < E) continue;
     const Philox4x64 r = philox4x64_10((uint64_t)b, (uint64_t)n, gen, kTagGa, seed, 0);
-    uint32_t* o = DR + (size_t)c * nblk * 8 + b * 8;
-#pragma unroll
-    for (int w = 0; w < 4; ++w) {
-      o[2 * w] = (uint32_t)(r.v[w] & 0xFFFFFFFFu);
-      o[2 * w + 1] = (uint32_t)(r.v[w] >> 32);
-    }
+    // two 16-byte stores per block (DR is 16-byte aligned): the eight words
+    // of consecutive threads are 32 bytes apart, so a quarter-warp covers all
+    // banks once instead of eight stores hitting four banks each
+    uint4* o = reinterpret_cast<uint4*>(DR + (size_t)c * nblk * 8 + b * 8);
+    o[0] = make_uint4((uint32_t)(r.v[0] & 0xFFFFFFFFu), (uint32_t)(r.v[0] >> 32),
+                      (uint32_t)(r.v[1] & 0xFFFFFFFFu), (uint32_t)(r.v[1] >> 32));
+    o[1] = make_uint4((uint32_t)(r.v[2] & 0xFFFFFFFFu), (uint32_t)(r.v[2] >> 32),
+                      (uint32_t)(r.v[3] & 0xFFFFFFFFu), (uint32_t)(r.v[3] >> 32));
   }
 }
 

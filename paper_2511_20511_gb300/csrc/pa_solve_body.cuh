@@ -211,6 +211,13 @@ __device__ __forceinline__ uint32_t ld_dsmem(uint32_t addr) {
   asm volatile("ld.shared::cluster.u32 %0, [%1];" : "=r"(v) : "r"(addr));
   return v;
 }
+__device__ __forceinline__ uint4 ld_dsmem_v4(uint32_t addr) {
+  uint4 v;
+  asm volatile("ld.shared::cluster.v4.u32 {%0, %1, %2, %3}, [%4];"
+               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+               : "r"(addr));
+  return v;
+}
 __device__ __forceinline__ uint32_t dsmem_addr(const void* local, int rank) {
   uint32_t a = (uint32_t)__cvta_generic_to_shared(local), r;
   asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
@@ -273,11 +280,13 @@ __device__ __forceinline__ void solve_body(const SolveArgs& a, unsigned char* sm
   double* SE = reinterpret_cast<double*>(p);  // FP64: NTT*LK per-user SE
   float* PART = reinterpret_cast<float*>(p);  // FP32: NTT*K*NPR per-(pilot, pair) SE
   p += F64 ? 8 * (size_t)a.NTT * LK : 4 * (size_t)((a.NTT * K * NPR + 3) & ~3);
+  p = smem + (((p - smem) + 15) & ~15);
   const int pop_off0 = (int)(p - smem);
   p += (size_t)NT * MS;
   const int pop_off1 = (int)(p - smem);
   p += (size_t)NT * MS;
   auto POPp = [&](int b) { return smem + (b ? pop_off1 : pop_off0); };
+  p = smem + (((p - smem) + 15) & ~15);
   uint32_t* DR = reinterpret_cast<uint32_t*>(p);  // [CH][nblk*8] draws of staged children
   p += (size_t)a.CH * a.nblk * 32;
   FT* CV = reinterpret_cast<FT*>(p);  // [32][E] elite candidates (value)
@@ -317,7 +326,6 @@ __device__ __forceinline__ void solve_body(const SolveArgs& a, unsigned char* sm
   int cur = 0;
   const int lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
   const int T_ = a.tour, nblk = a.nblk, E = a.E;
-  const int nwords = MS >> 2;
   // FP32 evaluation roles: q = member*K + pilot, column-pair share h.  Each
   // half-warp takes 16 consecutive q with one share h, so the 16 rows it
   // reads in a step (distinct users, RS/2 odd; equal users read the same
@@ -362,7 +370,7 @@ __device__ __forceinline__ void solve_body(const SolveArgs& a, unsigned char* sm
           int qq = rec[u];
           qq = qq < K ? qq : K - 1;
           SE[i] = value_user_f64(a.beta, a.bnc, rec + XO, L, K, j, k, qq, a.fin, a.M64, a.pc64,
-                                 a.obj);
+                                 a.obj, K, 1);
         }
         __syncthreads();
         if (tid < nv) {
@@ -492,30 +500,20 @@ __device__ __forceinline__ void solve_body(const SolveArgs& a, unsigned char* sm
           if ((uint64_t)dr[2 * T_] < a.pc_thresh) cut = 1 + (int)below(dr[2 * T_ + 1], (uint32_t)(L - 1));
           split = (int64_t)cut * K;
         }
-        // parents' records from their owners: all remote loads issued first
+        // parents' records from their owners, 16 bytes per lane and load
         const uint32_t ra = dsmem_addr(POPp(cur) + (pa_ % NT) * MS, pa_ / NT);
         const uint32_t rb = dsmem_addr(POPp(cur) + (pb_ % NT) * MS, pb_ / NT);
-        constexpr int kMaxW = 4;  // words per lane held at once (records <= 512 bytes)
-        uint32_t wa[kMaxW], wb[kMaxW];
-#pragma unroll
-        for (int r = 0; r < kMaxW; ++r) {
-          const int w = lane + 32 * r;
-          if (w < nwords) {
-            wa[r] = ld_dsmem(ra + 4 * w);
-            wb[r] = ld_dsmem(rb + 4 * w);
-          }
-        }
-        for (int w = lane + 32 * kMaxW; w < nwords; w += 32) {  // longer records
-          const int64_t off = 4 * (int64_t)w >= XO ? XO : 0;
-          child[w] = merge_word(ld_dsmem(ra + 4 * w), ld_dsmem(rb + 4 * w), w, split + off);
-        }
-#pragma unroll
-        for (int r = 0; r < kMaxW; ++r) {
-          const int w = lane + 32 * r;
-          if (w < nwords) {
-            const int64_t off = 4 * (int64_t)w >= XO ? XO : 0;
-            child[w] = merge_word(wa[r], wb[r], w, split + off);
-          }
+        for (int v = lane; v < (MS >> 4); v += 32) {
+          const uint4 qa = ld_dsmem_v4(ra + 16 * v), qb = ld_dsmem_v4(rb + 16 * v);
+          const int w = 4 * v;
+          const int64_t o0 = 4 * (int64_t)w >= XO ? XO : 0, o1 = 4 * (int64_t)(w + 1) >= XO ? XO : 0;
+          const int64_t o2 = 4 * (int64_t)(w + 2) >= XO ? XO : 0, o3 = 4 * (int64_t)(w + 3) >= XO ? XO : 0;
+          uint4 o;
+          o.x = merge_word(qa.x, qb.x, w, split + o0);
+          o.y = merge_word(qa.y, qb.y, w + 1, split + o1);
+          o.z = merge_word(qa.z, qb.z, w + 2, split + o2);
+          o.w = merge_word(qa.w, qb.w, w + 3, split + o3);
+          reinterpret_cast<uint4*>(child)[v] = o;
         }
         __syncwarp();
         if (n >= E) {
@@ -591,11 +589,12 @@ SolveShape solve_shape(const pa_ctx* ctx, int C, int maxnp, int threads) {
   s.C = C;
   s.NT = (c.N + C - 1) / C;
   s.CH = std::max(1, std::min(s.NT, 16384 / (s.nblk * 32)));
-  // record = X | INV, 4-byte aligned halves; an odd number of words per
-  // record keeps the per-member inverse reads of one warp in distinct banks
-  s.XO = ((LK + 3) / 4) * 4;
+  // record = X | INV, 16-byte aligned halves (records are copied 16 bytes
+  // per lane); an odd number of 16-byte units per record spreads the
+  // per-member inverse reads of one warp over the banks
+  s.XO = ((LK + 15) / 16) * 16;
   s.MS = 2 * s.XO;
-  if ((s.MS / 4) % 2 == 0) s.MS += 4;
+  if ((s.MS / 16) % 2 == 0) s.MS += 16;
   const int NJ = ctx->t32.NJ;
   const int JS = f64 ? 1 : fused_js(NJ, maxnp);
   const int NPR = f64 ? 0 : NJ / 2;
@@ -623,7 +622,9 @@ SolveShape solve_shape(const pa_ctx* ctx, int C, int maxnp, int threads) {
   const size_t fsz = f64 ? 8 : 4;
   b += 2 * fsz * (size_t)((c.N + 1) & ~1);
   b += f64 ? 8 * (size_t)s.NTT * LK : 4 * (size_t)((s.NTT * c.K * NPR + 3) & ~3);
+  b = (b + 15) & ~size_t(15);
   b += 2 * (size_t)s.NT * s.MS;
+  b = (b + 15) & ~size_t(15);
   b += (size_t)s.CH * s.nblk * 32;
   b += (f64 ? 8 : 4) * 32 * 64 + 4 * 32 * 64;  // elite candidates
   s.smem = (b + 15) & ~size_t(15);
