@@ -601,7 +601,7 @@ def run_streamed(B, inputs, dev, n=1 << 17, reps=5):
                       "gens_per_s": G5 / t_solve}}
 
 
-def run_serving(B, inputs, rate=2000.0, seconds=2.0, G=40, N=64, tick=20, budget=40 << 30):
+def run_serving(B, inputs, rate=2000.0, seconds=10.0, G=40, N=64, tick=40, budget=40 << 30):
     """Poisson arrivals (rate per second for `seconds`), each request a solve
     of a fresh seeded instance with L in {7, 19}, K in {8, 16} (tau_p = K,
     M = 256, finite-M SINR, N = 64, G = 40, FP32 beta).  Served: the
@@ -770,8 +770,9 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
-    ap.add_argument("--serve-tick", type=int, default=20,
-                    help="generations per scheduling tick of the serving comparison")
+    ap.add_argument("--serve-tick", type=int, default=40,
+                    help="generations per scheduling tick of the serving comparison (the "
+                         "default, G = 40, finishes a request in the tick that admits it)")
     ap.add_argument("--serve-seconds", type=float, default=10.0,
                     help="length of the Poisson arrival window of the serving comparison "
                          "(the configured workload: 10 s at 2000 requests/s)")

@@ -78,6 +78,11 @@ struct pa_server {
   };
   std::deque<Done> done;   // completions not yet returned by a poll
   int inject_failures = 0; // testing: admissions still to fail
+  // pinned staging of the requests admitted in one tick (their uploads are
+  // asynchronous; the tick's final synchronisation ends them)
+  unsigned char* h_stage = nullptr;
+  size_t stage_cap = 0, stage_used = 0;
+  bool stage_busy = false;  // uploads from the staging buffer may be in flight
   // per-tick device/pinned scratch
   void* d_seed_args = nullptr;
   void* h_seed_args = nullptr;
@@ -243,6 +248,7 @@ void destroy_server(pa_server* s) {
   cudaFree(s->d_counters);
   cudaFreeHost(s->h_best);
   cudaFreeHost(s->h_bestfit);
+  cudaFreeHost(s->h_stage);
   cudaFree(s->d_bestfit);
   if (s->own_stream) cudaStreamDestroy(s->stream);
   delete s;
@@ -408,9 +414,42 @@ pa_status pa_server_inject_admission_failures(pa_server* s, int32_t count) {
 
 }  // extern "C"
 
+// Bytes of pinned staging for one request's upload, 16-byte aligned parts.
+static size_t stage_bytes(const pa_server::Req& r) {
+  auto al = [](size_t x) { return (x + 15) & ~size_t(15); };
+  return al(8 * r.beta.size()) + al(4 * r.uxy.size()) + al(4 * r.bxy.size());
+}
+
 static pa_status tick_impl(pa_server* s) {
   pa_status st = PA_OK;
-  // ---- 1. admission, in arrival order
+  // pinned staging for this tick's admissions (grown between ticks only:
+  // earlier uploads of this tick may still read the old buffer otherwise;
+  // a tick that failed before its final synchronisation may have left
+  // uploads in flight)
+  if (s->stage_busy) {
+    st = scuda(s, cudaStreamSynchronize(s->stream), "staging sync");
+    if (st != PA_OK) return st;
+    s->stage_busy = false;
+  }
+  {
+    size_t need = 0;
+    for (const auto& r : s->pending) need += stage_bytes(r);
+    need = std::min(need, (size_t)64 << 20);
+    if (need > s->stage_cap) {  // rare: 4 MB first, then doubling (pinned allocations are slow)
+      const size_t cap = std::max({need, 2 * s->stage_cap, (size_t)16 << 20});
+      cudaFreeHost(s->h_stage);
+      s->h_stage = nullptr;
+      s->stage_cap = 0;
+      if (cudaMallocHost(&s->h_stage, cap) == cudaSuccess) s->stage_cap = cap;
+      else (void)cudaGetLastError();
+    }
+    s->stage_used = 0;
+  }
+  // ---- 1. admission, in arrival order; at most kMaxNewSlots contexts are
+  // created per tick (creating one allocates and synchronises), so a burst
+  // of new classes or a backlog cannot stall one tick for everyone
+  constexpr int kMaxNewSlots = 4;
+  int created_now = 0;
   std::vector<int> fresh;
   while (!s->pending.empty()) {
     pa_server::Req& r = s->pending.front();
@@ -423,8 +462,10 @@ static pa_status tick_impl(pa_server* s) {
       slot = fl.back();
       fl.pop_back();
     } else {
+      if (created_now == kMaxNewSlots) break;  // the next tick creates more
       const size_t need = slot_bytes(c);
       if (!make_room(s, need, key)) break;  // wait for running slots to finish
+      ++created_now;
       pa_ctx* ctx = nullptr;
       pa_status cs;
       std::string why;
@@ -458,14 +499,34 @@ static pa_status tick_impl(pa_server* s) {
       created = true;
     }
     pa_server::Slot& sl = s->slots[slot];
-    pa_status ls;
-    if (!created && s->inject_failures > 0) {
+    pa_status ls = PA_OK;
+    if (created) {  // pa_create uploaded this request's instance already
+      sl.ctx->cfg.seed = r.seed;
+    } else if (s->inject_failures > 0) {
       --s->inject_failures;
       ls = PA_ECUDA;
       s->err = "injected admission failure";
     } else {
       sl.ctx->cfg.seed = r.seed;
-      ls = pa_load_instance(sl.ctx, r.beta.data(), r.uxy.data(), r.bxy.data());
+      const double* beta = r.beta.data();
+      const int32_t* uxy = r.uxy.data();
+      const int32_t* bxy = r.bxy.data();
+      const size_t sb = stage_bytes(r);
+      if (s->stage_used + sb <= s->stage_cap) {  // else the pageable copy (synchronous upload)
+        unsigned char* h = s->h_stage + s->stage_used;
+        const size_t nb = 8 * r.beta.size(), nu = 4 * r.uxy.size();
+        std::memcpy(h, beta, nb);
+        std::memcpy(h + ((nb + 15) & ~size_t(15)), uxy, nu);
+        std::memcpy(h + ((nb + 15) & ~size_t(15)) + ((nu + 15) & ~size_t(15)), bxy,
+                    4 * r.bxy.size());
+        beta = reinterpret_cast<const double*>(h);
+        uxy = reinterpret_cast<const int32_t*>(h + ((nb + 15) & ~size_t(15)));
+        bxy = reinterpret_cast<const int32_t*>(h + ((nb + 15) & ~size_t(15)) +
+                                               ((nu + 15) & ~size_t(15)));
+        s->stage_used += sb;
+        s->stage_busy = true;
+      }
+      ls = pa_load_instance(sl.ctx, beta, uxy, bxy);
       if (ls != PA_OK) s->err = pa_last_error(sl.ctx);
     }
     if (ls != PA_OK) {  // the slot stays usable for later requests
@@ -558,6 +619,10 @@ static pa_status tick_impl(pa_server* s) {
     // once (16 CTAs for up to 9 slots on 152 SMs), smaller if it cannot fit
     int C = 16;
     while (C > 1 && n_act * C > proto->num_sms) C /= 2;
+    // while every active slot has 16 CTAs of its own, generations are
+    // latency-bound: the one-instance kernel's column split, else the
+    // throughput split
+    bool latency = C == 16;
     size_t smem = 0;
     bool ok = false;
     for (; C >= 1 && !ok; C /= 2) {
@@ -571,44 +636,52 @@ static pa_status tick_impl(pa_server* s) {
         double* best_fit = fin ? s->d_bestfit + fin_index[mem[m]] : nullptr;
         const size_t need = pa::solve_fill_args(sl.ctx, C, sl.gen, g_now, sl.ctx->pop[sl.ctx->cur],
                                                 sl.ctx->pop[sl.ctx->cur ^ 1], sl.ctx->fit, best_row,
-                                                best_fit, ha + a_off + ab * m);
+                                                best_fit, ha + a_off + ab * m, latency);
         if (need == 0) {
           ok = false;
           break;
         }
         smem = std::max(smem, need);
       }
-      if (ok && pa::solve_batch_max_clusters(proto, C, smem) < 1) ok = false;
+      if (ok && pa::solve_batch_max_clusters(proto, C, smem, latency) < 1) ok = false;
       if (ok) break;
+      if (latency) {  // the latency split does not fit: the throughput split, same C
+        latency = false;
+        C *= 2;
+      }
     }
     if (!ok) {  // cannot happen for shapes checked at submit; fail these requests only
       for (int i : mem) s->slots[i].failed = true;
       continue;
     }
     const int clusters =
-        std::min<int>((int)mem.size(), pa::solve_batch_max_clusters(proto, C, smem));
+        std::min<int>((int)mem.size(), pa::solve_batch_max_clusters(proto, C, smem, latency));
     unsigned char* dargs = static_cast<unsigned char*>(s->d_solve_args) + a_off;
     st = scuda(s, cudaMemcpyAsync(dargs, ha + a_off, ab * mem.size(), cudaMemcpyHostToDevice,
                                   s->stream),
                "copy solve args");
-    // the variants' launches run side by side: group k on side stream k,
-    // forked from and joined back into the server stream
-    if (st == PA_OK) st = side_stream(s, gk);
-    if (st == PA_OK) st = scuda(s, cudaEventRecord(s->fork, s->stream), "fork");
-    if (st == PA_OK) st = scuda(s, cudaStreamWaitEvent(s->side[gk], s->fork, 0), "fork wait");
+    // one group runs on the server stream itself; several run side by side,
+    // group k on side stream k, forked from and joined back into it
+    const bool forked = groups.size() > 1;
+    if (st == PA_OK && forked) st = side_stream(s, gk);
+    if (st == PA_OK && forked) st = scuda(s, cudaEventRecord(s->fork, s->stream), "fork");
+    if (st == PA_OK && forked)
+      st = scuda(s, cudaStreamWaitEvent(s->side[gk], s->fork, 0), "fork wait");
     if (st == PA_OK)
       st = scuda(s, pa::launch_solve_batch(proto, C, clusters, dargs, (int)mem.size(),
-                                           s->d_counters + gk, smem, s->side[gk]),
+                                           s->d_counters + gk, smem,
+                                           forked ? s->side[gk] : s->stream, latency),
                  "batched solve kernel");
-    if (st == PA_OK) st = scuda(s, cudaEventRecord(s->joined[gk], s->side[gk]), "join");
+    if (st == PA_OK && forked) st = scuda(s, cudaEventRecord(s->joined[gk], s->side[gk]), "join");
     if (st != PA_OK) return st;
     a_off += ab * mem.size();
     ++gk;
   }
-  for (int k = 0; k < gk; ++k) {
-    st = scuda(s, cudaStreamWaitEvent(s->stream, s->joined[k], 0), "join wait");
-    if (st != PA_OK) return st;
-  }
+  if (groups.size() > 1)
+    for (int k = 0; k < gk; ++k) {
+      st = scuda(s, cudaStreamWaitEvent(s->stream, s->joined[k], 0), "join wait");
+      if (st != PA_OK) return st;
+    }
   // ---- 4. collect finished requests
   for (int i : finishing) {
     pa_server::Slot& sl = s->slots[i];
@@ -626,6 +699,7 @@ static pa_status tick_impl(pa_server* s) {
   }
   st = scuda(s, cudaStreamSynchronize(s->stream), "tick sync");
   if (st != PA_OK) return st;
+  s->stage_busy = false;
   for (auto& kv : groups)
     for (int i : kv.second) {
       pa_server::Slot& sl = s->slots[i];

@@ -2,135 +2,27 @@
 // clusters take the next instance from a counter and run the whole GA on it
 // (the same device code as the one-instance kernel, pa_solve_body.cuh); the
 // argument records, launch shapes and CTA sizes of the batch and server paths.
-#include <algorithm>
-#include <atomic>
+// The throughput column split is instantiated here; the latency split (the
+// one-instance kernel's, for a few concurrent instances) in
+// pa_solve_batch_lat.cu.
 #include <cstring>
+#include <map>
+#include <mutex>
+#include <tuple>
 
-#include "pa_solve_body.cuh"
+#include "pa_solve_batch.cuh"
 
 namespace pa {
-namespace {
 
-// Many instances per launch (persistent clusters): each cluster takes the
-// next instance index from a global counter until the list is exhausted.
-// Instances of one launch share the kernel variant (NJ, VEC, FIN, FT); their
-// sizes may differ (shared memory is sized for the largest).
-template <typename FT, int NJ, int VEC, bool FIN, int THREADS>
-__global__ void __launch_bounds__(THREADS, kSolveThreads / THREADS)
-    k_solve_batch(const SolveArgs* __restrict__ insts, int n_inst, int* __restrict__ counter) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ int elites[64];
-  __shared__ int next;
-  // the instance's arguments live in shared memory (a local copy would sit
-  // in local memory: the kernel runs at the 64-register limit)
-  __shared__ SolveArgs sargs;
-  static_assert(sizeof(SolveArgs) % 8 == 0, "SolveArgs is copied as 8-byte words");
-  constexpr int kArgWords = (int)(sizeof(SolveArgs) / 8);
-  static_assert(kArgWords <= THREADS, "one word per thread");
-  cg::cluster_group cluster = cg::this_cluster();
-  const int C = (int)cluster.num_blocks();
-  for (;;) {
-    if (cluster.block_rank() == 0 && threadIdx.x == 0) {
-      const int i = atomicAdd(counter, 1);
-      for (int r = 0; r < C; ++r) *cluster.map_shared_rank(&next, r) = i;
-    }
-    cluster.sync();
-    const int i = next;
-    if (i >= n_inst) break;
-    if (threadIdx.x < kArgWords)
-      reinterpret_cast<uint64_t*>(&sargs)[threadIdx.x] =
-          reinterpret_cast<const uint64_t*>(insts + i)[threadIdx.x];
-    __syncthreads();
-    solve_body<FT, NJ, VEC, FIN, kBatchMaxNP>(sargs, smem, elites, cluster);
-  }
+cudaError_t dispatch_batch_latency(const pa_ctx* proto, int C, int clusters, const void* d, int n,
+                                   int* ctr, size_t smem, bool q, int* mc, cudaStream_t st);
+
+static cudaError_t dispatch_any(bool latency, const pa_ctx* proto, int C, int clusters,
+                                const SolveArgs* d, int n, int* ctr, size_t smem, bool q, int* mc,
+                                cudaStream_t st) {
+  return latency ? dispatch_batch_latency(proto, C, clusters, d, n, ctr, smem, q, mc, st)
+                 : dispatch_batch<kBatchMaxNP>(proto, C, clusters, d, n, ctr, smem, q, mc, st);
 }
-
-}  // namespace
-
-namespace {
-
-template <typename FT, int NJ, int VEC, bool FIN, int THREADS>
-cudaError_t run_solve_batch(int C, int clusters, const SolveArgs* d_args, int n, int* d_counter,
-                            size_t smem, bool query_only, int* max_clusters, cudaStream_t st) {
-  auto kern = k_solve_batch<FT, NJ, VEC, FIN, THREADS>;
-  static std::atomic<uint64_t> prepared{0};
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return e;
-  const uint64_t bit = 1ULL << (dev & 63);
-  if (!(prepared.load() & bit)) {
-    e = raise_smem_cap((const void*)kern, dev);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-    if (e != cudaSuccess) return e;
-    prepared.fetch_or(bit);
-  }
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(C * std::max(1, clusters), 1, 1);
-  cfg.blockDim = dim3(THREADS, 1, 1);
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = st;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = C;
-  attr[0].val.clusterDim.y = 1;
-  attr[0].val.clusterDim.z = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  if (query_only) {
-    int m = 0;
-    e = cudaOccupancyMaxActiveClusters(&m, kern, &cfg);
-    if (e != cudaSuccess) {
-      (void)cudaGetLastError();
-      m = 0;
-    }
-    *max_clusters = m;
-    return cudaSuccess;
-  }
-  (void)cudaGetLastError();  // drop a stale error of an earlier call
-  e = cudaLaunchKernelEx(&cfg, kern, d_args, n, d_counter);
-  count_launch();
-  return e;
-}
-
-template <typename FT, int VEC, bool FIN>
-cudaError_t pick_batch(int NJ, int C, int clusters, const SolveArgs* d, int n, int* ctr,
-                       size_t smem, bool q, int* mc, cudaStream_t st) {
-  constexpr int T = kSolveThreads;
-  switch (NJ) {
-    case 4: return run_solve_batch<FT, 4, VEC, FIN, T>(C, clusters, d, n, ctr, smem, q, mc, st);
-    case 8: return run_solve_batch<FT, 8, VEC, FIN, T>(C, clusters, d, n, ctr, smem, q, mc, st);
-    case 12: return run_solve_batch<FT, 12, VEC, FIN, T>(C, clusters, d, n, ctr, smem, q, mc, st);
-    case 16: return run_solve_batch<FT, 16, VEC, FIN, T>(C, clusters, d, n, ctr, smem, q, mc, st);
-    case 20: return run_solve_batch<FT, 20, VEC, FIN, T>(C, clusters, d, n, ctr, smem, q, mc, st);
-    case 24: return run_solve_batch<FT, 24, VEC, FIN, T>(C, clusters, d, n, ctr, smem, q, mc, st);
-    case 28: return run_solve_batch<FT, 28, VEC, FIN, T>(C, clusters, d, n, ctr, smem, q, mc, st);
-    case 32: return run_solve_batch<FT, 32, VEC, FIN, T>(C, clusters, d, n, ctr, smem, q, mc, st);
-    case 36: return run_solve_batch<FT, 36, VEC, FIN, T>(C, clusters, d, n, ctr, smem, q, mc, st);
-    case 40: return run_solve_batch<FT, 40, VEC, FIN, T>(C, clusters, d, n, ctr, smem, q, mc, st);
-    case 44: return run_solve_batch<FT, 44, VEC, FIN, T>(C, clusters, d, n, ctr, smem, q, mc, st);
-    case 48: return run_solve_batch<FT, 48, VEC, FIN, T>(C, clusters, d, n, ctr, smem, q, mc, st);
-    default: return cudaErrorInvalidValue;
-  }
-}
-
-
-cudaError_t dispatch_batch(const pa_ctx* proto, int C, int clusters, const SolveArgs* d, int n,
-                           int* ctr, size_t smem, bool q, int* mc, cudaStream_t st) {
-  const pa_config& c = proto->cfg;
-  const bool fin = c.mode == PA_SINR_FINITE_M;
-  if (c.prec == PA_FP64)
-    return run_solve_batch<double, 4, 2, false, kSolveThreads>(C, clusters, d, n, ctr, smem, q,
-                                                               mc, st);
-  const int NJ = proto->t32.NJ;
-  if (proto->t32.vec == 2)
-    return fin ? pick_batch<float, 2, true>(NJ, C, clusters, d, n, ctr, smem, q, mc, st)
-               : pick_batch<float, 2, false>(NJ, C, clusters, d, n, ctr, smem, q, mc, st);
-  return fin ? pick_batch<float, 1, true>(NJ, C, clusters, d, n, ctr, smem, q, mc, st)
-             : pick_batch<float, 1, false>(NJ, C, clusters, d, n, ctr, smem, q, mc, st);
-}
-
-}  // namespace
 
 size_t solve_args_bytes() { return sizeof(SolveArgs); }
 
@@ -139,10 +31,10 @@ size_t solve_args_bytes() { return sizeof(SolveArgs); }
 // does not fit in one CTA.
 size_t solve_fill_args(const pa_ctx* ctx, int C, int gen0, int G, const uint8_t* pop_in,
                        uint8_t* pop_out, void* fit_out, uint8_t* best_row, double* best_fit,
-                       void* args_out) {
+                       void* args_out, bool latency) {
   const pa_config& c = ctx->cfg;
   if (C > c.N || ctx->t32.streamed) return 0;
-  const SolveShape s = solve_shape(ctx, C, kBatchMaxNP, kSolveThreads);
+  const SolveShape s = solve_shape(ctx, C, latency ? kSoloMaxNP : kBatchMaxNP, kSolveThreads);
   if (s.smem > (size_t)kSmemBudget - 64 * 4 - 16) return 0;
   SolveArgs a{};
   a.pop_in = pop_in;
@@ -185,19 +77,41 @@ size_t solve_fill_args(const pa_ctx* ctx, int C, int gen0, int G, const uint8_t*
 
 // Clusters of size C that can be resident at once for the batched kernel of
 // proto's variant with this shared memory (0 when none).
-int solve_batch_max_clusters(const pa_ctx* proto, int C, size_t smem) {
+// Cached per (device, kernel variant, cluster size, shared memory): the
+// occupancy query costs host time on every scheduling tick otherwise.
+int solve_batch_max_clusters(const pa_ctx* proto, int C, size_t smem, bool latency) {
+  struct Key {
+    int dev, prec, fin, nj, vec, C, lat;
+    size_t smem;
+    bool operator<(const Key& o) const {
+      return std::tie(dev, prec, fin, nj, vec, C, lat, smem) <
+             std::tie(o.dev, o.prec, o.fin, o.nj, o.vec, o.C, o.lat, o.smem);
+    }
+  };
+  static std::map<Key, int> cache;
+  static std::mutex mu;
+  const Key k{proto->device, proto->cfg.prec, proto->cfg.mode, proto->t32.NJ, proto->t32.vec, C,
+              latency ? 1 : 0, smem};
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = cache.find(k);
+    if (it != cache.end()) return it->second;
+  }
   int m = 0;
-  if (dispatch_batch(proto, C, 1, nullptr, 0, nullptr, smem, true, &m, nullptr) != cudaSuccess)
+  if (dispatch_any(latency, proto, C, 1, nullptr, 0, nullptr, smem, true, &m, nullptr) !=
+      cudaSuccess)
     return 0;
+  std::lock_guard<std::mutex> lock(mu);
+  cache[k] = m;
   return m;
 }
 
 // Persistent batched solve of n instances sharing proto's kernel variant:
 // d_args holds their SolveArgs (cluster size C), d_counter must be zero.
 cudaError_t launch_solve_batch(const pa_ctx* proto, int C, int clusters, const void* d_args, int n,
-                               int* d_counter, size_t smem, cudaStream_t st) {
-  return dispatch_batch(proto, C, clusters, static_cast<const SolveArgs*>(d_args), n, d_counter,
-                        smem, false, nullptr, st);
+                               int* d_counter, size_t smem, cudaStream_t st, bool latency) {
+  return dispatch_any(latency, proto, C, clusters, static_cast<const SolveArgs*>(d_args), n,
+                      d_counter, smem, false, nullptr, st);
 }
 
 }  // namespace pa

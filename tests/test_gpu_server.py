@@ -293,10 +293,10 @@ def test_server_completions_are_not_lost_when_polls_return_fewer(B):
             inst = r["inst"]
             srv.submit(r["id"], r["L"], r["K"], r["seed"], inst["beta"], inst["user_xy_mm"],
                        inst["bs_xy_mm"])
-        done, active, pending = srv.poll(max_done=2)  # all seven finish in this tick
-        assert len(done) == 2 and active == 0 and pending == 0
+        done, _, _ = srv.poll(max_done=2)  # several finish in this tick (G = tick)
         ids += [d[0] for d in done]
-        for _ in range(5):
+        assert len(done) == 2 and srv.stats()["completed"] > 2  # the rest stay queued
+        for _ in range(10):
             done, _, _ = srv.poll(max_done=2)
             ids += [d[0] for d in done]
     finally:
