@@ -338,6 +338,15 @@ pa_status pa_batch_groups(pa_batch* b, int32_t* n_groups, int32_t* cluster_sizes
  */
 pa_status pa_batch_solve(pa_batch* b, int32_t generations, uint8_t* best_host, double* best_fit);
 
+/*
+ * Latency of each instance in the last pa_batch_solve: ms_host[i] = time
+ * from the start of that solve's GPU work until instance i's best member
+ * and final population were complete (device clock, %globaltimer).  The
+ * instances of a batch are all submitted at once, so this is each one's
+ * completion latency.  Synchronous.
+ */
+pa_status pa_batch_completion_times(pa_batch* b, double* ms_host);
+
 /* Context of instance i (owned by the batch): for pa_get_population etc. */
 pa_status pa_batch_context(pa_batch* b, int32_t i, pa_ctx** out);
 

@@ -80,6 +80,7 @@ _SIGS = {
     "pa_batch_groups": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "pa_batch_solve": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p]),
     "pa_batch_context": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_void_p)]),
+    "pa_batch_completion_times": (C.c_int, [C.c_void_p, C.c_void_p]),
     "pa_batch_last_error": (C.c_char_p, [C.c_void_p]),
     "pa_server_create": (C.c_int, [C.POINTER(pa_config), C.c_int32, C.c_int32, C.c_uint64,
                                    C.c_void_p, C.POINTER(C.c_void_p)]),
@@ -446,6 +447,12 @@ class Batch:
         rows = [best[self.offsets[i]:self.offsets[i + 1]].reshape(self.shapes[i])
                 for i in range(self.n)]
         return rows, fit
+
+    def completion_times_ms(self):
+        """Per-instance completion latency (ms) of the last solve."""
+        out = np.zeros(self.n, dtype=np.float64)
+        self._bcheck(lib().pa_batch_completion_times(self.handle, _host_ptr(out)))
+        return out
 
     def load(self, i, beta, user_xy_mm=None, bs_xy_mm=None):
         b = np.ascontiguousarray(beta, dtype=np.float64)

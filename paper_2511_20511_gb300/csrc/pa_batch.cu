@@ -57,10 +57,18 @@ struct pa_batch {
   int graph_G = -1;
   cudaEvent_t fork = nullptr;
   bool own_stream = false;
+  unsigned long long* d_stamp = nullptr;  // [n] completion of each instance, [n] start (ns)
   std::string err;
 };
 
 namespace {
+
+// The start of a batch solve on the device clock (ns).
+__global__ void k_stamp(unsigned long long* p) {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  *p = t;
+}
 
 pa_status bfail(pa_batch* b, pa_status st, const std::string& m) {
   if (b) b->err = m;
@@ -84,6 +92,7 @@ void destroy_batch(pa_batch* b) {
   if (b->fork) cudaEventDestroy(b->fork);
   cudaFree(b->d_seed_args);
   cudaFree(b->d_counters);
+  cudaFree(b->d_stamp);
   cudaFree(b->d_best);
   cudaFree(b->d_bestfit);
   cudaFreeHost(b->h_best);
@@ -106,6 +115,7 @@ pa_status build_group_args(pa_batch* b, pa_batch::Group& g, int C, int G) {
                                          b->d_best + b->best_off[i], b->d_bestfit + i,
                                          h.data() + m * ab);
     if (s == 0) return PA_EUNSUPPORTED;
+    pa::solve_args_set_stamp(h.data() + m * ab, b->d_stamp + i);
     smem = std::max(smem, s);
   }
   const int maxc = pa::solve_batch_max_clusters(b->ctx[g.members[0]], C, smem);
@@ -135,8 +145,12 @@ int default_cluster(const pa_batch* b, const pa_batch::Group& g) {
 }
 
 pa_status run_groups(pa_batch* b, cudaStream_t st) {
-  pa_status s = bcuda(b, cudaMemsetAsync(b->d_counters, 0, sizeof(int) * b->groups.size(), st),
-                      "reset counters");
+  k_stamp<<<1, 1, 0, st>>>(b->d_stamp + b->n);
+  pa::count_launch();
+  pa_status s = bcuda(b, cudaGetLastError(), "stamp kernel");
+  if (s != PA_OK) return s;
+  s = bcuda(b, cudaMemsetAsync(b->d_counters, 0, sizeof(int) * b->groups.size(), st),
+            "reset counters");
   if (s != PA_OK) return s;
   s = bcuda(b, pa::launch_seed_batch(b->d_seed_args, b->n, b->seed_smem, b->seed_C, st),
             "seed kernel");
@@ -257,6 +271,7 @@ pa_status pa_batch_create(int32_t n, const pa_config* cfgs, const double* const*
     chk(cudaMallocHost(&b->h_bestfit, sizeof(double) * n), "cudaMallocHost best fit");
     chk(cudaMalloc(&b->d_counters, sizeof(int) * std::max<size_t>(1, b->groups.size())),
         "cudaMalloc counters");
+    chk(cudaMalloc(&b->d_stamp, sizeof(unsigned long long) * (n + 1)), "cudaMalloc stamps");
     chk(cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming), "event");
   }
   if (st == PA_OK) {
@@ -430,6 +445,18 @@ pa_status pa_batch_solve(pa_batch* b, int32_t generations, uint8_t* best_host, d
   }
   if (best_host) std::memcpy(best_host, b->h_best, (size_t)b->best_bytes);
   if (best_fit) std::memcpy(best_fit, b->h_bestfit, sizeof(double) * b->n);
+  return PA_OK;
+}
+
+pa_status pa_batch_completion_times(pa_batch* b, double* ms_host) {
+  if (!b || !ms_host) return PA_EINVAL;
+  std::vector<unsigned long long> t(b->n + 1);
+  pa_status st = bcuda(b, cudaMemcpyAsync(t.data(), b->d_stamp, sizeof(t[0]) * t.size(),
+                                          cudaMemcpyDeviceToHost, b->stream),
+                       "copy stamps");
+  if (st == PA_OK) st = bcuda(b, cudaStreamSynchronize(b->stream), "sync");
+  if (st != PA_OK) return st;
+  for (int i = 0; i < b->n; ++i) ms_host[i] = (double)(long long)(t[i] - t[b->n]) * 1e-6;
   return PA_OK;
 }
 

@@ -140,6 +140,7 @@ size_t solve_fill_args(const pa_ctx* ctx, int C, int gen0, int G, const uint8_t*
                        uint8_t* pop_out, void* fit_out, uint8_t* best_row, double* best_fit,
                        void* args_out, bool latency = false);
 int solve_batch_max_clusters(const pa_ctx* proto, int C, size_t smem, bool latency = false);
+void solve_args_set_stamp(void* args, unsigned long long* stamp);
 cudaError_t launch_solve_batch(const pa_ctx* proto, int C, int clusters, const void* d_args, int n,
                                int* d_counter, size_t smem, cudaStream_t st, bool latency = false);
 // pa_ga.cu: seed many instances at once (a cluster of C CTAs each) from n

@@ -75,6 +75,11 @@ size_t solve_fill_args(const pa_ctx* ctx, int C, int gen0, int G, const uint8_t*
   return s.smem;
 }
 
+// Set the completion-time stamp of an argument record (a SolveArgs).
+void solve_args_set_stamp(void* args, unsigned long long* stamp) {
+  static_cast<SolveArgs*>(args)->stamp = stamp;
+}
+
 // Clusters of size C that can be resident at once for the batched kernel of
 // proto's variant with this shared memory (0 when none).
 // Cached per (device, kernel variant, cluster size, shared memory): the

@@ -46,6 +46,7 @@ struct SolveArgs {
   double M64, pc64;
   int fin;
   int obj;  // PA_OBJ_MIN_SINR: smallest SINR instead of the SE sum
+  unsigned long long* stamp;  // when given: %globaltimer (ns) once the outputs are complete
 };
 
 template <typename FT>
@@ -289,8 +290,10 @@ __device__ __forceinline__ void solve_body(const SolveArgs& a, unsigned char* sm
   p = smem + (((p - smem) + 15) & ~15);
   uint32_t* DR = reinterpret_cast<uint32_t*>(p);  // [CH][nblk*8] draws of staged children
   p += (size_t)a.CH * a.nblk * 32;
-  FT* CV = reinterpret_cast<FT*>(p);  // [32][E] elite candidates (value)
-  int* CI = reinterpret_cast<int*>(p + sizeof(FT) * 32 * 64);  // [32][E] (index)
+  // [32][E] elite candidates (value, index) of the large-E search (E > kSmallE
+  // only: the space is not reserved otherwise)
+  FT* CV = reinterpret_cast<FT*>(p);
+  int* CI = reinterpret_cast<int*>(p + sizeof(FT) * 32 * 64);
 
   const int base_n = rank * NT;
   const int nvalid = max(0, min(NT, N - base_n));
@@ -572,6 +575,11 @@ __device__ __forceinline__ void solve_body(const SolveArgs& a, unsigned char* sm
     if (lane == 0) *a.best_fit = (double)fit[best];
   }
   cluster.sync();  // keep this CTA's shared memory alive for remote readers
+  if (a.stamp && rank == 0 && tid == 0) {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    *a.stamp = t;
+  }
 }
 
 // ------------------------------------------------------------------ launch
@@ -626,7 +634,7 @@ SolveShape solve_shape(const pa_ctx* ctx, int C, int maxnp, int threads) {
   b += 2 * (size_t)s.NT * s.MS;
   b = (b + 15) & ~size_t(15);
   b += (size_t)s.CH * s.nblk * 32;
-  b += (f64 ? 8 : 4) * 32 * 64 + 4 * 32 * 64;  // elite candidates
+  if (c.E > kSmallE) b += (f64 ? 8 : 4) * 32 * 64 + 4 * 32 * 64;  // elite candidates
   s.smem = (b + 15) & ~size_t(15);
   return s;
 }
