@@ -9,10 +9,12 @@
 // CTAs per instance, 16 while the batch stays resident, down to 1).  The
 // whole batch solve -- counter reset, seeding, the group
 // launches on parallel streams, and the copies of the best members to the
-// host -- is captured once into a CUDA graph and replayed.  The cluster size
-// of each group (1 CTA per instance up to 16) is picked by pa_batch_tune,
-// which times the candidates on the batch itself; the results do not depend
-// on it (every instance's arithmetic is the same whatever the tiling).
+// host -- is captured once into a CUDA graph and replayed.  The tiling of
+// each group -- CTA size (1024 threads, one CTA per SM, or 256, four per SM
+// and so several instances sharing an SM) and cluster size (1 to 16 CTAs
+// per instance) -- is picked by pa_batch_tune, which times the candidates
+// on the batch itself; the results do not depend on it (every instance's
+// arithmetic is the same whatever the tiling).
 #include <algorithm>
 #include <cstring>
 #include <map>
@@ -35,6 +37,7 @@ struct pa_batch {
   struct Group {
     std::vector<int> members;
     int C = 0;
+    int threads = 1024;  // CTA size: 1024 (one CTA per SM) or 256 (four per SM)
     int clusters = 0;
     size_t smem = 0;
     std::vector<unsigned char> h_args;
@@ -104,7 +107,7 @@ void destroy_batch(pa_batch* b) {
 
 // (Re)build one group's argument records for cluster size C and G
 // generations; 0 on success, else the status.
-pa_status build_group_args(pa_batch* b, pa_batch::Group& g, int C, int G) {
+pa_status build_group_args(pa_batch* b, pa_batch::Group& g, int C, int G, int threads) {
   const size_t ab = pa::solve_args_bytes();
   std::vector<unsigned char> h(ab * g.members.size());
   size_t smem = 0;
@@ -113,12 +116,12 @@ pa_status build_group_args(pa_batch* b, pa_batch::Group& g, int C, int G) {
     pa_ctx* c = b->ctx[i];
     const size_t s = pa::solve_fill_args(c, C, 0, G, c->pop[0], c->pop[1], c->fit,
                                          b->d_best + b->best_off[i], b->d_bestfit + i,
-                                         h.data() + m * ab);
+                                         h.data() + m * ab, false, threads);
     if (s == 0) return PA_EUNSUPPORTED;
     pa::solve_args_set_stamp(h.data() + m * ab, b->d_stamp + i);
     smem = std::max(smem, s);
   }
-  const int maxc = pa::solve_batch_max_clusters(b->ctx[g.members[0]], C, smem);
+  const int maxc = pa::solve_batch_max_clusters(b->ctx[g.members[0]], C, smem, false, threads);
   if (maxc < 1) return PA_EUNSUPPORTED;
   if (!g.d_args) {
     pa_status st = bcuda(b, cudaMalloc(&g.d_args, h.size()), "cudaMalloc batch args");
@@ -129,6 +132,7 @@ pa_status build_group_args(pa_batch* b, pa_batch::Group& g, int C, int G) {
   if (st != PA_OK) return st;
   g.h_args.swap(h);
   g.C = C;
+  g.threads = threads;
   g.smem = smem;
   g.clusters = std::min<int>((int)g.members.size(), maxc);
   return PA_OK;
@@ -162,7 +166,8 @@ pa_status run_groups(pa_batch* b, cudaStream_t st) {
     s = bcuda(b, cudaStreamWaitEvent(g.side, b->fork, 0), "fork wait");
     if (s != PA_OK) return s;
     s = bcuda(b, pa::launch_solve_batch(b->ctx[g.members[0]], g.C, g.clusters, g.d_args,
-                                        (int)g.members.size(), b->d_counters + k, g.smem, g.side),
+                                        (int)g.members.size(), b->d_counters + k, g.smem, g.side,
+                                        false, g.threads),
               "batched solve kernel");
     if (s != PA_OK) return s;
     s = bcuda(b, cudaEventRecord(g.done, g.side), "join");
@@ -299,7 +304,7 @@ pa_status pa_batch_create(int32_t n, const pa_config* cfgs, const double* const*
     for (int C = C0 / 2; C >= 1; C /= 2) order.push_back(C);
     pa_status gs = PA_EUNSUPPORTED;
     for (int C : order) {
-      gs = build_group_args(b, g, C, 1);
+      gs = build_group_args(b, g, C, 1, 1024);
       if (gs != PA_EUNSUPPORTED) break;
     }
     if (gs != PA_OK) st = bfail(b, gs, "an instance of the batch does not fit the solve kernel");
@@ -336,49 +341,58 @@ pa_status pa_batch_load(pa_batch* b, int32_t i, const double* beta, const int32_
 pa_status pa_batch_tune(pa_batch* b, int32_t generations, int32_t* chosen) {
   if (!b) return PA_EINVAL;
   if (generations < 1) return bfail(b, PA_EINVAL, "generations must be >= 1");
-  pa_status st = bcuda(b,
-                       pa::launch_seed_batch(b->d_seed_args, b->n, b->seed_smem, b->seed_C,
-                                             b->stream),
-                       "seed kernel");
-  if (st != PA_OK) return st;
-  cudaEvent_t e0, e1;
-  cudaEventCreate(&e0);
-  cudaEventCreate(&e1);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  pa_status st = bcuda(b, cudaEventCreate(&e0), "event");
+  if (st == PA_OK) st = bcuda(b, cudaEventCreate(&e1), "event");
+  // The groups run concurrently, so a shape is judged by the whole batch's
+  // time: coordinate descent over the groups, each trying every shape that
+  // fits while the others keep theirs (seeding included, the same in every
+  // run).  Second of two runs counts.
+  auto time_all = [&](float* ms) {
+    for (int rep = 0; rep < 2 && st == PA_OK; ++rep) {
+      cudaEventRecord(e0, b->stream);
+      st = run_groups(b, b->stream);
+      if (st != PA_OK) break;
+      cudaEventRecord(e1, b->stream);
+      st = bcuda(b, cudaEventSynchronize(e1), "tune sync");
+      if (st == PA_OK) cudaEventElapsedTime(ms, e0, e1);
+    }
+  };
+  for (auto& g : b->groups)
+    if (st == PA_OK) st = build_group_args(b, g, g.C, generations, g.threads);
   for (size_t k = 0; k < b->groups.size() && st == PA_OK; ++k) {
     auto& g = b->groups[k];
-    int best_C = g.C;
-    float best_ms = -1.f;
-    for (int C : {1, 2, 4, 8, 16}) {
-      pa_status gs = build_group_args(b, g, C, generations);
-      if (gs == PA_EUNSUPPORTED) continue;
-      if (gs != PA_OK) {
-        st = gs;
-        break;
-      }
-      float ms = 0.f;
-      for (int rep = 0; rep < 2; ++rep) {  // first run warms up
-        cudaMemsetAsync(b->d_counters + k, 0, sizeof(int), b->stream);
-        cudaEventRecord(e0, b->stream);
-        cudaError_t e = pa::launch_solve_batch(b->ctx[g.members[0]], g.C, g.clusters, g.d_args,
-                                               (int)g.members.size(), b->d_counters + k, g.smem,
-                                               b->stream);
-        cudaEventRecord(e1, b->stream);
-        st = bcuda(b, e, "batched solve kernel");
-        if (st == PA_OK) st = bcuda(b, cudaEventSynchronize(e1), "tune sync");
+    int best_C = g.C, best_T = g.threads;
+    float best_ms = 0.f;
+    time_all(&best_ms);
+    // the tiling choice: clusters of 1024-thread CTAs (one CTA per SM) or of
+    // 256-thread CTAs (four per SM, several instances sharing an SM), each
+    // with 1 to 16 CTAs per instance
+    for (int T : {1024, 256})
+      for (int C : {1, 2, 4, 8, 16}) {
         if (st != PA_OK) break;
-        cudaEventElapsedTime(&ms, e0, e1);
+        if (T == best_T && C == best_C) continue;
+        pa_status gs = build_group_args(b, g, C, generations, T);
+        if (gs == PA_EUNSUPPORTED) continue;
+        if (gs != PA_OK) {
+          st = gs;
+          break;
+        }
+        float ms = 0.f;
+        time_all(&ms);
+        if (st == PA_OK && ms < best_ms) {
+          best_ms = ms;
+          best_C = C;
+          best_T = T;
+        }
       }
-      if (st != PA_OK) break;
-      if (best_ms < 0.f || ms < best_ms) {
-        best_ms = ms;
-        best_C = C;
-      }
-    }
-    if (st == PA_OK) st = build_group_args(b, g, best_C, 1);
+    if (st == PA_OK) st = build_group_args(b, g, best_C, generations, best_T);
     if (chosen && st == PA_OK) chosen[k] = best_C;
   }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
+  for (auto& g : b->groups)  // arguments of one generation until the next solve rebuilds them
+    if (st == PA_OK) st = build_group_args(b, g, g.C, 1, g.threads);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
   b->graph_G = -1;  // the captured graph used the previous shapes
   if (b->graph) {
     cudaGraphExecDestroy(b->graph);
@@ -388,11 +402,12 @@ pa_status pa_batch_tune(pa_batch* b, int32_t generations, int32_t* chosen) {
 }
 
 pa_status pa_batch_groups(pa_batch* b, int32_t* n_groups, int32_t* cluster_sizes,
-                          int32_t* group_of_instance) {
+                          int32_t* cta_threads, int32_t* group_of_instance) {
   if (!b) return PA_EINVAL;
   if (n_groups) *n_groups = (int32_t)b->groups.size();
   for (size_t k = 0; k < b->groups.size(); ++k) {
     if (cluster_sizes) cluster_sizes[k] = b->groups[k].C;
+    if (cta_threads) cta_threads[k] = b->groups[k].threads;
     if (group_of_instance)
       for (int i : b->groups[k].members) group_of_instance[i] = (int32_t)k;
   }
@@ -409,7 +424,7 @@ pa_status pa_batch_solve(pa_batch* b, int32_t generations, uint8_t* best_host, d
       b->graph = nullptr;
     }
     for (auto& g : b->groups) {
-      st = build_group_args(b, g, g.C, generations);
+      st = build_group_args(b, g, g.C, generations, g.threads);
       if (st != PA_OK) return bfail(b, st, "rebuilding batch arguments failed");
     }
     cudaGraph_t graph = nullptr;

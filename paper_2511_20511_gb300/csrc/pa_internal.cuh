@@ -135,14 +135,17 @@ cudaError_t launch_solve(pa_ctx* ctx, const uint8_t* pop_in, uint8_t* pop_out, i
                          void* fit_out, uint8_t* best_row, double* best_fit, cudaStream_t st);
 size_t solve_args_bytes();
 // latency: the one-instance kernel's column split (few concurrent
-// instances) instead of the throughput split
+// instances) instead of the throughput split; threads: CTA size, 1024 (one
+// CTA per SM) or 256 (four per SM)
 size_t solve_fill_args(const pa_ctx* ctx, int C, int gen0, int G, const uint8_t* pop_in,
                        uint8_t* pop_out, void* fit_out, uint8_t* best_row, double* best_fit,
-                       void* args_out, bool latency = false);
-int solve_batch_max_clusters(const pa_ctx* proto, int C, size_t smem, bool latency = false);
+                       void* args_out, bool latency = false, int threads = 1024);
+int solve_batch_max_clusters(const pa_ctx* proto, int C, size_t smem, bool latency = false,
+                             int threads = 1024);
 void solve_args_set_stamp(void* args, unsigned long long* stamp);
 cudaError_t launch_solve_batch(const pa_ctx* proto, int C, int clusters, const void* d_args, int n,
-                               int* d_counter, size_t smem, cudaStream_t st, bool latency = false);
+                               int* d_counter, size_t smem, cudaStream_t st, bool latency = false,
+                               int threads = 1024);
 // pa_ga.cu: seed many instances at once (a cluster of C CTAs each) from n
 // seed argument records (seed_args_bytes() each, filled by seed_fill_args
 // for that C) in device memory; smem = the largest seed_fill_args value

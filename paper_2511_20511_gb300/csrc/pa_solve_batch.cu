@@ -16,12 +16,16 @@ namespace pa {
 
 cudaError_t dispatch_batch_latency(const pa_ctx* proto, int C, int clusters, const void* d, int n,
                                    int* ctr, size_t smem, bool q, int* mc, cudaStream_t st);
+cudaError_t dispatch_batch_small(const pa_ctx* proto, int C, int clusters, const void* d, int n,
+                                 int* ctr, size_t smem, bool q, int* mc, cudaStream_t st);
 
-static cudaError_t dispatch_any(bool latency, const pa_ctx* proto, int C, int clusters,
-                                const SolveArgs* d, int n, int* ctr, size_t smem, bool q, int* mc,
-                                cudaStream_t st) {
-  return latency ? dispatch_batch_latency(proto, C, clusters, d, n, ctr, smem, q, mc, st)
-                 : dispatch_batch<kBatchMaxNP>(proto, C, clusters, d, n, ctr, smem, q, mc, st);
+static cudaError_t dispatch_any(bool latency, int threads, const pa_ctx* proto, int C,
+                                int clusters, const SolveArgs* d, int n, int* ctr, size_t smem,
+                                bool q, int* mc, cudaStream_t st) {
+  if (latency) return dispatch_batch_latency(proto, C, clusters, d, n, ctr, smem, q, mc, st);
+  if (threads == kSmallCtaThreads)
+    return dispatch_batch_small(proto, C, clusters, d, n, ctr, smem, q, mc, st);
+  return dispatch_batch<kBatchMaxNP, kSolveThreads>(proto, C, clusters, d, n, ctr, smem, q, mc, st);
 }
 
 size_t solve_args_bytes() { return sizeof(SolveArgs); }
@@ -31,10 +35,11 @@ size_t solve_args_bytes() { return sizeof(SolveArgs); }
 // does not fit in one CTA.
 size_t solve_fill_args(const pa_ctx* ctx, int C, int gen0, int G, const uint8_t* pop_in,
                        uint8_t* pop_out, void* fit_out, uint8_t* best_row, double* best_fit,
-                       void* args_out, bool latency) {
+                       void* args_out, bool latency, int threads) {
   const pa_config& c = ctx->cfg;
   if (C > c.N || ctx->t32.streamed) return 0;
-  const SolveShape s = solve_shape(ctx, C, latency ? kSoloMaxNP : kBatchMaxNP, kSolveThreads);
+  const SolveShape s = solve_shape(ctx, C, latency ? kSoloMaxNP : kBatchMaxNP,
+                                   threads == kSmallCtaThreads ? kSmallCtaThreads : kSolveThreads);
   if (s.smem > (size_t)kSmemBudget - 64 * 4 - 16) return 0;
   SolveArgs a{};
   a.pop_in = pop_in;
@@ -84,26 +89,26 @@ void solve_args_set_stamp(void* args, unsigned long long* stamp) {
 // proto's variant with this shared memory (0 when none).
 // Cached per (device, kernel variant, cluster size, shared memory): the
 // occupancy query costs host time on every scheduling tick otherwise.
-int solve_batch_max_clusters(const pa_ctx* proto, int C, size_t smem, bool latency) {
+int solve_batch_max_clusters(const pa_ctx* proto, int C, size_t smem, bool latency, int threads) {
   struct Key {
-    int dev, prec, fin, nj, vec, C, lat;
+    int dev, prec, fin, nj, vec, C, lat, thr;
     size_t smem;
     bool operator<(const Key& o) const {
-      return std::tie(dev, prec, fin, nj, vec, C, lat, smem) <
-             std::tie(o.dev, o.prec, o.fin, o.nj, o.vec, o.C, o.lat, o.smem);
+      return std::tie(dev, prec, fin, nj, vec, C, lat, thr, smem) <
+             std::tie(o.dev, o.prec, o.fin, o.nj, o.vec, o.C, o.lat, o.thr, o.smem);
     }
   };
   static std::map<Key, int> cache;
   static std::mutex mu;
   const Key k{proto->device, proto->cfg.prec, proto->cfg.mode, proto->t32.NJ, proto->t32.vec, C,
-              latency ? 1 : 0, smem};
+              latency ? 1 : 0, threads, smem};
   {
     std::lock_guard<std::mutex> lock(mu);
     auto it = cache.find(k);
     if (it != cache.end()) return it->second;
   }
   int m = 0;
-  if (dispatch_any(latency, proto, C, 1, nullptr, 0, nullptr, smem, true, &m, nullptr) !=
+  if (dispatch_any(latency, threads, proto, C, 1, nullptr, 0, nullptr, smem, true, &m, nullptr) !=
       cudaSuccess)
     return 0;
   std::lock_guard<std::mutex> lock(mu);
@@ -114,9 +119,10 @@ int solve_batch_max_clusters(const pa_ctx* proto, int C, size_t smem, bool laten
 // Persistent batched solve of n instances sharing proto's kernel variant:
 // d_args holds their SolveArgs (cluster size C), d_counter must be zero.
 cudaError_t launch_solve_batch(const pa_ctx* proto, int C, int clusters, const void* d_args, int n,
-                               int* d_counter, size_t smem, cudaStream_t st, bool latency) {
-  return dispatch_any(latency, proto, C, clusters, static_cast<const SolveArgs*>(d_args), n,
-                      d_counter, smem, false, nullptr, st);
+                               int* d_counter, size_t smem, cudaStream_t st, bool latency,
+                               int threads) {
+  return dispatch_any(latency, threads, proto, C, clusters, static_cast<const SolveArgs*>(d_args),
+                      n, d_counter, smem, false, nullptr, st);
 }
 
 }  // namespace pa

@@ -1,9 +1,11 @@
 // pa_solve_batch.cuh -- the persistent batched solve kernel (many
 // instances per launch, a thread-block cluster per instance at a time) and
 // its launch dispatch, templated on the column split of the evaluation
-// (MAXNP column pairs per thread at most): pa_solve_batch.cu instantiates
-// the throughput split, pa_solve_batch_lat.cu the one-instance (latency)
-// split, as separate translation units.
+// (MAXNP column pairs per thread at most) and the CTA size T:
+// pa_solve_batch.cu instantiates the throughput split with 1024-thread CTAs
+// (one per SM), pa_solve_batch_lat.cu the one-instance (latency) split,
+// pa_solve_batch_small.cu 256-thread CTAs (four instances per SM), as
+// separate translation units.
 #pragma once
 
 #include <algorithm>
@@ -96,10 +98,9 @@ cudaError_t run_solve_batch(int C, int clusters, const SolveArgs* d_args, int n,
   return e;
 }
 
-template <typename FT, int VEC, bool FIN, int MAXNP>
+template <typename FT, int VEC, bool FIN, int MAXNP, int T>
 cudaError_t pick_batch(int NJ, int C, int clusters, const SolveArgs* d, int n, int* ctr,
                        size_t smem, bool q, int* mc, cudaStream_t st) {
-  constexpr int T = kSolveThreads;
   switch (NJ) {
     case 4: return run_solve_batch<FT, 4, VEC, FIN, T, MAXNP>(C, clusters, d, n, ctr, smem, q, mc, st);
     case 8: return run_solve_batch<FT, 8, VEC, FIN, T, MAXNP>(C, clusters, d, n, ctr, smem, q, mc, st);
@@ -118,20 +119,20 @@ cudaError_t pick_batch(int NJ, int C, int clusters, const SolveArgs* d, int n, i
 }
 
 
-template <int MAXNP>
+template <int MAXNP, int T>
 cudaError_t dispatch_batch(const pa_ctx* proto, int C, int clusters, const SolveArgs* d, int n,
                            int* ctr, size_t smem, bool q, int* mc, cudaStream_t st) {
   const pa_config& c = proto->cfg;
   const bool fin = c.mode == PA_SINR_FINITE_M;
   if (c.prec == PA_FP64)
-    return run_solve_batch<double, 4, 2, false, kSolveThreads, MAXNP>(C, clusters, d, n, ctr, smem, q,
+    return run_solve_batch<double, 4, 2, false, T, MAXNP>(C, clusters, d, n, ctr, smem, q,
                                                                mc, st);
   const int NJ = proto->t32.NJ;
   if (proto->t32.vec == 2)
-    return fin ? pick_batch<float, 2, true, MAXNP>(NJ, C, clusters, d, n, ctr, smem, q, mc, st)
-               : pick_batch<float, 2, false, MAXNP>(NJ, C, clusters, d, n, ctr, smem, q, mc, st);
-  return fin ? pick_batch<float, 1, true, MAXNP>(NJ, C, clusters, d, n, ctr, smem, q, mc, st)
-             : pick_batch<float, 1, false, MAXNP>(NJ, C, clusters, d, n, ctr, smem, q, mc, st);
+    return fin ? pick_batch<float, 2, true, MAXNP, T>(NJ, C, clusters, d, n, ctr, smem, q, mc, st)
+               : pick_batch<float, 2, false, MAXNP, T>(NJ, C, clusters, d, n, ctr, smem, q, mc, st);
+  return fin ? pick_batch<float, 1, true, MAXNP, T>(NJ, C, clusters, d, n, ctr, smem, q, mc, st)
+             : pick_batch<float, 1, false, MAXNP, T>(NJ, C, clusters, d, n, ctr, smem, q, mc, st);
 }
 
 }  // namespace

@@ -9,7 +9,7 @@ namespace pa {
 
 cudaError_t dispatch_batch_latency(const pa_ctx* proto, int C, int clusters, const void* d, int n,
                                    int* ctr, size_t smem, bool q, int* mc, cudaStream_t st) {
-  return dispatch_batch<kSoloMaxNP>(proto, C, clusters, static_cast<const SolveArgs*>(d), n, ctr,
+  return dispatch_batch<kSoloMaxNP, kSolveThreads>(proto, C, clusters, static_cast<const SolveArgs*>(d), n, ctr,
                                     smem, q, mc, st);
 }
 

@@ -16,6 +16,7 @@ namespace pa {
 namespace {
 
 constexpr int kSolveThreads = 1024;
+constexpr int kSmallCtaThreads = 256;  // batched CTAs of the four-per-SM shape
 constexpr int kSmallE = 8;  // elites found by one warp in registers up to this E
 
 struct SolveArgs {

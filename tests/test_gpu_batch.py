@@ -77,6 +77,8 @@ def test_batch_equals_alone_and_tuning_keeps_results(B, oracle):
                 assert (rows[i] == ref["best"]).all() and fits[i] == ref["best_fit"]
         chosen = batch.tune(3)
         assert len(chosen) == len(sizes)
+        _, threads, _ = batch.group_shapes()
+        assert set(threads.tolist()) <= {256, 1024}
         rows2, fits2 = batch.solve(G)
         rows3, fits3 = batch.solve(G)  # graph replay
         for i in range(len(insts)):
@@ -100,5 +102,24 @@ def test_batch_load_replaces_an_instance(B):
                  bs_xy_mm=new["bs_xy_mm"])
         best, bf, _, _ = _alone(B, d, G)
         assert (rows[2] == best).all() and fits[2] == bf
+    finally:
+        batch.close()
+
+
+def test_batch_small_ctas_equal_alone(B):
+    """Every kernel-variant group forced to 256-thread CTAs (four per SM):
+    results still equal the solves alone, bit for bit."""
+    G = 8
+    insts = _mixed(B, 10, seed0=7)
+    batch = B.Batch(insts)
+    try:
+        rows0, fits0 = batch.solve(G)
+        batch.tune(2)
+        rows, fits = batch.solve(G)
+        for i in range(len(insts)):
+            assert (rows[i] == rows0[i]).all() and fits[i] == fits0[i]
+        for i, d in enumerate(insts):
+            best, bf, _, _ = _alone(B, d, G)
+            assert (rows[i] == best).all() and fits[i] == bf
     finally:
         batch.close()
