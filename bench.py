@@ -26,6 +26,7 @@ only; other ranks exit without work).
 """
 import argparse
 import csv
+import gc
 import json
 import os
 import statistics
@@ -646,13 +647,17 @@ def run_serving(B, inputs, rate=2000.0, seconds=10.0, G=40, N=64, tick=40, budge
     for i in range(min(8, n)):  # warm the slot pool and kernels
         srv.submit(-1 - i, shapes[i][0], shapes[i][1], 1, insts[i]["beta"],
                    insts[i]["user_xy_mm"], insts[i]["bs_xy_mm"])
-    while srv.stats()["completed"] < min(8, n):
-        srv.poll()
+    srv.run_until_idle()
+    # no cyclic-GC pauses inside the timed replays (the instances are tens of
+    # thousands of objects); the same for the plain replay below
+    gc.collect()
+    gc.freeze()
+    gc.disable()
     done_at = {}
     results = {}
     t0 = time.perf_counter()
     nxt = 0
-    ticks = 0
+    polls = 0
     while len(done_at) < n:
         now = time.perf_counter() - t0
         while nxt < n and arr[nxt] <= now:
@@ -661,14 +666,21 @@ def run_serving(B, inputs, rate=2000.0, seconds=10.0, G=40, N=64, tick=40, budge
                        insts[nxt]["bs_xy_mm"])
             nxt += 1
         done, active, pending = srv.poll()
-        ticks += 1
+        polls += 1
         tnow = time.perf_counter() - t0
         for rid, best, fit in done:
             if rid >= 0:
                 done_at[rid] = tnow
                 results[rid] = fit
-        if not done and active == 0 and pending == 0 and nxt < n:
-            time.sleep(max(0.0, arr[nxt] - (time.perf_counter() - t0)))
+        if not done:
+            # nothing finished: wait for a tick in flight, at most until the
+            # next arrival is due; with nothing in flight, sleep until then
+            until = (arr[nxt] - tnow) if nxt < n else 0.002
+            if active > 0:
+                srv.wait(int(max(0.0, min(until, 0.002)) * 1e6))
+            elif pending == 0 and nxt < n:
+                time.sleep(max(0.0, until))
+    gc.enable()
     served_lat = [done_at[i] - arr[i] for i in range(n)]
     served_span = max(done_at.values()) - arr[0]
     stats = srv.stats()
@@ -685,6 +697,8 @@ def run_serving(B, inputs, rate=2000.0, seconds=10.0, G=40, N=64, tick=40, budge
         ctxs[(L, K)].solve(G)
     plain_lat = []
     same = True
+    gc.collect()
+    gc.disable()
     t0 = time.perf_counter()
     for i in range(n):
         now = time.perf_counter() - t0
@@ -698,6 +712,8 @@ def run_serving(B, inputs, rate=2000.0, seconds=10.0, G=40, N=64, tick=40, budge
         plain_lat.append(time.perf_counter() - t0 - arr[i])
         same = same and bool(bf == results[i])
     plain_span = time.perf_counter() - t0 - arr[0]
+    gc.enable()
+    gc.unfreeze()
     for c in ctxs.values():
         c.close()
     ms = lambda x: 1e3 * x  # noqa: E731
@@ -705,7 +721,7 @@ def run_serving(B, inputs, rate=2000.0, seconds=10.0, G=40, N=64, tick=40, budge
             "population": N, "tick_generations": tick, "budget_bytes": budget,
             "served": {"p50_ms": ms(pct(served_lat, 50)), "p99_ms": ms(pct(served_lat, 99)),
                        "p999_ms": ms(pct(served_lat, 99.9)), "solves_per_s": n / served_span,
-                       "ticks": ticks, "slots": stats["slots"],
+                       "polls": polls, "slots": stats["slots"],
                        "slot_bytes": stats["used_bytes"]},
             "plain_sequential": {"p50_ms": ms(pct(plain_lat, 50)),
                                  "p99_ms": ms(pct(plain_lat, 99)),

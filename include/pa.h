@@ -357,14 +357,19 @@ const char* pa_batch_last_error(const pa_batch* b);
 
 /* ------------------------------------------------------------------------
  * Continuous-batching server.  Requests (one instance each) are queued by
- * pa_server_submit; each pa_server_poll runs one scheduling tick: queued
- * requests are admitted, in arrival order, into resident slots of their
- * (L, K) class while the device memory of the slots stays within the budget
- * (idle slots of other classes are destroyed when the next request needs
- * their memory), newly admitted slots are seeded (one launch), every active
- * slot advances by up to `tick` generations (one persistent launch per
- * kernel variant; populations stay resident between ticks), and requests
- * that reach `generations` are queued as completions.  A request's result
+ * pa_server_submit.  Each pa_server_poll (1) collects the ticks the GPU has
+ * finished, without waiting: their slots advance, and requests that reached
+ * `generations` are queued as completions; (2) admits queued requests, in
+ * arrival order, into resident slots of their (L, K) class while the device
+ * memory of the slots stays within the budget (idle slots of other classes
+ * are destroyed when the next request needs their memory); (3) launches one
+ * tick for every active slot that has none in flight: the newly admitted
+ * slots are seeded (one launch) and every slot of the tick advances by up
+ * to `tick` generations (one persistent launch per kernel variant;
+ * populations stay resident between ticks); (4) returns completions.  Up
+ * to four ticks are in flight at once on streams of their own, so a request
+ * admitted while another tick runs starts at once on the SMs it leaves
+ * free.  pa_server_wait blocks until a tick finishes.  A request's result
  * equals pa_solve's for the same instance, configuration and seed.  A
  * request whose admission fails (its slot cannot be created or loaded)
  * completes with that status; the others are not affected.  Not thread
@@ -398,8 +403,9 @@ pa_status pa_server_submit(pa_server* s, int64_t id, int32_t L, int32_t K, uint6
                            const int32_t* bs_xy_mm);
 
 /*
- * One scheduling tick (synchronous), then up to max_done completions are
- * returned in completion order (the rest wait for later polls): done_ids[i],
+ * One scheduling round (collect finished ticks, admit, launch; it does not
+ * wait for the GPU), then up to max_done completions are returned in
+ * completion order (the rest wait for later polls): done_ids[i],
  * done_status[i] (PA_OK, or why the request failed), their best member at
  * done_best + i*best_stride (L*K bytes; zeros for a failed request) and its
  * fitness done_fit[i] (NaN for a failed request) -- each output optional;
@@ -412,11 +418,18 @@ pa_status pa_server_poll(pa_server* s, int32_t max_done, int64_t* done_ids, int3
                          int32_t* n_done, int32_t* n_active, int32_t* n_pending);
 
 /*
+ * Block until the oldest tick in flight has finished (timeout_us < 0), or
+ * at most timeout_us microseconds; returns at once when none is in flight.
+ * The next pa_server_poll collects what finished.
+ */
+pa_status pa_server_wait(pa_server* s, int32_t timeout_us);
+
+/*
  * Withdraw request `id`: removed from the queue, or its slot released (the
- * slot stays resident for the next request of its class), or its unreturned
- * completion dropped.  No GPU work is in flight between polls, so this is
- * immediate.  PA_EINVAL when no queued, running or unreturned request has
- * this id.
+ * slot stays resident for the next request of its class; when a tick of it
+ * is in flight, once that tick has finished, and its result is dropped), or
+ * its unreturned completion dropped.  PA_EINVAL when no queued, running or
+ * unreturned request has this id.
  */
 pa_status pa_server_cancel(pa_server* s, int64_t id);
 

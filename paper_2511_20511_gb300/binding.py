@@ -91,6 +91,7 @@ _SIGS = {
                                  C.c_int64, C.c_void_p, C.POINTER(C.c_int32),
                                  C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
     "pa_server_cancel": (C.c_int, [C.c_void_p, C.c_int64]),
+    "pa_server_wait": (C.c_int, [C.c_void_p, C.c_int32]),
     "pa_server_inject_admission_failures": (C.c_int, [C.c_void_p, C.c_int32]),
     "pa_server_stats": (C.c_int, [C.c_void_p, C.POINTER(C.c_uint64), C.POINTER(C.c_int32),
                                   C.POINTER(C.c_int64)]),
@@ -533,6 +534,22 @@ class Server:
             out = [(int(self._ids[i]), self._best[i].copy(), float(self._fit[i]))
                    for i in range(k)]
         return out, na.value, npd.value
+
+    def wait(self, timeout_us=-1):
+        """Block until a tick in flight finishes (at most timeout_us when >= 0)."""
+        self._scheck(lib().pa_server_wait(self.handle, int(timeout_us)))
+
+    def run_until_idle(self, max_done=None, with_status=False):
+        """Poll (waiting for ticks in between) until nothing is queued or running;
+        returns every completion."""
+        out = []
+        while True:
+            done, active, pending = self.poll(max_done, with_status)
+            out += done
+            if not done and active == 0 and pending == 0:
+                return out
+            if not done:
+                self.wait()
 
     def cancel(self, rid):
         self._scheck(lib().pa_server_cancel(self.handle, int(rid)))

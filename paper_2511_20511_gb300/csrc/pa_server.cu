@@ -2,37 +2,43 @@
 //
 // Requests (one pilot-assignment instance each: L, K, gains, positions,
 // seed) arrive at any time through pa_server_submit.  Each pa_server_poll
-// runs one scheduling tick:
-//   1. admission: queued requests take free slots of their (L, K) class --
-//      a slot is a resident context (gains, tables, double-buffered
-//      population on the GPU); new slots are created while the device
-//      memory they need stays within the server's budget;
-//   2. the newly admitted slots are seeded in one batched launch;
-//   3. every active slot advances by up to `tick` generations in one
-//      persistent batched solve launch per kernel variant (populations stay
-//      resident between ticks; a slot reaching G generations also gets its
-//      final evaluation and best member);
-//   4. finished requests are copied back into a completion queue that
-//      polls drain (up to the caller's max_done per poll); their slots
-//      stay resident for the next request of the same class.
-// Requests that arrive while a tick runs join at the next tick, so work of
-// many requests overlaps on the device.  A request's result is exactly what
-// pa_solve gives for the same instance and seed alone: generations run in
-// the same order with the same draws, whatever the tick length or the mix.
+//   1. harvests the ticks that finished on the GPU (an event per tick, no
+//      waiting): their slots advance; requests that reached G generations
+//      are queued as completions and their slots stay resident for the next
+//      request of the same (L, K) class;
+//   2. admits queued requests, in arrival order, into resident slots of
+//      their class -- a slot is a resident context (gains, tables, double-
+//      buffered population on the GPU); new slots are created while the
+//      device memory they need stays within the server's budget (idle slots
+//      of other classes are destroyed when the next request needs their
+//      memory; at most four are created per poll);
+//   3. launches one tick for every active slot that has no tick in flight:
+//      the newly admitted ones are seeded (one launch), then each advances
+//      by up to `tick` generations in one persistent batched launch per
+//      kernel variant (side by side on side streams), and the best members
+//      of slots that finish are copied to pinned memory;
+//   4. returns queued completions.
+// Ticks run on a pool of streams, so a request admitted while another tick
+// is on the GPU starts at once on the SMs that tick leaves free instead of
+// waiting for it; pa_server_wait blocks until some tick finishes.  A
+// request's result is exactly what pa_solve gives for the same instance and
+// seed alone: generations run in the same order with the same draws,
+// whatever the tick length or the mix.
 //
 // Liveness: requests are checked at submit (shape, values, a slot of its
 // shape within the budget), so every queued request can eventually be
-// admitted; when the head of the queue needs memory, idle slots (of other
-// classes first) are destroyed; an admission that fails anyway completes
-// that request with the error and the queue moves on.  No C++ exception
-// crosses the C ABI: allocation failures return PA_ENOMEM.
+// admitted; an admission that fails anyway completes that request with the
+// error and the queue moves on.  No C++ exception crosses the C ABI:
+// allocation failures return PA_ENOMEM.
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstring>
 #include <deque>
 #include <map>
 #include <new>
 #include <string>
+#include <thread>
 #include <tuple>
 #include <vector>
 
@@ -44,11 +50,16 @@ bool config_ok(const pa_config* c, std::string* why);
 void f32_geometry(int L, int K, int* NJ, int* RS, int* vec);
 }
 
+namespace {
+constexpr int kTickPool = 4;     // ticks in flight at most
+constexpr int kMaxNewSlots = 4;  // contexts created per poll at most
+}  // namespace
+
 struct pa_server {
   pa_config base{};
   int G = 0, tick = 0;
   size_t budget = 0, used = 0;
-  cudaStream_t stream = nullptr;
+  cudaStream_t stream = nullptr;  // slot creation; ticks wait for it
   bool own_stream = false;
   struct Slot {
     pa_ctx* ctx = nullptr;  // null: destroyed (entry reusable)
@@ -56,8 +67,9 @@ struct pa_server {
     size_t bytes = 0;       // device bytes charged to the budget
     int64_t req = -1;
     int gen = 0;
-    bool active = false, fresh = false, failed = false;
-    int64_t best_off = 0;  // offset in the pinned results buffer
+    bool active = false, fresh = false;
+    int tick = -1;          // the tick in flight on this slot, or -1
+    bool cancelled = false; // withdrawn while its tick was in flight
   };
   std::vector<Slot> slots;
   std::map<std::pair<int, int>, std::vector<int>> free_slots;
@@ -78,28 +90,38 @@ struct pa_server {
   };
   std::deque<Done> done;   // completions not yet returned by a poll
   int inject_failures = 0; // testing: admissions still to fail
-  // pinned staging of the requests admitted in one tick (their uploads are
-  // asynchronous; the tick's final synchronisation ends them)
-  unsigned char* h_stage = nullptr;
-  size_t stage_cap = 0, stage_used = 0;
-  bool stage_busy = false;  // uploads from the staging buffer may be in flight
-  // per-tick device/pinned scratch
-  void* d_seed_args = nullptr;
-  void* h_seed_args = nullptr;
-  size_t seed_cap = 0;
-  void* d_solve_args = nullptr;
-  void* h_solve_args = nullptr;
-  size_t solve_cap = 0;
-  int* d_counters = nullptr;
-  int counters_cap = 0;
-  uint8_t* h_best = nullptr;  // pinned: best rows of finishing slots
-  double* h_bestfit = nullptr;
-  double* d_bestfit = nullptr;
-  size_t best_cap = 0, fit_cap = 0;
-  // side streams of the variant groups of a tick, with their events
-  std::vector<cudaStream_t> side;
-  std::vector<cudaEvent_t> joined;
-  cudaEvent_t fork = nullptr;
+  // One tick in flight: its stream and completion event, the slots it
+  // advances, and its own device/pinned scratch (ticks overlap).
+  struct Tick {
+    cudaStream_t st = nullptr;
+    cudaEvent_t ev = nullptr, fork = nullptr;
+    bool busy = false;
+    bool dirty = false;                // work enqueued by a launch that did not finish
+    uint64_t seq = 0;                  // launch order
+    std::vector<int> slots, g_now, finish_k;  // per slot: generations (-1: failed), index among finishing (-1)
+    std::vector<int> failed;           // slots whose group did not fit (complete with an error)
+    std::vector<int64_t> best_off;     // per finishing slot: offset in h_best
+    unsigned char* h_stage = nullptr;  // pinned uploads of this tick's admissions
+    size_t stage_cap = 0, stage_used = 0;
+    void* d_seed_args = nullptr;
+    void* h_seed_args = nullptr;
+    size_t seed_cap = 0;
+    void* d_solve_args = nullptr;
+    void* h_solve_args = nullptr;
+    size_t solve_cap = 0;
+    int* d_counters = nullptr;
+    size_t counters_cap = 0;
+    uint8_t* h_best = nullptr;
+    size_t best_cap = 0;
+    double* d_bestfit = nullptr;
+    double* h_bestfit = nullptr;
+    size_t fit_cap = 0;
+    std::vector<cudaStream_t> side;    // variant groups side by side
+    std::vector<cudaEvent_t> joined;
+  };
+  Tick ticks[kTickPool];
+  uint64_t tick_seq = 0;
+  std::vector<std::tuple<int, int, int, int>> prepared;  // kernel variants already loaded
   std::string err;
   int64_t completed = 0;
 };
@@ -155,19 +177,27 @@ size_t slot_bytes(const pa_config& c) {
   return b + 8 * 256;                            // allocation granularity slack
 }
 
+// Grow a device buffer (dev) and/or a pinned host buffer (host) to `need`
+// bytes (geometric growth: pinned allocations are slow).  Only called on a
+// tick that is not in flight.
 template <typename T>
-pa_status grow(pa_server* s, T** dev, T** host, size_t* cap, size_t need, bool pinned_host) {
+pa_status grow(pa_server* s, T** dev, T** host, size_t* cap, size_t need) {
   if (need <= *cap) return PA_OK;
-  size_t n = std::max(need, *cap * 2 + 64);
+  const size_t n = std::max(need, *cap * 2 + 64);
   if (dev) {
     cudaFree(*dev);
     *dev = nullptr;
+  }
+  if (host) {
+    cudaFreeHost(*host);
+    *host = nullptr;
+  }
+  *cap = 0;
+  if (dev) {
     pa_status st = scuda(s, cudaMalloc(dev, n), "cudaMalloc server scratch");
     if (st != PA_OK) return st;
   }
   if (host) {
-    if (pinned_host) cudaFreeHost(*host);
-    *host = nullptr;
     pa_status st = scuda(s, cudaMallocHost(host, n), "cudaMallocHost server scratch");
     if (st != PA_OK) return st;
   }
@@ -175,13 +205,15 @@ pa_status grow(pa_server* s, T** dev, T** host, size_t* cap, size_t need, bool p
   return PA_OK;
 }
 
-// Side stream k (created on first use).
-pa_status side_stream(pa_server* s, int k) {
-  if (!s->fork) {
-    pa_status st = scuda(s, cudaEventCreateWithFlags(&s->fork, cudaEventDisableTiming), "event");
+// Make sure tick t has a stream, events and k side streams.
+pa_status tick_streams(pa_server* s, pa_server::Tick& t, size_t k) {
+  if (!t.st) {
+    pa_status st = scuda(s, cudaStreamCreateWithFlags(&t.st, cudaStreamNonBlocking), "stream");
+    if (st == PA_OK) st = scuda(s, cudaEventCreateWithFlags(&t.ev, cudaEventDisableTiming), "event");
+    if (st == PA_OK) st = scuda(s, cudaEventCreateWithFlags(&t.fork, cudaEventDisableTiming), "event");
     if (st != PA_OK) return st;
   }
-  while ((int)s->side.size() <= k) {
+  while (t.side.size() < k) {
     cudaStream_t x = nullptr;
     cudaEvent_t e = nullptr;
     pa_status st = scuda(s, cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking), "stream");
@@ -191,8 +223,8 @@ pa_status side_stream(pa_server* s, int k) {
       cudaStreamDestroy(x);
       return st;
     }
-    s->side.push_back(x);
-    s->joined.push_back(e);
+    t.side.push_back(x);
+    t.joined.push_back(e);
   }
   return PA_OK;
 }
@@ -210,6 +242,19 @@ void complete(pa_server* s, int64_t id, pa_status st, int L, int K, const uint8_
   d.fit = st == PA_OK ? fit : std::nan("");
   s->done.push_back(std::move(d));
   ++s->completed;
+}
+
+// A slot is idle again: back to its class's free list (its context on the
+// server stream, so that destroying it never waits for a tick stream).
+void release(pa_server* s, int i) {
+  pa_server::Slot& sl = s->slots[i];
+  sl.active = false;
+  sl.fresh = false;
+  sl.cancelled = false;
+  sl.req = -1;
+  sl.tick = -1;
+  sl.ctx->stream = s->stream;
+  s->free_slots[std::make_pair(sl.L, sl.K)].push_back(i);
 }
 
 // Destroy one idle slot and give its memory back to the budget.
@@ -237,21 +282,107 @@ bool make_room(pa_server* s, size_t need, std::pair<int, int> key) {
 
 void destroy_server(pa_server* s) {
   if (!s) return;
-  for (auto x : s->side) cudaStreamDestroy(x);
-  for (auto e : s->joined) cudaEventDestroy(e);
-  if (s->fork) cudaEventDestroy(s->fork);
-  for (auto& sl : s->slots) pa_destroy(sl.ctx);
-  cudaFree(s->d_seed_args);
-  cudaFreeHost(s->h_seed_args);
-  cudaFree(s->d_solve_args);
-  cudaFreeHost(s->h_solve_args);
-  cudaFree(s->d_counters);
-  cudaFreeHost(s->h_best);
-  cudaFreeHost(s->h_bestfit);
-  cudaFreeHost(s->h_stage);
-  cudaFree(s->d_bestfit);
+  // drain every tick, then destroy the slot contexts (whose stream may still
+  // name a tick stream), then the ticks' streams and buffers
+  for (auto& t : s->ticks)
+    if (t.st) cudaStreamSynchronize(t.st);
+  for (auto& sl : s->slots)
+    if (sl.ctx) {
+      sl.ctx->stream = s->stream;
+      pa_destroy(sl.ctx);
+      sl.ctx = nullptr;
+    }
+  for (auto& t : s->ticks) {
+    for (auto x : t.side) cudaStreamDestroy(x);
+    for (auto e : t.joined) cudaEventDestroy(e);
+    if (t.st) cudaStreamDestroy(t.st);
+    if (t.ev) cudaEventDestroy(t.ev);
+    if (t.fork) cudaEventDestroy(t.fork);
+    cudaFreeHost(t.h_stage);
+    cudaFree(t.d_seed_args);
+    cudaFreeHost(t.h_seed_args);
+    cudaFree(t.d_solve_args);
+    cudaFreeHost(t.h_solve_args);
+    cudaFree(t.d_counters);
+    cudaFreeHost(t.h_best);
+    cudaFree(t.d_bestfit);
+    cudaFreeHost(t.h_bestfit);
+  }
   if (s->own_stream) cudaStreamDestroy(s->stream);
   delete s;
+}
+
+// First slot of a kernel variant: load every batched-kernel shape a tick
+// may choose for it (both column splits, every cluster size) and cache
+// their occupancy now -- loading a kernel on its first launch would stall a
+// tick by tens of milliseconds.
+void prepare_variant(pa_server* s, const pa_ctx* c) {
+  const auto key = std::make_tuple(c->cfg.prec, c->cfg.mode, c->t32.NJ, c->t32.vec);
+  if (std::find(s->prepared.begin(), s->prepared.end(), key) != s->prepared.end()) return;
+  s->prepared.push_back(key);
+  std::vector<unsigned char> args(pa::solve_args_bytes());
+  for (bool latency : {true, false})
+    for (int C : {16, 8, 4, 2, 1}) {
+      const size_t smem = pa::solve_fill_args(c, C, 0, 1, nullptr, nullptr, nullptr, nullptr,
+                                              nullptr, args.data(), latency);
+      if (smem) (void)pa::solve_batch_max_clusters(c, C, smem, latency);
+    }
+  (void)cudaGetLastError();
+}
+
+// Bytes of pinned staging for one request's upload, 16-byte aligned parts.
+size_t stage_bytes(const pa_server::Req& r) {
+  auto al = [](size_t x) { return (x + 15) & ~size_t(15); };
+  return al(8 * r.beta.size()) + al(4 * r.uxy.size()) + al(4 * r.bxy.size());
+}
+
+// A tick whose event has fired: advance its slots, queue the finished
+// requests, release their slots.
+void finalize(pa_server* s, pa_server::Tick& t) {
+  for (size_t m = 0; m < t.slots.size(); ++m) {
+    if (t.g_now[m] < 0) continue;  // its group failed: below
+    const int i = t.slots[m];
+    pa_server::Slot& sl = s->slots[i];
+    sl.tick = -1;
+    sl.fresh = false;
+    sl.gen += t.g_now[m];
+    sl.ctx->cur ^= 1;
+    sl.ctx->generation = sl.gen;
+    const int k = t.finish_k[m];
+    if (sl.cancelled) {
+      release(s, i);
+    } else if (k >= 0) {
+      complete(s, sl.req, PA_OK, sl.L, sl.K, t.h_best + t.best_off[k], t.h_bestfit[k]);
+      release(s, i);
+    }
+  }
+  for (int i : t.failed) {  // released without a result
+    pa_server::Slot& sl = s->slots[i];
+    if (!sl.cancelled) complete(s, sl.req, PA_EUNSUPPORTED, sl.L, sl.K, nullptr, 0.0);
+    release(s, i);
+  }
+  t.slots.clear();
+  t.failed.clear();
+  t.busy = false;
+}
+
+// Harvest every finished tick, in launch order among them (ticks hold
+// disjoint slots and may finish out of order).
+pa_status harvest(pa_server* s) {
+  pa_server::Tick* fin[kTickPool];
+  int nf = 0;
+  for (auto& t : s->ticks) {
+    if (!t.busy) continue;
+    const cudaError_t q = cudaEventQuery(t.ev);
+    if (q == cudaErrorNotReady) continue;
+    if (q != cudaSuccess) return scuda(s, q, "tick");
+    fin[nf++] = &t;
+  }
+  std::sort(fin, fin + nf, [](const pa_server::Tick* a, const pa_server::Tick* b) {
+    return a->seq < b->seq;
+  });
+  for (int k = 0; k < nf; ++k) finalize(s, *fin[k]);
+  return PA_OK;
 }
 
 }  // namespace
@@ -290,6 +421,23 @@ pa_status pa_server_create(const pa_config* base, int32_t generations, int32_t t
       return PA_ECUDA;
     }
     s->own_stream = true;
+  }
+  // the tick pool's streams, events and first buffers now, not on a poll
+  // (pinned allocations take milliseconds)
+  for (auto& t : s->ticks) {
+    pa_status st = tick_streams(s, t, 2);
+    if (st == PA_OK) st = grow<void>(s, &t.d_seed_args, &t.h_seed_args, &t.seed_cap, 16 << 10);
+    if (st == PA_OK) st = grow<void>(s, &t.d_solve_args, &t.h_solve_args, &t.solve_cap, 64 << 10);
+    if (st == PA_OK) st = grow<int>(s, &t.d_counters, nullptr, &t.counters_cap, 256);
+    if (st == PA_OK) st = grow<uint8_t>(s, nullptr, &t.h_best, &t.best_cap, 64 << 10);
+    if (st == PA_OK) st = grow<double>(s, &t.d_bestfit, &t.h_bestfit, &t.fit_cap, 4 << 10);
+    if (st == PA_OK && cudaMallocHost(&t.h_stage, (size_t)4 << 20) == cudaSuccess)
+      t.stage_cap = (size_t)4 << 20;
+    if (st != PA_OK) {
+      pa::set_thread_error(s->err);
+      destroy_server(s);
+      return st;
+    }
   }
   *out = s;
   return PA_OK;
@@ -355,7 +503,8 @@ pa_status pa_server_poll(pa_server* s, int32_t max_done, int64_t* done_ids, int3
   *n_done = 0;
   pa_status st;
   try {
-    st = tick_impl(s);
+    st = harvest(s);
+    if (st == PA_OK) st = tick_impl(s);
   } catch (const std::bad_alloc&) {
     st = sfail(s, PA_ENOMEM, "host memory during a tick");
   } catch (...) {
@@ -381,6 +530,23 @@ pa_status pa_server_poll(pa_server* s, int32_t max_done, int64_t* done_ids, int3
   return st;
 }
 
+pa_status pa_server_wait(pa_server* s, int32_t timeout_us) {
+  if (!s) return PA_EINVAL;
+  pa_server::Tick* oldest = nullptr;
+  for (auto& t : s->ticks)
+    if (t.busy && (!oldest || t.seq < oldest->seq)) oldest = &t;
+  if (!oldest) return PA_OK;
+  if (timeout_us < 0) return scuda(s, cudaEventSynchronize(oldest->ev), "tick wait");
+  const auto t_end = std::chrono::steady_clock::now() + std::chrono::microseconds(timeout_us);
+  for (;;) {
+    const cudaError_t q = cudaEventQuery(oldest->ev);
+    if (q == cudaSuccess) return PA_OK;
+    if (q != cudaErrorNotReady) return scuda(s, q, "tick");
+    if (std::chrono::steady_clock::now() >= t_end) return PA_OK;
+    std::this_thread::yield();
+  }
+}
+
 pa_status pa_server_cancel(pa_server* s, int64_t id) {
   if (!s) return PA_EINVAL;
   for (auto it = s->pending.begin(); it != s->pending.end(); ++it)
@@ -390,11 +556,11 @@ pa_status pa_server_cancel(pa_server* s, int64_t id) {
     }
   for (size_t i = 0; i < s->slots.size(); ++i) {
     pa_server::Slot& sl = s->slots[i];
-    if (sl.ctx && sl.active && sl.req == id) {
-      sl.active = false;
-      sl.fresh = false;
-      sl.req = -1;
-      s->free_slots[std::make_pair(sl.L, sl.K)].push_back((int)i);
+    if (sl.ctx && sl.active && !sl.cancelled && sl.req == id) {
+      if (sl.tick >= 0)
+        sl.cancelled = true;  // released when its tick has finished
+      else
+        release(s, (int)i);
       return PA_OK;
     }
   }
@@ -412,43 +578,55 @@ pa_status pa_server_inject_admission_failures(pa_server* s, int32_t count) {
   return PA_OK;
 }
 
-}  // extern "C"
-
-// Bytes of pinned staging for one request's upload, 16-byte aligned parts.
-static size_t stage_bytes(const pa_server::Req& r) {
-  auto al = [](size_t x) { return (x + 15) & ~size_t(15); };
-  return al(8 * r.beta.size()) + al(4 * r.uxy.size()) + al(4 * r.bxy.size());
+pa_status pa_server_stats(const pa_server* s, uint64_t* used_bytes, int32_t* n_slots,
+                          int64_t* completed) {
+  if (!s) return PA_EINVAL;
+  if (used_bytes) *used_bytes = s->used;
+  if (n_slots) {
+    int n = 0;
+    for (auto& sl : s->slots) n += sl.ctx ? 1 : 0;
+    *n_slots = n;
+  }
+  if (completed) *completed = s->completed;
+  return PA_OK;
 }
 
+}  // extern "C"
+
+// Admission into free slots and one tick for every idle active slot, on a
+// tick of the pool that is not in flight (none free: the next poll).
 static pa_status tick_impl(pa_server* s) {
-  pa_status st = PA_OK;
-  // pinned staging for this tick's admissions (grown between ticks only:
-  // earlier uploads of this tick may still read the old buffer otherwise;
-  // a tick that failed before its final synchronisation may have left
-  // uploads in flight)
-  if (s->stage_busy) {
-    st = scuda(s, cudaStreamSynchronize(s->stream), "staging sync");
+  pa_server::Tick* tp = nullptr;
+  for (auto& t : s->ticks)
+    if (!t.busy) {
+      tp = &t;
+      break;
+    }
+  if (!tp) return PA_OK;
+  pa_server::Tick& t = *tp;
+  pa_status st = tick_streams(s, t, 0);
+  if (st != PA_OK) return st;
+  if (t.dirty) {  // an earlier launch on this tick failed midway: let its work drain
+    st = scuda(s, cudaStreamSynchronize(t.st), "tick drain");
     if (st != PA_OK) return st;
-    s->stage_busy = false;
+    t.dirty = false;
   }
+  // pinned staging for this tick's admissions
   {
     size_t need = 0;
     for (const auto& r : s->pending) need += stage_bytes(r);
     need = std::min(need, (size_t)64 << 20);
-    if (need > s->stage_cap) {  // rare: 4 MB first, then doubling (pinned allocations are slow)
-      const size_t cap = std::max({need, 2 * s->stage_cap, (size_t)16 << 20});
-      cudaFreeHost(s->h_stage);
-      s->h_stage = nullptr;
-      s->stage_cap = 0;
-      if (cudaMallocHost(&s->h_stage, cap) == cudaSuccess) s->stage_cap = cap;
+    if (need > t.stage_cap) {  // doubling (4 MB at creation)
+      const size_t cap = std::max({need, 2 * t.stage_cap, (size_t)16 << 20});
+      cudaFreeHost(t.h_stage);
+      t.h_stage = nullptr;
+      t.stage_cap = 0;
+      if (cudaMallocHost(&t.h_stage, cap) == cudaSuccess) t.stage_cap = cap;
       else (void)cudaGetLastError();
     }
-    s->stage_used = 0;
+    t.stage_used = 0;
   }
-  // ---- 1. admission, in arrival order; at most kMaxNewSlots contexts are
-  // created per tick (creating one allocates and synchronises), so a burst
-  // of new classes or a backlog cannot stall one tick for everyone
-  constexpr int kMaxNewSlots = 4;
+  // ---- admission, in arrival order
   int created_now = 0;
   std::vector<int> fresh;
   while (!s->pending.empty()) {
@@ -462,7 +640,7 @@ static pa_status tick_impl(pa_server* s) {
       slot = fl.back();
       fl.pop_back();
     } else {
-      if (created_now == kMaxNewSlots) break;  // the next tick creates more
+      if (created_now == kMaxNewSlots) break;  // the next poll creates more
       const size_t need = slot_bytes(c);
       if (!make_room(s, need, key)) break;  // wait for running slots to finish
       ++created_now;
@@ -489,6 +667,7 @@ static pa_status tick_impl(pa_server* s) {
         s->slots.emplace_back();
         slot = (int)s->slots.size() - 1;
       }
+      prepare_variant(s, ctx);
       pa_server::Slot& ns = s->slots[slot];
       ns = pa_server::Slot();
       ns.ctx = ctx;
@@ -499,37 +678,36 @@ static pa_status tick_impl(pa_server* s) {
       created = true;
     }
     pa_server::Slot& sl = s->slots[slot];
+    sl.ctx->stream = t.st;
+    sl.ctx->cfg.seed = r.seed;
     pa_status ls = PA_OK;
-    if (created) {  // pa_create uploaded this request's instance already
-      sl.ctx->cfg.seed = r.seed;
-    } else if (s->inject_failures > 0) {
+    if (!created && s->inject_failures > 0) {
       --s->inject_failures;
       ls = PA_ECUDA;
       s->err = "injected admission failure";
-    } else {
-      sl.ctx->cfg.seed = r.seed;
+    } else if (!created) {  // pa_create uploaded a new slot's instance already
       const double* beta = r.beta.data();
       const int32_t* uxy = r.uxy.data();
       const int32_t* bxy = r.bxy.data();
       const size_t sb = stage_bytes(r);
-      if (s->stage_used + sb <= s->stage_cap) {  // else the pageable copy (synchronous upload)
-        unsigned char* h = s->h_stage + s->stage_used;
+      if (t.stage_used + sb <= t.stage_cap) {  // else the pageable copy (synchronous upload)
+        unsigned char* h = t.h_stage + t.stage_used;
         const size_t nb = 8 * r.beta.size(), nu = 4 * r.uxy.size();
+        const size_t ob = (nb + 15) & ~size_t(15), ou = (nu + 15) & ~size_t(15);
         std::memcpy(h, beta, nb);
-        std::memcpy(h + ((nb + 15) & ~size_t(15)), uxy, nu);
-        std::memcpy(h + ((nb + 15) & ~size_t(15)) + ((nu + 15) & ~size_t(15)), bxy,
-                    4 * r.bxy.size());
+        std::memcpy(h + ob, uxy, nu);
+        std::memcpy(h + ob + ou, bxy, 4 * r.bxy.size());
         beta = reinterpret_cast<const double*>(h);
-        uxy = reinterpret_cast<const int32_t*>(h + ((nb + 15) & ~size_t(15)));
-        bxy = reinterpret_cast<const int32_t*>(h + ((nb + 15) & ~size_t(15)) +
-                                               ((nu + 15) & ~size_t(15)));
-        s->stage_used += sb;
-        s->stage_busy = true;
+        uxy = reinterpret_cast<const int32_t*>(h + ob);
+        bxy = reinterpret_cast<const int32_t*>(h + ob + ou);
+        t.stage_used += sb;
       }
+      t.dirty = true;  // uploads enqueued on the tick's stream
       ls = pa_load_instance(sl.ctx, beta, uxy, bxy);
       if (ls != PA_OK) s->err = pa_last_error(sl.ctx);
     }
     if (ls != PA_OK) {  // the slot stays usable for later requests
+      sl.ctx->stream = s->stream;
       fl.push_back(slot);
       complete(s, r.id, ls, r.L, r.K, nullptr, 0.0);
       s->pending.pop_front();
@@ -539,89 +717,104 @@ static pa_status tick_impl(pa_server* s) {
     sl.gen = 0;
     sl.active = true;
     sl.fresh = true;
-    sl.failed = false;
+    sl.cancelled = false;
     sl.ctx->cur = 0;
     fresh.push_back(slot);
     s->pending.pop_front();
   }
-  // ---- 2. seed the new slots
-  if (!fresh.empty()) {
-    const size_t sb = pa::seed_args_bytes();
-    unsigned char* h = nullptr;
-    st = grow<void>(s, &s->d_seed_args, &s->h_seed_args, &s->seed_cap, sb * fresh.size(), true);
-    if (st != PA_OK) return st;
-    h = static_cast<unsigned char*>(s->h_seed_args);
-    size_t smem = 0;
-    const int sc = pa::seed_batch_cluster((int)fresh.size());
-    for (size_t i = 0; i < fresh.size(); ++i)
-      smem = std::max(smem, pa::seed_fill_args(s->slots[fresh[i]].ctx, h + sb * i, sc));
-    st = scuda(s, cudaMemcpyAsync(s->d_seed_args, h, sb * fresh.size(), cudaMemcpyHostToDevice,
-                                  s->stream),
-               "copy seed args");
-    if (st == PA_OK)
-      st = scuda(s, pa::launch_seed_batch(s->d_seed_args, (int)fresh.size(), smem, sc, s->stream),
-                 "seed kernel");
-    if (st != PA_OK) return st;
-    for (int i : fresh) s->slots[i].fresh = false;
-  }
-  // ---- 3. one tick of generations for every active slot, grouped by variant
+  // ---- the slots this tick advances: every active slot without a tick in flight
   std::map<std::tuple<int, int, int>, std::vector<int>> groups;
   int n_act = 0;
   for (size_t i = 0; i < s->slots.size(); ++i) {
     const auto& sl = s->slots[i];
     if (!sl.active || !sl.ctx) continue;
     ++n_act;
+    if (sl.tick >= 0) continue;
     const pa_ctx* c = sl.ctx;
     groups[std::make_tuple(c->t32.NJ, c->t32.vec, c->cfg.prec)].push_back((int)i);
   }
+  if (groups.empty()) return PA_OK;
+  const int t_index = (int)(&t - s->ticks);
+  // the tick waits for the slot creations and uploads on the server stream
+  t.dirty = true;
+  st = scuda(s, cudaEventRecord(t.fork, s->stream), "order");
+  if (st == PA_OK) st = scuda(s, cudaStreamWaitEvent(t.st, t.fork, 0), "order wait");
+  if (st != PA_OK) return st;
+  // ---- seed the new slots (one launch)
+  if (!fresh.empty()) {
+    const size_t sb = pa::seed_args_bytes();
+    st = grow<void>(s, &t.d_seed_args, &t.h_seed_args, &t.seed_cap, sb * fresh.size());
+    if (st != PA_OK) return st;
+    unsigned char* h = static_cast<unsigned char*>(t.h_seed_args);
+    size_t smem = 0;
+    const int sc = pa::seed_batch_cluster((int)fresh.size());
+    for (size_t i = 0; i < fresh.size(); ++i)
+      smem = std::max(smem, pa::seed_fill_args(s->slots[fresh[i]].ctx, h + sb * i, sc));
+    st = scuda(s, cudaMemcpyAsync(t.d_seed_args, h, sb * fresh.size(), cudaMemcpyHostToDevice,
+                                  t.st),
+               "copy seed args");
+    if (st == PA_OK)
+      st = scuda(s, pa::launch_seed_batch(t.d_seed_args, (int)fresh.size(), smem, sc, t.st),
+                 "seed kernel");
+    if (st != PA_OK) return st;
+  }
+  // ---- one persistent launch per variant group, side by side
+  size_t n_tick = 0;
+  for (auto& kv : groups) n_tick += kv.second.size();
   const size_t ab = pa::solve_args_bytes();
-  st = grow<void>(s, &s->d_solve_args, &s->h_solve_args, &s->solve_cap, ab * std::max(1, n_act),
-                  true);
+  st = grow<void>(s, &t.d_solve_args, &t.h_solve_args, &t.solve_cap, ab * n_tick);
+  if (st == PA_OK) st = grow<int>(s, &t.d_counters, nullptr, &t.counters_cap, sizeof(int) * groups.size());
+  if (st == PA_OK) st = tick_streams(s, t, groups.size() > 1 ? groups.size() : 0);
   if (st != PA_OK) return st;
-  if (s->counters_cap < (int)groups.size()) {
-    cudaFree(s->d_counters);
-    s->d_counters = nullptr;
-    st = scuda(s, cudaMalloc(&s->d_counters, sizeof(int) * std::max<size_t>(1, groups.size())),
-               "cudaMalloc counters");
-    if (st != PA_OK) return st;
-    s->counters_cap = (int)groups.size();
-  }
-  // results of slots finishing this tick: rows in a pinned buffer, fitness
-  // through a device array
-  std::vector<int> finishing;
+  t.slots.clear();
+  t.g_now.clear();
+  t.finish_k.clear();
+  t.best_off.clear();
+  t.failed.clear();
   int64_t best_total = 0;
+  int n_fin = 0;
   for (auto& kv : groups)
-    for (int i : kv.second)
-      if (s->slots[i].gen + s->tick >= s->G) {
-        finishing.push_back(i);
-        s->slots[i].best_off = best_total;
-        best_total += (int64_t)s->slots[i].L * s->slots[i].K;
+    for (int i : kv.second) {
+      const pa_server::Slot& sl = s->slots[i];
+      const int g_now = std::min(s->tick, s->G - sl.gen);
+      t.slots.push_back(i);
+      t.g_now.push_back(g_now);
+      if (sl.gen + g_now >= s->G) {
+        t.finish_k.push_back(n_fin++);
+        t.best_off.push_back(best_total);
+        best_total += (int64_t)sl.L * sl.K;
+      } else {
+        t.finish_k.push_back(-1);
       }
-  st = grow<uint8_t>(s, nullptr, &s->h_best, &s->best_cap, std::max<int64_t>(1, best_total), true);
-  if (st != PA_OK) return st;
-  st = grow<double>(s, &s->d_bestfit, &s->h_bestfit, &s->fit_cap,
-                    sizeof(double) * std::max<size_t>(1, finishing.size()), true);
-  if (st != PA_OK) return st;
-  std::map<int, int> fin_index;
-  for (size_t k = 0; k < finishing.size(); ++k) fin_index[finishing[k]] = (int)k;
-  if (!groups.empty()) {
-    st = scuda(s, cudaMemsetAsync(s->d_counters, 0, sizeof(int) * groups.size(), s->stream),
+    }
+  st = grow<uint8_t>(s, nullptr, &t.h_best, &t.best_cap, (size_t)std::max<int64_t>(1, best_total));
+  if (st == PA_OK)
+    st = grow<double>(s, &t.d_bestfit, &t.h_bestfit, &t.fit_cap,
+                      sizeof(double) * std::max(1, n_fin));
+  if (st == PA_OK)
+    st = scuda(s, cudaMemsetAsync(t.d_counters, 0, sizeof(int) * groups.size(), t.st),
                "reset counters");
-    if (st != PA_OK) return st;
-  }
-  unsigned char* ha = static_cast<unsigned char*>(s->h_solve_args);
+  if (st != PA_OK) return st;
+  std::map<int, size_t> pos_of;  // slot -> position in t.slots
+  for (size_t m = 0; m < t.slots.size(); ++m) pos_of[t.slots[m]] = m;
+  unsigned char* ha = static_cast<unsigned char*>(t.h_solve_args);
   size_t a_off = 0;
   int gk = 0;
+  const bool forked = groups.size() > 1;
+  if (forked) {
+    st = scuda(s, cudaEventRecord(t.fork, t.st), "fork");
+    if (st != PA_OK) return st;
+  }
   for (auto& kv : groups) {
     const std::vector<int>& mem = kv.second;
     const pa_ctx* proto = s->slots[mem[0]].ctx;
     // cluster size: the largest that keeps every active slot resident at
-    // once (16 CTAs for up to 9 slots on 152 SMs), smaller if it cannot fit
-    int C = 16;
-    while (C > 1 && n_act * C > proto->num_sms) C /= 2;
+    // once (16 CTAs for up to 9 slots on 152 SMs), smaller if it cannot fit;
     // while every active slot has 16 CTAs of its own, generations are
     // latency-bound: the one-instance kernel's column split, else the
     // throughput split
+    int C = 16;
+    while (C > 1 && n_act * C > proto->num_sms) C /= 2;
     bool latency = C == 16;
     size_t smem = 0;
     bool ok = false;
@@ -630,13 +823,14 @@ static pa_status tick_impl(pa_server* s) {
       smem = 0;
       for (size_t m = 0; m < mem.size(); ++m) {
         pa_server::Slot& sl = s->slots[mem[m]];
-        const int g_now = std::min(s->tick, s->G - sl.gen);
-        const bool fin = sl.gen + g_now >= s->G;
-        uint8_t* best_row = fin ? sl.ctx->best_row : nullptr;
-        double* best_fit = fin ? s->d_bestfit + fin_index[mem[m]] : nullptr;
-        const size_t need = pa::solve_fill_args(sl.ctx, C, sl.gen, g_now, sl.ctx->pop[sl.ctx->cur],
-                                                sl.ctx->pop[sl.ctx->cur ^ 1], sl.ctx->fit, best_row,
-                                                best_fit, ha + a_off + ab * m, latency);
+        const size_t p = pos_of[mem[m]];
+        const int k = t.finish_k[p];
+        uint8_t* best_row = k >= 0 ? sl.ctx->best_row : nullptr;
+        double* best_fit = k >= 0 ? t.d_bestfit + k : nullptr;
+        const size_t need = pa::solve_fill_args(sl.ctx, C, sl.gen, t.g_now[p],
+                                                sl.ctx->pop[sl.ctx->cur],
+                                                sl.ctx->pop[sl.ctx->cur ^ 1], sl.ctx->fit,
+                                                best_row, best_fit, ha + a_off + ab * m, latency);
         if (need == 0) {
           ok = false;
           break;
@@ -651,95 +845,57 @@ static pa_status tick_impl(pa_server* s) {
       }
     }
     if (!ok) {  // cannot happen for shapes checked at submit; fail these requests only
-      for (int i : mem) s->slots[i].failed = true;
+      for (int i : mem) {
+        t.failed.push_back(i);
+        t.g_now[pos_of[i]] = -1;
+      }
       continue;
     }
     const int clusters =
         std::min<int>((int)mem.size(), pa::solve_batch_max_clusters(proto, C, smem, latency));
-    unsigned char* dargs = static_cast<unsigned char*>(s->d_solve_args) + a_off;
-    st = scuda(s, cudaMemcpyAsync(dargs, ha + a_off, ab * mem.size(), cudaMemcpyHostToDevice,
-                                  s->stream),
-               "copy solve args");
-    // one group runs on the server stream itself; several run side by side,
-    // group k on side stream k, forked from and joined back into it
-    const bool forked = groups.size() > 1;
-    if (st == PA_OK && forked) st = side_stream(s, gk);
-    if (st == PA_OK && forked) st = scuda(s, cudaEventRecord(s->fork, s->stream), "fork");
-    if (st == PA_OK && forked)
-      st = scuda(s, cudaStreamWaitEvent(s->side[gk], s->fork, 0), "fork wait");
+    unsigned char* dargs = static_cast<unsigned char*>(t.d_solve_args) + a_off;
+    cudaStream_t gs = forked ? t.side[gk] : t.st;
+    if (forked) st = scuda(s, cudaStreamWaitEvent(gs, t.fork, 0), "fork wait");
+    if (st == PA_OK)
+      st = scuda(s, cudaMemcpyAsync(dargs, ha + a_off, ab * mem.size(), cudaMemcpyHostToDevice,
+                                    gs),
+                 "copy solve args");
     if (st == PA_OK)
       st = scuda(s, pa::launch_solve_batch(proto, C, clusters, dargs, (int)mem.size(),
-                                           s->d_counters + gk, smem,
-                                           forked ? s->side[gk] : s->stream, latency),
+                                           t.d_counters + gk, smem, gs, latency),
                  "batched solve kernel");
-    if (st == PA_OK && forked) st = scuda(s, cudaEventRecord(s->joined[gk], s->side[gk]), "join");
+    if (st == PA_OK && forked) st = scuda(s, cudaEventRecord(t.joined[gk], gs), "join");
     if (st != PA_OK) return st;
     a_off += ab * mem.size();
     ++gk;
   }
-  if (groups.size() > 1)
+  if (forked)
     for (int k = 0; k < gk; ++k) {
-      st = scuda(s, cudaStreamWaitEvent(s->stream, s->joined[k], 0), "join wait");
+      st = scuda(s, cudaStreamWaitEvent(t.st, t.joined[k], 0), "join wait");
       if (st != PA_OK) return st;
     }
-  // ---- 4. collect finished requests
-  for (int i : finishing) {
-    pa_server::Slot& sl = s->slots[i];
-    if (sl.failed) continue;
-    st = scuda(s, cudaMemcpyAsync(s->h_best + sl.best_off, sl.ctx->best_row,
-                                  (size_t)sl.L * sl.K, cudaMemcpyDeviceToHost, s->stream),
+  // ---- results of finishing slots to pinned memory
+  for (size_t m = 0; m < t.slots.size(); ++m) {
+    const int k = t.finish_k[m];
+    if (k < 0) continue;
+    const pa_server::Slot& sl = s->slots[t.slots[m]];
+    st = scuda(s, cudaMemcpyAsync(t.h_best + t.best_off[k], sl.ctx->best_row, (size_t)sl.L * sl.K,
+                                  cudaMemcpyDeviceToHost, t.st),
                "copy best");
     if (st != PA_OK) return st;
   }
-  if (!finishing.empty()) {
-    st = scuda(s, cudaMemcpyAsync(s->h_bestfit, s->d_bestfit, sizeof(double) * finishing.size(),
-                                  cudaMemcpyDeviceToHost, s->stream),
+  if (n_fin > 0) {
+    st = scuda(s, cudaMemcpyAsync(t.h_bestfit, t.d_bestfit, sizeof(double) * n_fin,
+                                  cudaMemcpyDeviceToHost, t.st),
                "copy best fit");
     if (st != PA_OK) return st;
   }
-  st = scuda(s, cudaStreamSynchronize(s->stream), "tick sync");
+  st = scuda(s, cudaEventRecord(t.ev, t.st), "tick event");
   if (st != PA_OK) return st;
-  s->stage_busy = false;
-  for (auto& kv : groups)
-    for (int i : kv.second) {
-      pa_server::Slot& sl = s->slots[i];
-      if (sl.failed) {  // released without a result
-        complete(s, sl.req, PA_EUNSUPPORTED, sl.L, sl.K, nullptr, 0.0);
-        sl.active = false;
-        sl.failed = false;
-        sl.req = -1;
-        s->free_slots[std::make_pair(sl.L, sl.K)].push_back(i);
-        continue;
-      }
-      const int g_now = std::min(s->tick, s->G - sl.gen);
-      sl.gen += g_now;
-      sl.ctx->cur ^= 1;
-      sl.ctx->generation = sl.gen;
-    }
-  for (size_t k = 0; k < finishing.size(); ++k) {
-    pa_server::Slot& sl = s->slots[finishing[k]];
-    if (!sl.active) continue;  // failed above
-    complete(s, sl.req, PA_OK, sl.L, sl.K, s->h_best + sl.best_off, s->h_bestfit[k]);
-    sl.active = false;
-    sl.req = -1;
-    s->free_slots[std::make_pair(sl.L, sl.K)].push_back(finishing[k]);
-  }
+  for (int i : t.slots) s->slots[i].tick = t_index;
+  for (int i : t.failed) s->slots[i].tick = t_index;
+  t.busy = true;
+  t.dirty = false;
+  t.seq = ++s->tick_seq;
   return PA_OK;
 }
-
-extern "C" {
-
-pa_status pa_server_stats(const pa_server* s, uint64_t* used_bytes, int32_t* n_slots,
-                          int64_t* completed) {
-  if (!s) return PA_EINVAL;
-  if (used_bytes) *used_bytes = s->used;
-  if (n_slots) {
-    int n = 0;
-    for (auto& sl : s->slots) n += sl.ctx ? 1 : 0;
-    *n_slots = n;
-  }
-  if (completed) *completed = s->completed;
-  return PA_OK;
-}
-
-}  // extern "C"
