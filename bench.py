@@ -15,8 +15,11 @@ step's dominant kernel (the fused solve) and of the population-wide
 evaluation kernel on 2^20 chromosomes, the 512-instance batched solve, the
 61-cell streamed evaluation and solve, the serving comparison (Poisson
 arrivals, continuous batching vs one plain solve at a time, plus an
-overload point), and the CPU oracle as a reported baseline.  `--only eval |
-solve | stream | batch` runs one part untimed, for profilers.
+overload point), the PK-means island solve (Alg. 2) beside the plain solve,
+the max-min objective's evaluation throughput, and the CPU oracle as a
+reported baseline (one core for whole solves, every core for the
+evaluation).  `--only eval | solve | stream | batch | islands` runs one part
+untimed, for profilers.
 
 Under torchrun each rank solves its own instance (seed = rank): the units
 are independent, so there is no data-path collective ("weak" scaling).
@@ -322,11 +325,24 @@ def run_ours(args):
     if args.only == "batch":
         insts = c3_instances(B, inputs, 512)
         batch = B.Batch(insts)
+        batch.tune(10)  # the shapes the benchmark's batched section uses
         for _ in range(args.warmup + args.steps):
+            torch.cuda.nvtx.range_push("batch_solve")  # profilers can select the tuned solves
             batch.solve(100)
+            torch.cuda.nvtx.range_pop()
         torch.cuda.synchronize()
         print(json.dumps({"only": "batch", "solves": args.warmup + args.steps}))
         batch.close()
+        ctx.close()
+        return 0
+    if args.only == "islands":
+        icfg = B.pa_config_default(L, K, mode=B.PA_SINR_FINITE_M, M=M_ANT, tau_p=TAU_P, N=N_POP,
+                                   rho=inst["rho"], kmeans_k=KMEANS_K, islands=5)
+        ictx = B.Context(icfg, inst["beta"], inst["user_xy_mm"], inst["bs_xy_mm"])
+        for _ in range(args.warmup + args.steps):
+            ictx.solve(G_GEN)
+        print(json.dumps({"only": "islands", "solves": args.warmup + args.steps}))
+        ictx.close()
         ctx.close()
         return 0
     if args.only == "solve":
@@ -465,6 +481,8 @@ def run_ours(args):
         # twice the rate: beyond what one solve at a time can sustain
         line["serving_c4"]["overload_4000_per_s"] = run_serving(
             B, inputs, rate=4000.0, seconds=max(0.5, args.serve_seconds / 2), tick=args.serve_tick)
+    line["islands_pkmeans"] = run_islands(B, inputs, dev)
+    line["objective_min_sinr"] = run_min_sinr(B, inputs, dev)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
     ctx.close()
@@ -756,6 +774,86 @@ def make_serving_instances(shapes):
         return list(ex.map(_serving_instance, jobs, chunksize=128))
 
 
+def run_islands(B, inputs, dev, steps=10):
+    """The PK-means GA (Alg. 2) on the benchmark instance: C = 5 islands
+    found by K-means over the population every 3 generations (Sec. 6.1),
+    N = 256, G = 200, finite-M SINR, FP32 -- per-generation kernels (K-means
+    of the population, island lists, island generation, evaluation) -- beside
+    the plain one-population solve of the same instance; plus the island
+    K-means alone (one re-clustering of 256 chromosomes)."""
+    import numpy as np
+    import torch
+
+    inst = make_instance(0)
+    out = {}
+    for C in (0, 5):
+        cfg = B.pa_config_default(L, K, mode=B.PA_SINR_FINITE_M, M=M_ANT, tau_p=TAU_P, N=N_POP,
+                                  rho=inst["rho"], kmeans_k=KMEANS_K, islands=C)
+        ctx = B.Context(cfg, inst["beta"], inst["user_xy_mm"], inst["bs_xy_mm"])
+        ctx.solve(G_GEN)
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(steps):
+            t0 = time.perf_counter()
+            _, bf = ctx.solve(G_GEN)
+            ms.append(1e3 * (time.perf_counter() - t0))
+        key = "plain" if C == 0 else f"islands_{C}"
+        out[key] = {"ms_per_solve": statistics.median(ms), "best_fitness": bf,
+                    "evals_per_s": N_POP * (G_GEN + 1) / (statistics.median(ms) / 1e3),
+                    "gens_per_s": G_GEN / (statistics.median(ms) / 1e3)}
+        if C:
+            pop, _, _ = ctx.get_population(with_fitness=False)
+            dpop = torch.from_numpy(pop).to(dev)
+            lab = torch.empty(N_POP, dtype=torch.int32, device=dev)
+            B.pa_island_cluster(ctx.handle, dpop, 0, lab)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record()
+            for _ in range(20):
+                B.lib().pa_island_cluster(ctx.handle, B._dev_ptr(dpop), 0, B._dev_ptr(lab), None)
+            e1.record()
+            e1.synchronize()
+            out[key]["kmeans_ms"] = e0.elapsed_time(e1) / 20
+            out[key]["labels_per_island"] = np.bincount(lab.cpu().numpy(), minlength=C).tolist()
+        ctx.close()
+    out["what"] = ("host wall clock per whole solve (K-means seeding + 200 generations + final "
+                   "evaluation); islands run one evaluation, island-generation and (every third "
+                   "generation) population-K-means launch per generation")
+    return out
+
+
+def run_min_sinr(B, inputs, dev):
+    """The max-min objective (Sec. 2): population evaluation of the 2^20
+    chromosomes of the evaluation roofline, on the same instance and
+    kernels, smallest SINR instead of the sum SE."""
+    import torch
+
+    inst = make_instance(0)
+    nb = 1 << BATCH_LOG2
+    pop = inputs.random_population_torch(nb, L, K, seed=1000, device=dev)
+    res = {}
+    for obj in (0, 1):
+        cfg = B.pa_config_default(L, K, mode=B.PA_SINR_FINITE_M, M=M_ANT, tau_p=TAU_P, N=N_POP,
+                                  rho=inst["rho"], objective=obj)
+        ctx = B.Context(cfg, inst["beta"])
+        fit = torch.empty(nb, dtype=torch.float32, device=dev)
+        for _ in range(3):
+            B.pa_eval_population(ctx.handle, pop, fit)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(10):
+            B.pa_eval_population(ctx.handle, pop, fit)
+        e1.record()
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / 10
+        res["min_sinr" if obj else "sum_se"] = {"avg_launch_ms": ms, "evals_per_s": nb / (ms / 1e3)}
+        ctx.close()
+    return res
+
+
 def run_stream_only(args, B, inputs, dev):
     """Only the 61-cell, 32-user streamed evaluation of 2^17 chromosomes (for
     profilers)."""
@@ -811,11 +909,12 @@ def main():
                          "(the configured workload: 10 s at 2000 requests/s)")
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the 512-instance batched-solve comparison")
-    ap.add_argument("--only", choices=["all", "eval", "solve", "stream", "batch"],
+    ap.add_argument("--only", choices=["all", "eval", "solve", "stream", "batch", "islands"],
                     default="all",
-                    help="eval / solve / stream / batch: run only the 2^20-chromosome "
-                         "evaluation, the solves, the 61x32 streamed evaluation or the "
-                         "512-instance batched solve, untimed (for profilers)")
+                    help="eval / solve / stream / batch / islands: run only the 2^20-chromosome "
+                         "evaluation, the solves, the 61x32 streamed evaluation, the "
+                         "512-instance batched solve (tuned shapes) or the island solves, "
+                         "untimed (for profilers)")
     args = ap.parse_args()
     if args.warmup < 3:
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)

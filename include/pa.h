@@ -254,7 +254,8 @@ pa_status pa_population_device(pa_ctx* ctx, uint8_t** pop_dev, void** fit_dev);
  * cfg.island_iter Lloyd passes; ties go to the lower cluster; an emptied
  * cluster keeps its centroid.  labels_dev: device, N int32 (cluster of each
  * member).  passes_host (optional): the number of assignment passes; when
- * given the call synchronises, otherwise it is asynchronous.
+ * given the call synchronises, otherwise it is asynchronous.  Rows are
+ * expected to be permutations; a pilot >= K is read as K-1.
  */
 pa_status pa_island_cluster(pa_ctx* ctx, const uint8_t* pop_dev, int32_t generation,
                             int32_t* labels_dev, int32_t* passes_host);

@@ -302,7 +302,7 @@ pa_status pa_create(const pa_config* cfg, const double* beta, const int32_t* use
       }
       want(&c->isl_passes, sizeof(int32_t));
       if (!pa::island_cnt_in_smem(cfg->N, L, K, cfg->islands))
-        want(&c->isl_cnt, sizeof(int32_t) * (size_t)cfg->islands * LK * K);
+        want(&c->isl_cnt, sizeof(uint32_t) * pa::island_cnt_words(L, K, cfg->islands));
     }
     size_t total = 0;
     for (auto& pt : parts) total = ((total + 255) & ~size_t(255)) + pt.second;

@@ -158,6 +158,7 @@ cudaError_t launch_validate(const pa_ctx* ctx, const uint8_t* pop, int64_t n, in
                             cudaStream_t st);
 // pa_island.cu: PK-means GA (Alg. 2)
 bool island_cnt_in_smem(int N, int L, int K, int C);
+size_t island_cnt_words(int L, int K, int C);
 cudaError_t launch_island_kmeans(const pa_ctx* ctx, const uint8_t* pop, int gen, int32_t* labels,
                                  cudaStream_t st);
 cudaError_t launch_island_lists(const pa_ctx* ctx, const int32_t* labels, const IslandLists& il,

@@ -14,8 +14,8 @@
 // 2^62 for N, L*K <= 4096).  Counts live in shared memory (global memory for
 // large C*L*K*K); a warp computes one member's S for up to eight clusters at
 // a time (lanes over users, then a shuffle sum); the update adds one count
-// per (member, user) with shared-memory atomics -- integer sums, so the
-// order does not matter.  Initial centroids are C distinct members by a
+// per (member, user) with shared-memory atomics, one warp per member --
+// integer sums, so the order does not matter.  Initial centroids are C distinct members by a
 // partial Fisher-Yates shuffle (Philox tag 4, keyed by the generation);
 // Lloyd passes run until no label changes or the pass limit; an emptied
 // cluster keeps its counts.
@@ -39,7 +39,8 @@ namespace pa {
 namespace {
 
 constexpr int kIslandThreads = 1024;
-constexpr int kKmChunk = 8;  // clusters whose sums one warp accumulates at once
+constexpr int kKmMaxW = 8;   // pair words of counts one lane sums at once (16 clusters)
+constexpr int kKmSplits = 8; // most warps sharing one group of 32 members (user ranges)
 
 struct KmArgs {
   const uint8_t* pop;  // [N][LK]
@@ -47,125 +48,361 @@ struct KmArgs {
   uint64_t seed;
   int gen;
   int32_t* label;      // [N] out
-  int32_t* cnt_g;      // [C][LK][K] in global memory, or null (shared memory)
+  uint32_t* cnt_g;     // [LK*K][CWp] in global memory, or null (shared memory)
   int32_t* passes;     // [1] out
+  int us;              // warps sharing a group of 32 members, each a range of users
+  int CWp;             // words per (user, pilot) entry: ceil(C/2), rounded up to odd
+  int NP;              // word stride of the staged population (odd)
+  int o_cnt, o_sb, o_pw;  // dynamic shared-memory offsets (bytes)
 };
 
-__device__ __forceinline__ int warp_sum_i(int v) {
+// Shared-memory layout of one K-means launch: labels and the initial
+// permutation, counts (when in shared memory), per-split partial sums (when
+// us > 1), the population staged as words (when it fits).
+struct KmLayout {
+  int CWp, NP, W, us;
+  size_t o_cnt, o_sb, o_pw, total;
+};
+
+KmLayout km_layout(int N, int L, int K, int C, bool cnt_in_smem, bool pop_in_smem, int us) {
+  KmLayout k;
+  const size_t LK = (size_t)L * K;
+  k.CWp = ((C + 1) / 2) | 1;
+  k.NP = N | 1;
+  k.W = (int)((LK + 3) / 4);
+  k.us = us;
+  size_t b = 2 * 4 * (size_t)((N + 3) & ~3);
+  k.o_cnt = b;
+  if (cnt_in_smem) b += 4 * LK * K * k.CWp;
+  k.o_sb = b;
+  if (us > 1) b += 4 * (size_t)us * C * N;
+  b = (b + 15) & ~size_t(15);
+  k.o_pw = b;
+  if (pop_in_smem) b += 4 * (size_t)k.W * k.NP;
+  k.total = (b + 15) & ~size_t(15);
+  return k;
+}
+
+constexpr size_t kKmSmemBudget = (size_t)kSmemBudget - 2048;  // beside the static arrays
+
+__device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v) {
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
   return v;
 }
 
+// Pilot of user u of member n (a pilot >= K reads as K-1): from the staged
+// words (clamped when staged), or from the rows.
+template <bool PS>
+__device__ __forceinline__ int km_pilot(const uint32_t* pw, int NP, const uint8_t* pop, int LK,
+                                        int K, int n, int u) {
+  if (PS) return (int)((pw[(u >> 2) * NP + n] >> (8 * (u & 3))) & 0xffu);
+  return min((int)pop[(int64_t)n * LK + u], K - 1);
+}
+
+// Word w of member n: the (clamped) pilots of users 4w .. 4w+3, low byte
+// first; bytes past the row end are K-1.
+template <bool PS>
+__device__ __forceinline__ uint32_t km_word(const uint32_t* pw, int NP, const uint8_t* pop, int LK,
+                                            int K, int n, int w) {
+  if (PS) return pw[w * NP + n];
+  uint32_t v = 0;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int u = 4 * w + j;
+    v |= (uint32_t)(u < LK ? min((int)pop[(int64_t)n * LK + u], K - 1) : K - 1) << (8 * j);
+  }
+  return v;
+}
+
+// S(n, c) for the 2*NW clusters of pair words i0 .. i0+NW-1 over the users
+// of words w0 .. w1-1: a lane sums packed 16-bit pairs (one load serves two
+// clusters) for wblk words at a time -- a half stays below 2^16 since each
+// count is at most N -- and widens them into S.  Words below wfull hold
+// four users each; only the row's last word is checked.
+template <int NW, bool PS>
+__device__ __forceinline__ void km_sums(int (&S)[2 * kKmMaxW], const uint32_t* cnt, int CWp,
+                                        int i0, int K, int LK, int w0, int w1, int wblk,
+                                        const uint32_t* pw, int NP, const uint8_t* pop, int n) {
+  const int wfull = LK >> 2, KC = K * CWp;
+#pragma unroll
+  for (int q = 0; q < 2 * NW; ++q) S[q] = 0;
+  for (int wb = w0; wb < w1; wb += wblk) {
+    const int we = min(w1, wb + wblk);
+    uint32_t P[NW];
+#pragma unroll
+    for (int i = 0; i < NW; ++i) P[i] = 0;
+    int w = wb;
+    for (; w < min(we, wfull); ++w) {
+      const uint32_t v = km_word<PS>(pw, NP, pop, LK, K, n, w);
+      const uint32_t* row = cnt + 4 * w * KC + i0;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const uint32_t* e = row + j * KC + (int)((v >> (8 * j)) & 0xffu) * CWp;
+#pragma unroll
+        for (int i = 0; i < NW; ++i) P[i] += e[i];
+      }
+    }
+    for (; w < we; ++w) {  // the row's last, partial word
+      const uint32_t v = km_word<PS>(pw, NP, pop, LK, K, n, w);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int u = 4 * w + j;
+        if (u < LK) {
+          const uint32_t* e = cnt + u * KC + (int)((v >> (8 * j)) & 0xffu) * CWp + i0;
+#pragma unroll
+          for (int i = 0; i < NW; ++i) P[i] += e[i];
+        }
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < NW; ++i) {
+      S[2 * i] += (int)(P[i] & 0xffffu);
+      S[2 * i + 1] += (int)(P[i] >> 16);
+    }
+  }
+}
+
+// Half h (0: low, 16: high) of a packed word.
+__device__ __forceinline__ long long km_half(uint32_t v, int h) {
+  return (long long)((v >> h) & 0xffffu);
+}
+
+// Every loop below is a nested 32-bit loop (counts and members stay below
+// 2^24 entries: L*K*K*CWp and N*L*K for N, L*K <= 4096).
+//
+// Counts are updated, not rebuilt: a pass moves the one-hot vectors of the
+// members whose cluster changed (subtracted from the old cluster, added to
+// the new), and Q follows each count's change exactly ((v+1)^2 - v^2 =
+// 2v + 1 from the value an atomic returns; any order of the moves gives the
+// same Q).  This equals the recount over the new partition because a
+// cluster's counts are the sum over its current members, except for
+// clusters that had no members (kept counts; the initial one-hot centroids):
+// those restart from zero when they gain members -- all of which then moved
+// in -- and keep their counts while they stay empty.
+template <bool CS, bool PS>
 __global__ void __launch_bounds__(kIslandThreads) k_island_kmeans(const KmArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ int s_changed;
-  const int N = a.N, K = a.K, C = a.C, LK = a.L * a.K;
-  const int64_t csz = (int64_t)LK * K;
+  __shared__ unsigned long long Q[kMaxIslands];
+  __shared__ int m[kMaxIslands];       // centroid sizes
+  __shared__ int nm[kMaxIslands];      // sizes of the new partition
+  __shared__ int live[kMaxIslands];    // the cluster has members in the new partition
+  __shared__ int stale[kMaxIslands];   // its counts are not the sum over its members
+  __shared__ uint32_t rdraw[kMaxIslands];
+  __shared__ int nchg[2];              // members that changed cluster, per pass parity
+  const int N = a.N, K = a.K, C = a.C, LK = a.L * a.K, LKK = LK * a.K;
+  const int CW = (C + 1) >> 1, CWp = a.CWp, NP = a.NP, W = (LK + 3) >> 2, us = a.us;
   const int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31, warp = tid >> 5;
   const int nwarps = nthr >> 5;
-  unsigned long long* Q = reinterpret_cast<unsigned long long*>(smem);  // [C]
-  int* m = reinterpret_cast<int*>(Q + kMaxIslands);                     // [C] centroid sizes
-  int* nm = m + kMaxIslands;                                            // [C] new sizes
-  int* lab = nm + kMaxIslands;                                          // [N]
-  int* idx = lab + kMaxIslandN;                                         // [N]
-  int* cnt = a.cnt_g ? a.cnt_g : idx + kMaxIslandN;                     // [C][LK][K]
-  const uint8_t* pop = a.pop;
-
-  for (int64_t i = tid; i < C * csz; i += nthr) cnt[i] = 0;
-  for (int n = tid; n < N; n += nthr) {
-    idx[n] = n;
-    lab[n] = -1;
+  const unsigned full = 0xffffffffu;
+  int* lab = reinterpret_cast<int*>(smem);  // [N]
+  // [N]: the initial permutation, then per pass the changed members
+  // (member << 7 | old cluster + 1)
+  int* chg = lab + ((N + 3) & ~3);
+  uint32_t* cnt = CS ? reinterpret_cast<uint32_t*>(smem + a.o_cnt) : a.cnt_g;
+  int* sb = reinterpret_cast<int*>(smem + a.o_sb);            // [us][C][N]
+  uint32_t* pw = reinterpret_cast<uint32_t*>(smem + a.o_pw);  // [W][NP]
+  if (warp == nwarps - 1) {
+    // the initial draws (a Philox block per eight) overlap the set-up below
+    for (int c = lane; c < C; c += 32) {
+      DrawStream ds(a.seed, 0, (uint64_t)a.gen, kTagIsland);
+      rdraw[c] = below(ds.draw((uint32_t)c), (uint32_t)(N - c));
+    }
+  } else {
+    const int sw = nwarps - 1, st = nthr - 32;
+    if (PS) {  // word w of member n holds the pilots of users 4w .. 4w+3
+      for (int n = warp; n < N; n += sw) {
+        const uint8_t* X = a.pop + (int64_t)n * LK;
+        for (int w = lane; w < W; w += 32) {
+          uint32_t v = 0;
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const int u = 4 * w + j;
+            v |= (uint32_t)(u < LK ? min((int)X[u], K - 1) : K - 1) << (8 * j);
+          }
+          pw[w * NP + n] = v;
+        }
+      }
+    }
+    for (int i = tid; i < LKK * CWp; i += st) cnt[i] = 0;
+    for (int n = tid; n < N; n += st) {
+      chg[n] = n;
+      lab[n] = -1;
+    }
+    if (tid < kMaxIslands) {
+      Q[tid] = 0ULL;
+      nm[tid] = 0;
+      stale[tid] = 1;
+    }
+    if (tid < 2) nchg[tid] = 0;
   }
   __syncthreads();
   if (tid == 0) {
     // initial centroids: C distinct members (partial Fisher-Yates shuffle)
-    DrawStream ds(a.seed, 0, (uint64_t)a.gen, kTagIsland);
     for (int c = 0; c < C; ++c) {
-      const int j = c + (int)below(ds.draw((uint32_t)c), (uint32_t)(N - c));
-      const int t = idx[c];
-      idx[c] = idx[j];
-      idx[j] = t;
+      const int j = c + (int)rdraw[c];
+      const int t = chg[c];
+      chg[c] = chg[j];
+      chg[j] = t;
       m[c] = 1;
     }
   }
   __syncthreads();
-  for (int t = tid; t < C * LK; t += nthr) {
-    const int c = t / LK, u = t - c * LK;
-    cnt[c * csz + (int64_t)u * K + pop[(int64_t)idx[c] * LK + u]] = 1;
+  for (int c = warp; c < C; c += nwarps) {  // one-hot of each initial member
+    const int n = chg[c], h = (c & 1) * 16;
+    unsigned long long dq = 0;
+    for (int u = lane; u < LK; u += 32) {
+      const int x = km_pilot<PS>(pw, NP, a.pop, LK, K, n, u);
+      const uint32_t o = atomicAdd(cnt + (u * K + x) * CWp + (c >> 1), 1u << h);
+      dq += (unsigned long long)(2 * km_half(o, h) + 1);
+    }
+    dq = warp_sum_u64(dq);
+    if (lane == 0) atomicAdd(&Q[c], dq);
   }
+  __syncthreads();
+  const int G = (N + 31) >> 5;
+  const int wblk = max(1, 65535 / (4 * N));
+  // one member's nearest centroid so far (lowest index on ties)
+  auto fold = [&](int c, long long S, int& best, long long& bd) {
+    const long long mc = m[c];
+    const long long A = (long long)LK * mc * mc - 2 * mc * S + (long long)Q[c];
+    const long long mb = m[best];
+    if (c == 0 || A * mb * mb < bd * mc * mc) {
+      best = c;
+      bd = A;
+    }
+  };
+  // a warp's members take their labels (lanes past N pass): changed members
+  // are listed, sizes counted by one atomic per distinct label in the warp
+  auto record = [&](int n, int best, int par) {
+    const bool valid = n < N;
+    const int old = valid ? lab[n] : 0;
+    const bool moved = valid && old != best;
+    const unsigned bm = __ballot_sync(full, moved);
+    if (bm) {
+      const int leader = __ffs(bm) - 1;
+      int base = 0;
+      if (lane == leader) base = atomicAdd(&nchg[par], __popc(bm));
+      base = __shfl_sync(full, base, leader);
+      if (moved) chg[base + __popc(bm & ((1u << lane) - 1u))] = (n << 7) | (old + 1);
+    }
+    const unsigned same = __match_any_sync(full, valid ? best : -1 - lane);
+    if (valid) {
+      lab[n] = best;
+      if ((int)(__ffs(same) - 1) == lane) atomicAdd(&nm[best], __popc(same));
+    }
+  };
   int passes = 0;
   for (int it = 0; it < a.max_iter; ++it) {
-    if (tid < C) Q[tid] = 0ULL;
-    if (tid == 0) s_changed = 0;
-    __syncthreads();
-    for (int64_t i = tid; i < C * csz; i += nthr) {
-      const unsigned long long v = (unsigned long long)cnt[i];
-      if (v) atomicAdd(&Q[i / csz], v * v);
-    }
-    __syncthreads();
-    // ---- assignment: one warp per member
-    for (int n = warp; n < N; n += nwarps) {
-      const uint8_t* X = pop + (int64_t)n * LK;
+    const int par = it & 1;
+    // ---- assignment: a lane per member, warps over (member group, user range)
+    for (int t = warp; t < G * us; t += nwarps) {
+      const int g = t / us, s = t - g * us;
+      const int n = g * 32 + lane;
+      const int nn = n < N ? n : N - 1;
+      const int w0 = (int)((long long)W * s / us), w1 = (int)((long long)W * (s + 1) / us);
       int best = 0;
       long long bd = 0;
-      for (int c0 = 0; c0 < C; c0 += kKmChunk) {
-        int s[kKmChunk];
-#pragma unroll
-        for (int q = 0; q < kKmChunk; ++q) s[q] = 0;
-        for (int u = lane; u < LK; u += 32) {
-          const int64_t o = (int64_t)u * K + X[u];
-#pragma unroll
-          for (int q = 0; q < kKmChunk; ++q)
-            if (c0 + q < C) s[q] += cnt[(c0 + q) * csz + o];
+      for (int c0 = 0; c0 < C; c0 += 2 * kKmMaxW) {
+        int S[2 * kKmMaxW];
+        const int i0 = c0 >> 1;
+        switch (min(kKmMaxW, CW - i0)) {
+#define PA_KM_CASE(NW)                                                                    \
+  case NW:                                                                                \
+    km_sums<NW, PS>(S, cnt, CWp, i0, K, LK, w0, w1, wblk, pw, NP, a.pop, nn);             \
+    break;
+          PA_KM_CASE(1)
+          PA_KM_CASE(2)
+          PA_KM_CASE(3)
+          PA_KM_CASE(4)
+          PA_KM_CASE(5)
+          PA_KM_CASE(6)
+          PA_KM_CASE(7)
+          default:
+            km_sums<8, PS>(S, cnt, CWp, i0, K, LK, w0, w1, wblk, pw, NP, a.pop, nn);
+#undef PA_KM_CASE
         }
 #pragma unroll
-        for (int q = 0; q < kKmChunk; ++q) {
+        for (int q = 0; q < 2 * kKmMaxW; ++q) {
           const int c = c0 + q;
           if (c < C) {
-            const long long S = warp_sum_i(s[q]);
-            const long long mc = m[c];
-            const long long A = (long long)LK * mc * mc - 2 * mc * S + (long long)Q[c];
-            const long long mb = m[best];
-            if (c == 0 || A * mb * mb < bd * mc * mc) {
-              best = c;
-              bd = A;
+            if (us > 1) {
+              if (n < N) sb[(s * C + c) * N + n] = S[q];
+            } else {
+              fold(c, S[q], best, bd);
             }
           }
         }
       }
-      if (lane == 0) {
-        if (lab[n] != best) s_changed = 1;
-        lab[n] = best;
+      if (us == 1) record(n, best, par);
+    }
+    __syncthreads();
+    if (us > 1) {  // the splits' partial sums, then the nearest centroid
+      for (int n0 = warp * 32; n0 < N; n0 += nthr) {
+        const int n = n0 + lane;
+        int best = 0;
+        long long bd = 0;
+        if (n < N)
+          for (int c = 0; c < C; ++c) {
+            int S = 0;
+            for (int s = 0; s < us; ++s) S += sb[(s * C + c) * N + n];
+            fold(c, S, best, bd);
+          }
+        record(n, best, par);
+      }
+      __syncthreads();
+    }
+    ++passes;
+    if (nchg[par] == 0 || it == a.max_iter - 1) break;
+    // ---- update: clusters that gain members after having none restart at zero
+    for (int e = tid; e < LKK; e += nthr)
+      for (int i = 0; i < CW; ++i) {
+        const bool z0 = stale[2 * i] && nm[2 * i] > 0;
+        const bool z1 = 2 * i + 1 < C && stale[2 * i + 1] && nm[2 * i + 1] > 0;
+        if (z0 || z1) cnt[e * CWp + i] &= (z0 ? 0u : 0xffffu) | (z1 ? 0u : 0xffff0000u);
+      }
+    if (tid < C) {
+      live[tid] = nm[tid] > 0;
+      if (nm[tid] > 0) {
+        if (stale[tid]) Q[tid] = 0ULL;
+        m[tid] = nm[tid];
       }
     }
+    if (tid == 0) nchg[par ^ 1] = 0;
     __syncthreads();
-    ++passes;
-    if (s_changed == 0 || it == a.max_iter - 1) break;
-    // ---- update: sizes, then the counts of every cluster that has members
-    if (tid < C) nm[tid] = 0;
-    __syncthreads();
-    for (int n = tid; n < N; n += nthr) atomicAdd(&nm[lab[n]], 1);
-    __syncthreads();
-    for (int64_t i = tid; i < C * csz; i += nthr)
-      if (nm[i / csz] > 0) cnt[i] = 0;
-    __syncthreads();
-    for (int64_t t = tid; t < (int64_t)N * LK; t += nthr) {
-      const int n = (int)(t / LK), u = (int)(t - (int64_t)n * LK);
-      atomicAdd(&cnt[lab[n] * csz + (int64_t)u * K + pop[t]], 1);
+    // ... then every changed member's one-hot moves from its old cluster (when
+    // that one still has members) to its new one
+    for (int k = warp; k < nchg[par]; k += nwarps) {
+      const int e = chg[k], n = e >> 7, A = (e & 127) - 1, Bc = lab[n];
+      const bool sub = A >= 0 && live[A];
+      const int hb = (Bc & 1) * 16, ha = (A & 1) * 16;
+      uint32_t* pb = cnt + (Bc >> 1);
+      uint32_t* pold = cnt + (sub ? A >> 1 : 0);
+      unsigned long long dqb = 0, dqa = 0;
+      for (int u = lane; u < LK; u += 32) {
+        const int o = (u * K + km_pilot<PS>(pw, NP, a.pop, LK, K, n, u)) * CWp;
+        const uint32_t ob = atomicAdd(pb + o, 1u << hb);
+        dqb += (unsigned long long)(2 * km_half(ob, hb) + 1);
+        if (sub) {  // the half is >= 1 (the member is counted in it): no borrow
+          const uint32_t oa = atomicAdd(pold + o, 0u - (1u << ha));
+          dqa += (unsigned long long)(1 - 2 * km_half(oa, ha));
+        }
+      }
+      dqb = warp_sum_u64(dqb);
+      dqa = warp_sum_u64(dqa);
+      if (lane == 0) {
+        atomicAdd(&Q[Bc], dqb);
+        if (sub) atomicAdd(&Q[A], dqa);
+      }
     }
-    if (tid < C && nm[tid] > 0) m[tid] = nm[tid];
+    if (tid < C) {
+      stale[tid] = nm[tid] == 0;
+      nm[tid] = 0;
+    }
     __syncthreads();
   }
   for (int n = tid; n < N; n += nthr) a.label[n] = lab[n];
   if (tid == 0 && a.passes) *a.passes = passes;
-}
-
-size_t kmeans_smem(int N, int L, int K, int C, bool cnt_in_smem) {
-  size_t b = 8 * (size_t)kMaxIslands + 4 * 2 * (size_t)kMaxIslands + 4 * 2 * (size_t)kMaxIslandN;
-  if (cnt_in_smem) b += 4 * (size_t)C * L * K * K;
-  (void)N;
-  return (b + 15) & ~size_t(15);
 }
 
 // Members grouped by island.  One CTA: counts, prefix over islands, then
@@ -348,12 +585,25 @@ __global__ void __launch_bounds__(kStepThreads) k_island_step(const IslandStepAr
 
 // Counts of a population K-means fit in shared memory next to the labels.
 bool island_cnt_in_smem(int N, int L, int K, int C) {
-  return kmeans_smem(N, L, K, C, true) <= (size_t)kSmemBudget;
+  return km_layout(N, L, K, C, true, false, 1).total <= kKmSmemBudget;
+}
+
+// Words of the K-means counts: two clusters per word, ceil(C/2) words (odd)
+// per (user, pilot).
+size_t island_cnt_words(int L, int K, int C) {
+  return (size_t)L * K * K * (((C + 1) / 2) | 1);
 }
 
 cudaError_t launch_island_kmeans(const pa_ctx* ctx, const uint8_t* pop, int gen, int32_t* labels,
                                  cudaStream_t st) {
   const pa_config& c = ctx->cfg;
+  const bool cs = ctx->isl_cnt == nullptr;
+  const bool ps = km_layout(c.N, c.L, c.K, c.islands, cs, true, 1).total <= kKmSmemBudget;
+  // warps per group of 32 members: fill the CTA's warps, within the budget
+  const int groups = (c.N + 31) / 32, W = (c.L * c.K + 3) / 4;
+  int us = std::max(1, std::min({kKmSplits, kIslandThreads / 32 / groups, W}));
+  while (us > 1 && km_layout(c.N, c.L, c.K, c.islands, cs, ps, us).total > kKmSmemBudget) --us;
+  const KmLayout k = km_layout(c.N, c.L, c.K, c.islands, cs, ps, us);
   KmArgs a;
   a.pop = pop;
   a.N = c.N;
@@ -364,18 +614,35 @@ cudaError_t launch_island_kmeans(const pa_ctx* ctx, const uint8_t* pop, int gen,
   a.seed = c.seed;
   a.gen = gen;
   a.label = labels;
-  a.cnt_g = ctx->isl_cnt;  // null when the counts fit in shared memory
+  a.cnt_g = reinterpret_cast<uint32_t*>(ctx->isl_cnt);
   a.passes = ctx->isl_passes;
-  const size_t smem = kmeans_smem(c.N, c.L, c.K, c.islands, a.cnt_g == nullptr);
-  static std::atomic<uint64_t> capped{0};
+  a.us = us;
+  a.CWp = k.CWp;
+  a.NP = k.NP;
+  a.o_cnt = (int)k.o_cnt;
+  a.o_sb = (int)k.o_sb;
+  a.o_pw = (int)k.o_pw;
+  const void* fn = cs ? (ps ? (const void*)k_island_kmeans<true, true>
+                            : (const void*)k_island_kmeans<true, false>)
+                      : (ps ? (const void*)k_island_kmeans<false, true>
+                            : (const void*)k_island_kmeans<false, false>);
+  static std::atomic<uint64_t> capped[4];
+  const int vi = (cs ? 2 : 0) + (ps ? 1 : 0);
   const uint64_t bit = 1ULL << (ctx->device & 63);
-  if (!(capped.load() & bit)) {
-    cudaError_t e = raise_smem_cap((const void*)k_island_kmeans, ctx->device);
+  if (!(capped[vi].load() & bit)) {
+    cudaError_t e = raise_smem_cap(fn, ctx->device);
     if (e != cudaSuccess) return e;
-    capped.fetch_or(bit);
+    capped[vi].fetch_or(bit);
   }
   (void)cudaGetLastError();  // drop a stale error of an earlier call
-  k_island_kmeans<<<1, kIslandThreads, smem, st>>>(a);
+  if (cs && ps)
+    k_island_kmeans<true, true><<<1, kIslandThreads, k.total, st>>>(a);
+  else if (cs)
+    k_island_kmeans<true, false><<<1, kIslandThreads, k.total, st>>>(a);
+  else if (ps)
+    k_island_kmeans<false, true><<<1, kIslandThreads, k.total, st>>>(a);
+  else
+    k_island_kmeans<false, false><<<1, kIslandThreads, k.total, st>>>(a);
   count_launch();
   return cudaGetLastError();
 }
