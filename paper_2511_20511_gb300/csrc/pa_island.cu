@@ -15,7 +15,11 @@
 // large C*L*K*K); a warp computes one member's S for up to eight clusters at
 // a time (lanes over users, then a shuffle sum); the update adds one count
 // per (member, user) with shared-memory atomics, one warp per member --
-// integer sums, so the order does not matter.  Initial centroids are C distinct members by a
+// integer sums, so the order does not matter.  When the counts and the population fit in shared
+// memory, a cluster of up to eight CTAs runs it instead (k_island_kmeans_cl):
+// each CTA assigns a slice of the members, keeps its own copy of the counts,
+// and after one cluster barrier per pass replays every CTA's changed members
+// into that copy (the same integer updates in every CTA).  Initial centroids are C distinct members by a
 // partial Fisher-Yates shuffle (Philox tag 4, keyed by the generation);
 // Lloyd passes run until no label changes or the pass limit; an emptied
 // cluster keeps its counts.
@@ -30,6 +34,8 @@
 // argmax over the island's members -- and otherwise a child of two
 // tournaments among the island's members, row-wise crossover and swap
 // mutation with the draws of slot n (tag 3), exactly those of k_ga_step.
+#include <cooperative_groups.h>
+
 #include <algorithm>
 #include <atomic>
 
@@ -37,6 +43,8 @@
 
 namespace pa {
 namespace {
+
+namespace cg = cooperative_groups;
 
 constexpr int kIslandThreads = 1024;
 constexpr int kKmMaxW = 8;   // pair words of counts one lane sums at once (16 clusters)
@@ -83,7 +91,7 @@ KmLayout km_layout(int N, int L, int K, int C, bool cnt_in_smem, bool pop_in_sme
   return k;
 }
 
-constexpr size_t kKmSmemBudget = (size_t)kSmemBudget - 2048;  // beside the static arrays
+constexpr size_t kKmSmemBudget = (size_t)kSmemBudget - 4096;  // beside the static arrays
 
 __device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v) {
 #pragma unroll
@@ -405,6 +413,300 @@ __global__ void __launch_bounds__(kIslandThreads) k_island_kmeans(const KmArgs a
   if (tid == 0 && a.passes) *a.passes = passes;
 }
 
+// The cluster form of k_island_kmeans: CTA r of R assigns members
+// [N r / R, N (r+1) / R); every CTA holds the whole staged population and
+// its own copy of the counts, Q, m and the initial centroids (all computed
+// identically).  A pass: assignment of the own slice, the changed members
+// listed per CTA; one cluster barrier; every CTA reads the other CTAs'
+// changed lists and cluster sizes (distributed shared memory), decides the
+// same stop, and replays all changed members into its counts.  Lists and
+// sizes are double-buffered by pass parity, so a CTA can list the next
+// pass's changes while another still reads this pass's.
+struct KmClLayout {
+  int NP, W, us, Nr;
+  size_t o_lab, o_chg, o_gchg, o_cnt, o_sb, o_pw, total;
+};
+
+KmClLayout km_cl_layout(int N, int L, int K, int C, int R, int us) {
+  KmClLayout k;
+  const size_t LK = (size_t)L * K;
+  const int CWp = ((C + 1) / 2) | 1;
+  const size_t N4 = (size_t)((N + 3) & ~3);
+  k.NP = N | 1;
+  k.W = (int)((LK + 3) / 4);
+  k.us = us;
+  k.Nr = (N + R - 1) / R;
+  size_t b = 0;
+  k.o_lab = b;   // [N] labels of the own slice (whole range allocated)
+  b += 4 * N4;   // + [N] initial permutation
+  b += 4 * N4;
+  k.o_chg = b;   // [2][N] own changed members per pass parity
+  b += 4 * 2 * N4;
+  k.o_gchg = b;  // [N] every CTA's changed members of this pass
+  b += 4 * N4;
+  k.o_cnt = b;
+  b += 4 * LK * K * CWp;
+  k.o_sb = b;
+  if (us > 1) b += 4 * (size_t)us * C * k.Nr;
+  b = (b + 15) & ~size_t(15);
+  k.o_pw = b;
+  b += 4 * (size_t)k.W * k.NP;
+  k.total = (b + 15) & ~size_t(15);
+  return k;
+}
+
+constexpr int kKmClusterMax = 8;
+
+struct KmClArgs {
+  KmArgs a;
+  int Nr;
+  int o_lab, o_chg, o_gchg;
+};
+
+__global__ void __launch_bounds__(kIslandThreads) k_island_kmeans_cl(const KmClArgs ca) {
+  cg::cluster_group cluster = cg::this_cluster();
+  const KmArgs& a = ca.a;
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ unsigned long long Q[kMaxIslands];
+  __shared__ int m[kMaxIslands];       // centroid sizes
+  __shared__ int nm[kMaxIslands];      // sizes of the new partition (all CTAs)
+  __shared__ int live[kMaxIslands];    // the cluster has members in the new partition
+  __shared__ int stale[kMaxIslands];   // its counts are not the sum over its members
+  __shared__ uint32_t rdraw[kMaxIslands];
+  __shared__ int nm_own[2][kMaxIslands];  // own slice's sizes, per pass parity
+  __shared__ int nchg_own[2];             // own slice's changed members, per pass parity
+  __shared__ int cnt_r[kKmClusterMax];    // changed members of each CTA in this pass
+  const int R = (int)cluster.num_blocks(), rank = (int)cluster.block_rank();
+  const int N = a.N, K = a.K, C = a.C, LK = a.L * a.K, LKK = LK * a.K;
+  const int CW = (C + 1) >> 1, CWp = a.CWp, NP = a.NP, W = (LK + 3) >> 2, us = a.us;
+  const int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31, warp = tid >> 5;
+  const int nwarps = nthr >> 5;
+  const unsigned full = 0xffffffffu;
+  const int n_lo = (int)((long long)N * rank / R), n_hi = (int)((long long)N * (rank + 1) / R);
+  const int Nr = ca.Nr;
+  int* lab = reinterpret_cast<int*>(smem + ca.o_lab);             // [N]
+  int* perm = lab + ((N + 3) & ~3);                               // [N]
+  int* chg = reinterpret_cast<int*>(smem + ca.o_chg);             // [2][N4]
+  int* gchg = reinterpret_cast<int*>(smem + ca.o_gchg);           // [N]
+  uint32_t* cnt = reinterpret_cast<uint32_t*>(smem + a.o_cnt);    // [LK*K][CWp]
+  int* sb = reinterpret_cast<int*>(smem + a.o_sb);                // [us][C][Nr]
+  uint32_t* pw = reinterpret_cast<uint32_t*>(smem + a.o_pw);      // [W][NP]
+  const int N4 = (N + 3) & ~3;
+  if (warp == nwarps - 1) {
+    for (int c = lane; c < C; c += 32) {
+      DrawStream ds(a.seed, 0, (uint64_t)a.gen, kTagIsland);
+      rdraw[c] = below(ds.draw((uint32_t)c), (uint32_t)(N - c));
+    }
+  } else {
+    const int sw = nwarps - 1, st = nthr - 32;
+    for (int n = warp; n < N; n += sw) {
+      const uint8_t* X = a.pop + (int64_t)n * LK;
+      for (int w = lane; w < W; w += 32) {
+        uint32_t v = 0;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int u = 4 * w + j;
+          v |= (uint32_t)(u < LK ? min((int)X[u], K - 1) : K - 1) << (8 * j);
+        }
+        pw[w * NP + n] = v;
+      }
+    }
+    for (int i = tid; i < LKK * CWp; i += st) cnt[i] = 0;
+    for (int n = tid; n < N; n += st) {
+      perm[n] = n;
+      lab[n] = -1;
+    }
+    if (tid < kMaxIslands) {
+      Q[tid] = 0ULL;
+      stale[tid] = 1;
+      nm_own[0][tid] = 0;
+      nm_own[1][tid] = 0;
+    }
+    if (tid < 2) nchg_own[tid] = 0;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    for (int c = 0; c < C; ++c) {
+      const int j = c + (int)rdraw[c];
+      const int t = perm[c];
+      perm[c] = perm[j];
+      perm[j] = t;
+      m[c] = 1;
+    }
+  }
+  __syncthreads();
+  for (int c = warp; c < C; c += nwarps) {
+    const int n = perm[c], h = (c & 1) * 16;
+    unsigned long long dq = 0;
+    for (int u = lane; u < LK; u += 32) {
+      const int x = km_pilot<true>(pw, NP, a.pop, LK, K, n, u);
+      const uint32_t o = atomicAdd(cnt + (u * K + x) * CWp + (c >> 1), 1u << h);
+      dq += (unsigned long long)(2 * km_half(o, h) + 1);
+    }
+    dq = warp_sum_u64(dq);
+    if (lane == 0) atomicAdd(&Q[c], dq);
+  }
+  __syncthreads();
+  const int G = (n_hi - n_lo + 31) >> 5;
+  const int wblk = max(1, 65535 / (4 * N));
+  auto fold = [&](int c, long long S, int& best, long long& bd) {
+    const long long mc = m[c];
+    const long long A = (long long)LK * mc * mc - 2 * mc * S + (long long)Q[c];
+    const long long mb = m[best];
+    if (c == 0 || A * mb * mb < bd * mc * mc) {
+      best = c;
+      bd = A;
+    }
+  };
+  auto record = [&](int n, int best, int par) {
+    const bool valid = n < n_hi;
+    const int old = valid ? lab[n] : 0;
+    const bool moved = valid && old != best;
+    const unsigned bm = __ballot_sync(full, moved);
+    if (bm) {
+      const int leader = __ffs(bm) - 1;
+      int base = 0;
+      if (lane == leader) base = atomicAdd(&nchg_own[par], __popc(bm));
+      base = __shfl_sync(full, base, leader);
+      if (moved)
+        chg[par * N4 + base + __popc(bm & ((1u << lane) - 1u))] = (n << 13) | ((old + 1) << 6) | best;
+    }
+    const unsigned same = __match_any_sync(full, valid ? best : -1 - lane);
+    if (valid) {
+      lab[n] = best;
+      if ((int)(__ffs(same) - 1) == lane) atomicAdd(&nm_own[par][best], __popc(same));
+    }
+  };
+  int passes = 0;
+  for (int it = 0; it < a.max_iter; ++it) {
+    const int par = it & 1;
+    // ---- assignment of the own slice
+    for (int t = warp; t < G * us; t += nwarps) {
+      const int g = t / us, s = t - g * us;
+      const int n = n_lo + g * 32 + lane;
+      const int nn = n < n_hi ? n : n_hi - 1;
+      const int w0 = (int)((long long)W * s / us), w1 = (int)((long long)W * (s + 1) / us);
+      int best = 0;
+      long long bd = 0;
+      for (int c0 = 0; c0 < C; c0 += 2 * kKmMaxW) {
+        int S[2 * kKmMaxW];
+        const int i0 = c0 >> 1;
+        switch (min(kKmMaxW, CW - i0)) {
+#define PA_KM_CASE(NW)                                                                    \
+  case NW:                                                                                \
+    km_sums<NW, true>(S, cnt, CWp, i0, K, LK, w0, w1, wblk, pw, NP, a.pop, nn);           \
+    break;
+          PA_KM_CASE(1)
+          PA_KM_CASE(2)
+          PA_KM_CASE(3)
+          PA_KM_CASE(4)
+          PA_KM_CASE(5)
+          PA_KM_CASE(6)
+          PA_KM_CASE(7)
+          default:
+            km_sums<8, true>(S, cnt, CWp, i0, K, LK, w0, w1, wblk, pw, NP, a.pop, nn);
+#undef PA_KM_CASE
+        }
+#pragma unroll
+        for (int q = 0; q < 2 * kKmMaxW; ++q) {
+          const int c = c0 + q;
+          if (c < C) {
+            if (us > 1) {
+              if (n < n_hi) sb[(s * C + c) * Nr + (n - n_lo)] = S[q];
+            } else {
+              fold(c, S[q], best, bd);
+            }
+          }
+        }
+      }
+      if (us == 1) record(n, best, par);
+    }
+    __syncthreads();
+    if (us > 1) {
+      for (int n0 = n_lo + warp * 32; n0 < n_hi; n0 += nthr) {
+        const int n = n0 + lane;
+        int best = 0;
+        long long bd = 0;
+        if (n < n_hi)
+          for (int c = 0; c < C; ++c) {
+            int S = 0;
+            for (int s = 0; s < us; ++s) S += sb[(s * C + c) * Nr + (n - n_lo)];
+            fold(c, S, best, bd);
+          }
+        record(n, best, par);
+      }
+    }
+    // ---- every CTA's labels, lists and sizes of this pass are visible
+    cluster.sync();
+    if (tid < R) cnt_r[tid] = *cluster.map_shared_rank(&nchg_own[par], tid);
+    if (tid >= 32 && tid < 32 + C) {
+      const int c = tid - 32;
+      int v = 0;
+      for (int r = 0; r < R; ++r) v += *cluster.map_shared_rank(&nm_own[par][c], r);
+      nm[c] = v;
+    }
+    __syncthreads();
+    int total = 0;
+    for (int r = 0; r < R; ++r) total += cnt_r[r];
+    ++passes;
+    if (total == 0 || it == a.max_iter - 1) break;
+    // every CTA's changed members, in CTA order
+    for (int k = tid; k < total; k += nthr) {
+      int r = 0, base = 0;
+      while (k >= base + cnt_r[r]) {
+        base += cnt_r[r];
+        ++r;
+      }
+      gchg[k] = *cluster.map_shared_rank(chg + par * N4 + (k - base), r);
+    }
+    for (int e = tid; e < LKK; e += nthr)
+      for (int i = 0; i < CW; ++i) {
+        const bool z0 = stale[2 * i] && nm[2 * i] > 0;
+        const bool z1 = 2 * i + 1 < C && stale[2 * i + 1] && nm[2 * i + 1] > 0;
+        if (z0 || z1) cnt[e * CWp + i] &= (z0 ? 0u : 0xffffu) | (z1 ? 0u : 0xffff0000u);
+      }
+    if (tid < C) {
+      live[tid] = nm[tid] > 0;
+      if (nm[tid] > 0) {
+        if (stale[tid]) Q[tid] = 0ULL;
+        m[tid] = nm[tid];
+      }
+    }
+    // the other parity's own lists were last read before this pass's barrier
+    if (tid < kMaxIslands) nm_own[par ^ 1][tid] = 0;
+    if (tid == 0) nchg_own[par ^ 1] = 0;
+    __syncthreads();
+    for (int k = warp; k < total; k += nwarps) {
+      const int e = gchg[k], n = e >> 13, A = ((e >> 6) & 127) - 1, Bc = e & 63;
+      const bool sub = A >= 0 && live[A];
+      const int hb = (Bc & 1) * 16, ha = (A & 1) * 16;
+      uint32_t* pb = cnt + (Bc >> 1);
+      uint32_t* pold = cnt + (sub ? A >> 1 : 0);
+      unsigned long long dqb = 0, dqa = 0;
+      for (int u = lane; u < LK; u += 32) {
+        const int o = (u * K + km_pilot<true>(pw, NP, a.pop, LK, K, n, u)) * CWp;
+        const uint32_t ob = atomicAdd(pb + o, 1u << hb);
+        dqb += (unsigned long long)(2 * km_half(ob, hb) + 1);
+        if (sub) {
+          const uint32_t oa = atomicAdd(pold + o, 0u - (1u << ha));
+          dqa += (unsigned long long)(1 - 2 * km_half(oa, ha));
+        }
+      }
+      dqb = warp_sum_u64(dqb);
+      dqa = warp_sum_u64(dqa);
+      if (lane == 0) {
+        atomicAdd(&Q[Bc], dqb);
+        if (sub) atomicAdd(&Q[A], dqa);
+      }
+    }
+    if (tid < C) stale[tid] = nm[tid] == 0;
+    __syncthreads();
+  }
+  for (int n = n_lo + tid; n < n_hi; n += nthr) a.label[n] = lab[n];
+  if (rank == 0 && tid == 0 && a.passes) *a.passes = passes;
+  cluster.sync();  // the other CTAs may still read this CTA's lists
+}
+
 // Members grouped by island.  One CTA: counts, prefix over islands, then
 // chunks of blockDim.x members ranked within warps and across warps.
 __global__ void __launch_bounds__(kIslandThreads) k_island_lists(const int32_t* __restrict__ label,
@@ -594,9 +896,99 @@ size_t island_cnt_words(int L, int K, int C) {
   return (size_t)L * K * K * (((C + 1) / 2) | 1);
 }
 
+// Cluster form of the K-means (k_island_kmeans_cl): R = min(8, N/32) CTAs,
+// each holding the whole population and its own counts.
+// cudaErrorNotSupported when it does not apply (fewer than 64 members, a
+// layout beyond shared memory, a cluster shape that cannot be resident).
+cudaError_t launch_island_kmeans_cl(const pa_ctx* ctx, const uint8_t* pop, int gen, int32_t* labels,
+                                    cudaStream_t st) {
+  const pa_config& c = ctx->cfg;
+  if (c.N < 64) return cudaErrorNotSupported;
+  const int R = std::min(kKmClusterMax, std::max(2, c.N / 32));
+  const int Nr = (c.N + R - 1) / R;
+  const int groups = (Nr + 31) / 32, W = (c.L * c.K + 3) / 4;
+  int us = std::max(1, std::min({kKmSplits, kIslandThreads / 32 / groups, W}));
+  while (us > 1 && km_cl_layout(c.N, c.L, c.K, c.islands, R, us).total > kKmSmemBudget) --us;
+  const KmClLayout k = km_cl_layout(c.N, c.L, c.K, c.islands, R, us);
+  if (k.total > kKmSmemBudget) return cudaErrorNotSupported;
+  // residency of this shape, once per (device, cluster size, shared memory)
+  struct Fit {
+    int dev, R;
+    size_t smem;
+    bool ok;
+  };
+  static Fit fits[64];
+  static std::atomic<int> nfits{0};
+  static std::atomic<uint64_t> capped{0};
+  const uint64_t bit = 1ULL << (ctx->device & 63);
+  if (!(capped.load() & bit)) {
+    cudaError_t e = raise_smem_cap((const void*)k_island_kmeans_cl, ctx->device);
+    if (e != cudaSuccess) return e;
+    capped.fetch_or(bit);
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(R, 1, 1);
+  cfg.blockDim = dim3(kIslandThreads, 1, 1);
+  cfg.dynamicSmemBytes = k.total;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = R;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int known = -1;
+  const int nf = std::min(nfits.load(), 64);
+  for (int i = 0; i < nf; ++i)
+    if (fits[i].dev == ctx->device && fits[i].R == R && fits[i].smem == k.total)
+      known = fits[i].ok ? 1 : 0;
+  if (known < 0) {
+    int nclusters = 0;
+    const bool ok = cudaOccupancyMaxActiveClusters(&nclusters, k_island_kmeans_cl, &cfg) ==
+                        cudaSuccess && nclusters >= 1;
+    (void)cudaGetLastError();
+    const int i = nfits.fetch_add(1);
+    if (i < 64) fits[i] = Fit{ctx->device, R, k.total, ok};
+    known = ok ? 1 : 0;
+  }
+  if (!known) return cudaErrorNotSupported;
+  KmClArgs ca;
+  KmArgs& a = ca.a;
+  a.pop = pop;
+  a.N = c.N;
+  a.L = c.L;
+  a.K = c.K;
+  a.C = c.islands;
+  a.max_iter = c.island_iter;
+  a.seed = c.seed;
+  a.gen = gen;
+  a.label = labels;
+  a.cnt_g = nullptr;
+  a.passes = ctx->isl_passes;
+  a.us = us;
+  a.CWp = ((c.islands + 1) / 2) | 1;
+  a.NP = k.NP;
+  a.o_cnt = (int)k.o_cnt;
+  a.o_sb = (int)k.o_sb;
+  a.o_pw = (int)k.o_pw;
+  ca.Nr = k.Nr;
+  ca.o_lab = (int)k.o_lab;
+  ca.o_chg = (int)k.o_chg;
+  ca.o_gchg = (int)k.o_gchg;
+  (void)cudaGetLastError();  // drop a stale error of an earlier call
+  cudaError_t e = cudaLaunchKernelEx(&cfg, k_island_kmeans_cl, ca);
+  count_launch();
+  return e;
+}
+
 cudaError_t launch_island_kmeans(const pa_ctx* ctx, const uint8_t* pop, int gen, int32_t* labels,
                                  cudaStream_t st) {
   const pa_config& c = ctx->cfg;
+  if (ctx->isl_cnt == nullptr) {  // the cluster form, where it fits and can be resident
+    cudaError_t e = launch_island_kmeans_cl(ctx, pop, gen, labels, st);
+    if (e != cudaErrorNotSupported) return e;
+  }
   const bool cs = ctx->isl_cnt == nullptr;
   const bool ps = km_layout(c.N, c.L, c.K, c.islands, cs, true, 1).total <= kKmSmemBudget;
   // warps per group of 32 members: fill the CTA's warps, within the budget
