@@ -479,14 +479,18 @@ static pa_status run_generations(pa_ctx* ctx, int32_t generations, bool* final_e
   *final_evaluated = false;
   if (generations == 0) return PA_OK;
   if (ctx->cfg.islands >= 2) {
-    // Alg. 2: fitness; every `recluster` generations (and whenever the
-    // labels do not belong to this population) K-means into islands and
-    // their member lists; then one island generation
-    for (int32_t g = 0; g < generations; ++g) {
+    // Alg. 2: every `recluster` generations (and whenever the labels do not
+    // belong to this population) K-means into islands and their member
+    // lists; the generations up to the next re-clustering then run in one
+    // cluster launch of the fused solve in island mode (which leaves the
+    // final population's fitness), or where that does not fit one at a time
+    // (fitness, one island generation)
+    int32_t done = 0;
+    while (done < generations) {
       uint8_t* cur = ctx->pop[ctx->cur];
       uint8_t* nxt = ctx->pop[ctx->cur ^ 1];
-      PA_TRY(ctx, eval_any(ctx, cur, ctx->cfg.N, ctx->fit), "eval kernel");
-      if (!ctx->isl_valid || ctx->generation % ctx->cfg.recluster == 0) {
+      const int R = ctx->cfg.recluster;
+      if (!ctx->isl_valid || ctx->generation % R == 0) {
         PA_TRY(ctx, pa::launch_island_kmeans(ctx, cur, ctx->generation, ctx->isl_label,
                                              ctx->stream),
                "island K-means kernel");
@@ -494,11 +498,26 @@ static pa_status run_generations(pa_ctx* ctx, int32_t generations, bool* final_e
                "island lists kernel");
         ctx->isl_valid = 1;
       }
+      const int32_t block = std::min(generations - done, R - ctx->generation % R);
+      const cudaError_t e = pa::launch_solve(ctx, cur, nxt, ctx->generation, block, ctx->fit,
+                                             nullptr, nullptr, ctx->stream, ctx->isl_label,
+                                             &ctx->isl_res);
+      if (e == cudaSuccess) {
+        ctx->cur ^= 1;
+        ctx->generation += block;
+        done += block;
+        *final_evaluated = true;
+        continue;
+      }
+      if (e != cudaErrorNotSupported) return cuda_check(ctx, e, "island solve kernel");
+      PA_TRY(ctx, eval_any(ctx, cur, ctx->cfg.N, ctx->fit), "eval kernel");
       PA_TRY(ctx, pa::launch_island_step(ctx, cur, ctx->fit, ctx->isl_label, ctx->isl_res,
                                          ctx->generation, nxt, ctx->stream),
              "island step kernel");
       ctx->cur ^= 1;
       ctx->generation += 1;
+      done += 1;
+      *final_evaluated = false;
     }
     return PA_OK;
   }
@@ -541,7 +560,8 @@ pa_status pa_solve(pa_ctx* ctx, int32_t generations, uint8_t* best_host, double*
   const int64_t LK = (int64_t)ctx->cfg.L * ctx->cfg.K;
   double* best_dev = reinterpret_cast<double*>(ctx->best_row + ((LK + 7) & ~int64_t(7)));
   // fused path: all generations, the final evaluation and the best member
-  // in one cluster launch (Alg. 1 only; islands run per generation)
+  // in one cluster launch (Alg. 1 only; islands launch once per
+  // re-clustering)
   cudaError_t e = ctx->cfg.islands >= 2
                       ? cudaErrorNotSupported
                       : pa::launch_solve(ctx, ctx->pop[0], ctx->pop[1], 0, generations, ctx->fit,
@@ -554,7 +574,7 @@ pa_status pa_solve(pa_ctx* ctx, int32_t generations, uint8_t* best_host, double*
     st = run_generations(ctx, generations, &evaluated);
     if (st != PA_OK) return st;
     uint8_t* cur = ctx->pop[ctx->cur];
-    PA_TRY(ctx, eval_any(ctx, cur, ctx->cfg.N, ctx->fit), "eval kernel");
+    if (!evaluated) PA_TRY(ctx, eval_any(ctx, cur, ctx->cfg.N, ctx->fit), "eval kernel");
     PA_TRY(ctx, pa::launch_argbest(ctx, ctx->fit, cur, ctx->best_row, best_dev, ctx->stream),
            "argbest kernel");
   } else {

@@ -27,81 +27,9 @@
 #include <atomic>
 #include <mutex>
 
-#include "pa_solve_body.cuh"
+#include "pa_solve_launch.cuh"
 
 namespace pa {
-namespace {
-
-// One instance per launch: the cluster runs solve_body once.
-template <typename FT, int NJ, int VEC, bool FIN>
-__global__ void __launch_bounds__(kSolveThreads) k_solve(const SolveArgs a) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ int elites[64];
-  cg::cluster_group cluster = cg::this_cluster();
-  solve_body<FT, NJ, VEC, FIN, kSoloMaxNP>(a, smem, elites, cluster);
-}
-
-template <typename FT, int NJ, int VEC, bool FIN>
-cudaError_t run_solve(const SolveArgs& a, const SolveShape& s, bool check_fit, cudaStream_t st) {
-  auto kern = k_solve<FT, NJ, VEC, FIN>;
-  static std::atomic<uint64_t> prepared{0};
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return e;
-  const uint64_t bit = 1ULL << (dev & 63);
-  if (!(prepared.load() & bit)) {
-    e = raise_smem_cap((const void*)kern, dev);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-    if (e != cudaSuccess) return e;
-    prepared.fetch_or(bit);
-  }
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(s.C, 1, 1);
-  cfg.blockDim = dim3(kSolveThreads, 1, 1);
-  cfg.dynamicSmemBytes = s.smem;
-  cfg.stream = st;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = s.C;
-  attr[0].val.clusterDim.y = 1;
-  attr[0].val.clusterDim.z = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  if (check_fit) {
-    int nclusters = 0;
-    e = cudaOccupancyMaxActiveClusters(&nclusters, kern, &cfg);
-    if (e != cudaSuccess || nclusters < 1) {
-      (void)cudaGetLastError();
-      return cudaErrorNotSupported;  // this cluster shape cannot be resident
-    }
-  }
-  (void)cudaGetLastError();  // drop a stale error of an earlier call
-  e = cudaLaunchKernelEx(&cfg, kern, a);
-  count_launch();
-  return e;
-}
-
-template <typename FT, int VEC, bool FIN>
-cudaError_t pick_solve(int NJ, const SolveArgs& a, const SolveShape& s, bool chk, cudaStream_t st) {
-  switch (NJ) {
-    case 4: return run_solve<FT, 4, VEC, FIN>(a, s, chk, st);
-    case 8: return run_solve<FT, 8, VEC, FIN>(a, s, chk, st);
-    case 12: return run_solve<FT, 12, VEC, FIN>(a, s, chk, st);
-    case 16: return run_solve<FT, 16, VEC, FIN>(a, s, chk, st);
-    case 20: return run_solve<FT, 20, VEC, FIN>(a, s, chk, st);
-    case 24: return run_solve<FT, 24, VEC, FIN>(a, s, chk, st);
-    case 28: return run_solve<FT, 28, VEC, FIN>(a, s, chk, st);
-    case 32: return run_solve<FT, 32, VEC, FIN>(a, s, chk, st);
-    case 36: return run_solve<FT, 36, VEC, FIN>(a, s, chk, st);
-    case 40: return run_solve<FT, 40, VEC, FIN>(a, s, chk, st);
-    case 44: return run_solve<FT, 44, VEC, FIN>(a, s, chk, st);
-    case 48: return run_solve<FT, 48, VEC, FIN>(a, s, chk, st);
-    default: return cudaErrorInvalidValue;
-  }
-}
-
-}  // namespace
 
 // Run G generations from pop_in into pop_out (fitness of the final
 // population to fit_out; best member to best_row/best_fit when given) in
@@ -109,11 +37,15 @@ cudaError_t pick_solve(int NJ, const SolveArgs& a, const SolveShape& s, bool chk
 // 8, 4, 2, 1 CTAs that can be resident with this shared memory, never more
 // CTAs than members; it is found on the first call and kept in the context.
 // Returns cudaErrorNotSupported when no shape fits (the caller then runs
-// the per-generation kernels).
+// the per-generation kernels).  With isl given: island mode (Alg. 2), the
+// islands of isl_label with member lists isl (E <= 8 only).
 cudaError_t launch_solve(pa_ctx* ctx, const uint8_t* pop_in, uint8_t* pop_out, int gen0, int G,
-                         void* fit_out, uint8_t* best_row, double* best_fit, cudaStream_t st) {
+                         void* fit_out, uint8_t* best_row, double* best_fit, cudaStream_t st,
+                         const int32_t* isl_label, const IslandLists* isl) {
   if (ctx->solve_C == 0 || ctx->t32.streamed) return cudaErrorNotSupported;
   const pa_config& c = ctx->cfg;
+  if ((c.islands >= 2) != (isl != nullptr)) return cudaErrorNotSupported;
+  if (isl && c.E > kSmallE) return cudaErrorNotSupported;
   static const int sizes[] = {16, 8, 4, 2, 1};
   for (int C : sizes) {
     if (ctx->solve_C > 0 && C != ctx->solve_C) continue;
@@ -155,17 +87,27 @@ cudaError_t launch_solve(pa_ctx* ctx, const uint8_t* pop_in, uint8_t* pop_out, i
     a.pc64 = ctx->pc;
     a.fin = c.mode == PA_SINR_FINITE_M;
     a.obj = c.objective;
+    if (isl) {
+      a.isl_label = isl_label;
+      a.isl_off = isl->off;
+      a.isl_list = isl->list;
+      a.isl_pos = isl->pos;
+      a.isl_C = c.islands;
+    }
     const bool fin = a.fin;
     const bool chk = ctx->solve_C < 0;
     cudaError_t e;
-    if (c.prec == PA_FP64)
-      e = run_solve<double, 4, 2, false>(a, s, chk, st);
+    if (isl)
+      e = solve_island_dispatch(&a, &s, chk, c.prec == PA_FP64, ctx->t32.vec, fin, ctx->t32.NJ,
+                                st);
+    else if (c.prec == PA_FP64)
+      e = run_solve<double, 4, 2, false, false>(a, s, chk, st);
     else if (ctx->t32.vec == 2)
-      e = fin ? pick_solve<float, 2, true>(ctx->t32.NJ, a, s, chk, st)
-              : pick_solve<float, 2, false>(ctx->t32.NJ, a, s, chk, st);
+      e = fin ? pick_solve<float, 2, true, false>(ctx->t32.NJ, a, s, chk, st)
+              : pick_solve<float, 2, false, false>(ctx->t32.NJ, a, s, chk, st);
     else
-      e = fin ? pick_solve<float, 1, true>(ctx->t32.NJ, a, s, chk, st)
-              : pick_solve<float, 1, false>(ctx->t32.NJ, a, s, chk, st);
+      e = fin ? pick_solve<float, 1, true, false>(ctx->t32.NJ, a, s, chk, st)
+              : pick_solve<float, 1, false, false>(ctx->t32.NJ, a, s, chk, st);
     if (e == cudaErrorNotSupported) continue;
     if (e == cudaSuccess) ctx->solve_C = C;
     return e;

@@ -48,6 +48,14 @@ struct SolveArgs {
   int fin;
   int obj;  // PA_OBJ_MIN_SINR: smallest SINR instead of the SE sum
   unsigned long long* stamp;  // when given: %globaltimer (ns) once the outputs are complete
+  // island mode (Alg. 2) when isl_C >= 2: each member's island, the islands'
+  // member lists (off[C+1], list[N], ascending) and each member's position
+  // in its island; E <= kSmallE
+  const int32_t* isl_label;
+  const int32_t* isl_off;
+  const int32_t* isl_list;
+  const int32_t* isl_pos;
+  int isl_C;
 };
 
 template <typename FT>
@@ -154,6 +162,67 @@ __device__ __forceinline__ int tournament_lane(const FT* fit, int N, int T, cons
   return best;
 }
 
+// Tournament among the m members mem[0..m): candidates mem[u*m >> 32] for
+// the draws dr[0 .. T), the best by (fitness desc, index asc) wins.  Every
+// lane computes it.
+template <typename FT>
+__device__ __forceinline__ int tournament_list(const FT* fit, const int* mem, int m, int T,
+                                               const uint32_t* dr) {
+  int best = -1;
+  FT bv = (FT)0;
+  for (int t = 0; t < T; ++t) {
+    const int c = mem[below(dr[t], (uint32_t)m)];
+    const FT v = fit[c];
+    if (best < 0 || better_v(v, c, bv, best)) {
+      best = c;
+      bv = v;
+    }
+  }
+  return best;
+}
+
+// The E best (fitness desc, index asc) of the m members mem[0..m), E <= m,
+// by one warp in E rounds of a warp argmax; out[0..E) by lane 0.
+template <typename FT>
+__device__ __forceinline__ void warp_top_e_list(const FT* fit, const int* mem, int m, int E,
+                                                int lane, int* out) {
+  int chosen[kSmallE];
+#pragma unroll
+  for (int e = 0; e < kSmallE; ++e) {
+    chosen[e] = -1;
+    if (e < E) {
+      int best = -1;
+      FT bv = (FT)0;
+      for (int t = lane; t < m; t += 32) {
+        const int c = mem[t];
+        bool taken = false;
+#pragma unroll
+        for (int f = 0; f < e; ++f) taken |= chosen[f] == c;
+        if (taken) continue;
+        const FT v = fit[c];
+        if (best < 0 || better_v(v, c, bv, best)) {
+          best = c;
+          bv = v;
+        }
+      }
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) {
+        const int o = __shfl_xor_sync(0xffffffffu, best, off);
+        const FT ov = shfl_xor_ft(bv, off);
+        if (o >= 0 && (best < 0 || better_v(ov, o, bv, best))) {
+          best = o;
+          bv = ov;
+        }
+      }
+      chosen[e] = best;
+    }
+  }
+  if (lane == 0)
+#pragma unroll
+    for (int e = 0; e < kSmallE; ++e)
+      if (e < E) out[e] = chosen[e];
+}
+
 // Block-wide best member by (fitness desc, index asc), skipping excluded[0..nex).
 template <typename FT>
 __device__ int block_best_s(const FT* fit, int N, const int* excluded, int nex, int* red) {
@@ -248,7 +317,7 @@ __host__ __device__ constexpr int fused_js(int NJ, int maxnp) {
 // pilot of each user) at offset 0 and its inverse INV (L*K bytes, user of
 // each pilot, row by row) at offset XO.  Crossover takes whole rows, so the
 // child's INV rows are its parents' INV rows; a swap mutation updates both.
-template <typename FT, int NJ, int VEC, bool FIN, int MAXNP>
+template <typename FT, int NJ, int VEC, bool FIN, int MAXNP, bool ISL = false>
 __device__ __forceinline__ void solve_body(const SolveArgs& a, unsigned char* smem, int* elites,
                                            cg::cluster_group& cluster) {
   const int rank = (int)cluster.block_rank();
@@ -295,6 +364,15 @@ __device__ __forceinline__ void solve_body(const SolveArgs& a, unsigned char* sm
   // only: the space is not reserved otherwise)
   FT* CV = reinterpret_cast<FT*>(p);
   int* CI = reinterpret_cast<int*>(p + sizeof(FT) * 32 * 64);
+  // island mode (E <= kSmallE, so the candidates above are not reserved):
+  // labels, positions, member lists, offsets, each island's elites
+  const bool isl = ISL && a.isl_C >= 2;
+  const int iC = a.isl_C;
+  int* ilab = reinterpret_cast<int*>(p);
+  int* ipos = ilab + ((N + 3) & ~3);
+  int* ilist = ipos + ((N + 3) & ~3);
+  int* ioff = ilist + ((N + 3) & ~3);
+  int* ielite = ioff + ((iC + 4) & ~3);  // [C][kSmallE]
 
   const int base_n = rank * NT;
   const int nvalid = max(0, min(NT, N - base_n));
@@ -309,6 +387,14 @@ __device__ __forceinline__ void solve_body(const SolveArgs& a, unsigned char* sm
       for (int i = tid; i < L; i += blockDim.x) BN[i] = __ldg(a.bn + i);
   }
   for (int i = tid; i < NT * MS; i += blockDim.x) POPp(0)[i] = 0;
+  if (isl) {
+    for (int i = tid; i < N; i += blockDim.x) {
+      ilab[i] = min(max((int)a.isl_label[i], 0), iC - 1);
+      ipos[i] = a.isl_pos[i];
+      ilist[i] = a.isl_list[i];
+    }
+    for (int i = tid; i <= iC; i += blockDim.x) ioff[i] = a.isl_off[i];
+  }
   __syncthreads();
   for (int i = tid; i < nvalid * LK; i += blockDim.x) {
     const int c = i / LK, r = i - c * LK;
@@ -336,7 +422,8 @@ __device__ __forceinline__ void solve_body(const SolveArgs& a, unsigned char* sm
   // address) fall in distinct banks
   const int q = (tid / (16 * JS)) * 16 + (tid & 15), h = (tid >> 4) % JS;
   const bool one_chunk = nvalid <= a.CH;
-  const int n_elite_here = max(0, min(E - base_n, nvalid));
+  const int n_elite_here = isl ? 0 : max(0, min(E - base_n, nvalid));
+  const int E_draw = isl ? 0 : E;  // slots below E_draw take no draws (plain elites)
   for (int g = 0;; ++g) {
     FT* fit = FITp(g & 1);
     const unsigned char* popc = POPp(cur);
@@ -356,7 +443,7 @@ __device__ __forceinline__ void solve_body(const SolveArgs& a, unsigned char* sm
         } else if (c0 == 0 && one_chunk && g < a.G && eval_threads + 32 <= (int)blockDim.x &&
                    tid >= ((eval_threads + 31) & ~31)) {
           const int t0 = (eval_threads + 31) & ~31;
-          gen_child_draws_from(DR, base_n, nvalid, nblk, a.seed, (uint64_t)(a.gen0 + g), E,
+          gen_child_draws_from(DR, base_n, nvalid, nblk, a.seed, (uint64_t)(a.gen0 + g), E_draw,
                                tid - t0, blockDim.x - t0);
         }
         if (c0 == 0 && one_chunk && eval_threads + 32 <= (int)blockDim.x) drawn = true;
@@ -458,6 +545,14 @@ __device__ __forceinline__ void solve_body(const SolveArgs& a, unsigned char* sm
       }
       __syncthreads();
     }
+    if (isl) {
+      // each island's min(E, m_c) best members, a warp per island
+      for (int c = warp; c < iC; c += nwarps) {
+        const int m = ioff[c + 1] - ioff[c];
+        warp_top_e_list<FT>(fit, ilist + ioff[c], m, min(E, m), lane, ielite + c * kSmallE);
+      }
+      __syncthreads();
+    }
     if (n_elite_here > 0 && small_e && warp == 0) {
       if (E <= 2)
         warp_top_e_rounds<FT, 2, 8>(fit, N, E, lane, elites);
@@ -470,7 +565,7 @@ __device__ __forceinline__ void solve_body(const SolveArgs& a, unsigned char* sm
     for (int c0 = 0; c0 < nvalid; c0 += a.CH) {
       const int nc = min(a.CH, nvalid - c0);
       if (!(drawn && c0 == 0)) {
-        gen_child_draws(DR, base_n + c0, nc, nblk, a.seed, (uint64_t)(a.gen0 + g), E);
+        gen_child_draws(DR, base_n + c0, nc, nblk, a.seed, (uint64_t)(a.gen0 + g), E_draw);
         __syncthreads();
       }
       // elite slots of a small E are warp 0's (it found the elites); other
@@ -494,9 +589,27 @@ __device__ __forceinline__ void solve_body(const SolveArgs& a, unsigned char* sm
         uint32_t* child = reinterpret_cast<uint32_t*>(popn + slot * MS);
         int pa_, pb_;
         int64_t split;
-        if (n < E) {
+        bool elite = false;
+        if (isl) {
+          // slot n belongs to island c at position i: the island's rank-i
+          // member for i < min(E, m_c), else a child of two tournaments
+          // among the island's members
+          const int c = ilab[n], i = ipos[n], m = ioff[c + 1] - ioff[c];
+          if (i < min(E, m)) {
+            pa_ = pb_ = ielite[c * kSmallE + i];
+            split = LK;
+            elite = true;
+          } else {
+            pa_ = tournament_list(fit, ilist + ioff[c], m, T_, dr);
+            pb_ = tournament_list(fit, ilist + ioff[c], m, T_, dr + T_);
+            int cut = L;
+            if ((uint64_t)dr[2 * T_] < a.pc_thresh) cut = 1 + (int)below(dr[2 * T_ + 1], (uint32_t)(L - 1));
+            split = (int64_t)cut * K;
+          }
+        } else if (n < E) {
           pa_ = pb_ = elites[n];
           split = LK;
+          elite = true;
         } else {
           pa_ = tournament_lane(fit, N, T_, dr);
           pb_ = tournament_lane(fit, N, T_, dr + T_);
@@ -520,7 +633,7 @@ __device__ __forceinline__ void solve_body(const SolveArgs& a, unsigned char* sm
           reinterpret_cast<uint4*>(child)[v] = o;
         }
         __syncwarp();
-        if (n >= E) {
+        if (!elite) {
           uint8_t* cx = reinterpret_cast<uint8_t*>(child);
           for (int l = lane; l < L; l += 32) {
             const int base = 2 * T_ + 2 + 3 * l;
@@ -636,6 +749,10 @@ SolveShape solve_shape(const pa_ctx* ctx, int C, int maxnp, int threads) {
   b = (b + 15) & ~size_t(15);
   b += (size_t)s.CH * s.nblk * 32;
   if (c.E > kSmallE) b += (f64 ? 8 : 4) * 32 * 64 + 4 * 32 * 64;  // elite candidates
+  if (c.islands >= 2) {  // labels, positions, lists, offsets, island elites
+    const size_t N4 = (size_t)((c.N + 3) & ~3);
+    b += 4 * (3 * N4 + (size_t)((c.islands + 4) & ~3) + (size_t)c.islands * kSmallE);
+  }
   s.smem = (b + 15) & ~size_t(15);
   return s;
 }

@@ -164,6 +164,37 @@ def test_island_solve_in_pieces_equals_whole(B, oracle):
     assert gen == 12 and (pop == ref["pop"]).all()
 
 
+@pytest.mark.parametrize("prec,E,R", [(0, 2, 3), (0, 0, 2), (1, 3, 3), (0, 8, 4)])
+def test_island_fused_blocks_equal_per_generation_kernels(B, prec, E, R):
+    """pa_step runs the generations between re-clusterings as one cluster
+    launch (island mode of the fused solve); composing the per-generation
+    kernels through the ABI -- pa_island_cluster every R generations,
+    pa_eval_population, pa_island_step -- gives the same population and
+    labels bit for bit."""
+    L, K, N, C, G = 19, 10, 128, 5, 10
+    inst = inputs.instance(L, K, seed=12, dtype=np.float32)
+    cfg = _cfg(B, L, K, prec=prec, N=N, E=E, islands=C, recluster=R, seed=4)
+    with B.Context(cfg, inst["beta"], inst["user_xy_mm"], inst["bs_xy_mm"]) as ctx:
+        ctx.kmeans_seed()
+        pop0, _, _ = ctx.get_population(with_fitness=False)
+        ctx.step(G)
+        fused, _, gen = ctx.get_population(with_fitness=False)
+        labels_fused = B.pa_get_islands(ctx.handle, N)
+        cur = torch.from_numpy(pop0).cuda()
+        lab = torch.empty(N, dtype=torch.int32, device="cuda")
+        for g in range(G):
+            if g % R == 0:
+                B.pa_island_cluster(ctx.handle, cur, g, lab)
+            fit = ctx.eval_population(cur)
+            nxt = torch.empty_like(cur)
+            B.pa_island_step(ctx.handle, cur, fit, lab, g, nxt)
+            cur = nxt
+        torch.cuda.synchronize()
+    assert gen == G
+    assert (cur.cpu().numpy() == fused).all()
+    assert (lab.cpu().numpy() == labels_fused).all()
+
+
 def test_island_solve_fp32(B, oracle):
     L, K, N, C = 19, 10, 256, 5
     inst = inputs.instance(L, K, seed=7, dtype=np.float32)
