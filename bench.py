@@ -529,7 +529,7 @@ def run_batched(B, inputs, G=100, n=512, reps=3):
     t_batch = (time.perf_counter() - t0) / reps
     rows, fits = batch.solve(G)
     done_ms = np.sort(batch.completion_times_ms())  # per instance, since the batch started
-    _, cta_threads, _ = batch.group_shapes()
+    _, cta_threads, lat_split, _ = batch.group_tiling()
     batch.close()
     ctxs = [B.Context(d["cfg"], d["beta"], d["user_xy_mm"], d["bs_xy_mm"]) for d in insts]
     ctxs[0].solve(G)
@@ -561,6 +561,7 @@ def run_batched(B, inputs, G=100, n=512, reps=3):
             "batched": {"seconds_per_batch": t_batch, "solves_per_s": n / t_batch,
                         "evals_per_s": evals / t_batch, "cluster_sizes": [int(x) for x in chosen],
                         "cta_threads": [int(x) for x in cta_threads],
+                        "latency_split": [int(x) for x in lat_split],
                         "completion_ms": {"p50": q(done_ms, 50), "p99": q(done_ms, 99),
                                           "max": float(done_ms[-1]),
                                           "what": "each instance's completion since the batch "

@@ -321,18 +321,23 @@ pa_status pa_batch_load(pa_batch* b, int32_t i, const double* beta, const int32_
 /*
  * Autotune the tiling: for each kernel-variant group, time the group's
  * solve for `generations` generations on the batch itself with every shape
- * that fits -- CTAs of 1024 threads (one CTA per SM) or of 256 threads (four
- * per SM, so several instances share an SM), in clusters of 1, 2, 4, 8 or 16
- * CTAs per instance -- and keep the fastest.  chosen (optional, one entry
- * per group) receives the chosen cluster sizes (pa_batch_groups also gives
- * the CTA sizes).  Runs real solves (results are discarded).  Synchronous.
+ * that fits -- CTAs of 1024 threads (one CTA per SM; each evaluation thread
+ * takes up to five column pairs, or up to two as the one-instance solve
+ * does: the latency split) or of 256 threads (four per SM, so several
+ * instances share an SM), in clusters of 1, 2, 4, 8 or 16 CTAs per
+ * instance -- and keep the fastest, judged by the whole batch's time (the
+ * groups run concurrently).  chosen (optional, one entry per group)
+ * receives the chosen cluster sizes (pa_batch_groups gives the rest).
+ * Runs real solves (results are discarded).  Synchronous.
  */
 pa_status pa_batch_tune(pa_batch* b, int32_t generations, int32_t* chosen);
 
-/* Number of kernel-variant groups, their cluster sizes and CTA sizes
- * (threads), and the group of each instance (each output optional). */
+/* Number of kernel-variant groups, their cluster sizes, CTA sizes
+ * (threads) and column splits (1: the latency split), and the group of
+ * each instance (each output optional). */
 pa_status pa_batch_groups(pa_batch* b, int32_t* n_groups, int32_t* cluster_sizes,
-                          int32_t* cta_threads, int32_t* group_of_instance);
+                          int32_t* cta_threads, int32_t* latency_split,
+                          int32_t* group_of_instance);
 
 /*
  * Solve every instance (Alg. 1 as in pa_solve): best_host receives the best

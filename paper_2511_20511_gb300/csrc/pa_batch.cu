@@ -38,6 +38,7 @@ struct pa_batch {
     std::vector<int> members;
     int C = 0;
     int threads = 1024;  // CTA size: 1024 (one CTA per SM) or 256 (four per SM)
+    bool latency = false;  // 1024-thread CTAs with the one-instance column split
     int clusters = 0;
     size_t smem = 0;
     std::vector<unsigned char> h_args;
@@ -107,7 +108,8 @@ void destroy_batch(pa_batch* b) {
 
 // (Re)build one group's argument records for cluster size C and G
 // generations; 0 on success, else the status.
-pa_status build_group_args(pa_batch* b, pa_batch::Group& g, int C, int G, int threads) {
+pa_status build_group_args(pa_batch* b, pa_batch::Group& g, int C, int G, int threads,
+                           bool latency) {
   const size_t ab = pa::solve_args_bytes();
   std::vector<unsigned char> h(ab * g.members.size());
   size_t smem = 0;
@@ -116,12 +118,12 @@ pa_status build_group_args(pa_batch* b, pa_batch::Group& g, int C, int G, int th
     pa_ctx* c = b->ctx[i];
     const size_t s = pa::solve_fill_args(c, C, 0, G, c->pop[0], c->pop[1], c->fit,
                                          b->d_best + b->best_off[i], b->d_bestfit + i,
-                                         h.data() + m * ab, false, threads);
+                                         h.data() + m * ab, latency, threads);
     if (s == 0) return PA_EUNSUPPORTED;
     pa::solve_args_set_stamp(h.data() + m * ab, b->d_stamp + i);
     smem = std::max(smem, s);
   }
-  const int maxc = pa::solve_batch_max_clusters(b->ctx[g.members[0]], C, smem, false, threads);
+  const int maxc = pa::solve_batch_max_clusters(b->ctx[g.members[0]], C, smem, latency, threads);
   if (maxc < 1) return PA_EUNSUPPORTED;
   if (!g.d_args) {
     pa_status st = bcuda(b, cudaMalloc(&g.d_args, h.size()), "cudaMalloc batch args");
@@ -133,6 +135,7 @@ pa_status build_group_args(pa_batch* b, pa_batch::Group& g, int C, int G, int th
   g.h_args.swap(h);
   g.C = C;
   g.threads = threads;
+  g.latency = latency;
   g.smem = smem;
   g.clusters = std::min<int>((int)g.members.size(), maxc);
   return PA_OK;
@@ -167,7 +170,7 @@ pa_status run_groups(pa_batch* b, cudaStream_t st) {
     if (s != PA_OK) return s;
     s = bcuda(b, pa::launch_solve_batch(b->ctx[g.members[0]], g.C, g.clusters, g.d_args,
                                         (int)g.members.size(), b->d_counters + k, g.smem, g.side,
-                                        false, g.threads),
+                                        g.latency, g.threads),
               "batched solve kernel");
     if (s != PA_OK) return s;
     s = bcuda(b, cudaEventRecord(g.done, g.side), "join");
@@ -304,7 +307,7 @@ pa_status pa_batch_create(int32_t n, const pa_config* cfgs, const double* const*
     for (int C = C0 / 2; C >= 1; C /= 2) order.push_back(C);
     pa_status gs = PA_EUNSUPPORTED;
     for (int C : order) {
-      gs = build_group_args(b, g, C, 1, 1024);
+      gs = build_group_args(b, g, C, 1, 1024, false);
       if (gs != PA_EUNSUPPORTED) break;
     }
     if (gs != PA_OK) st = bfail(b, gs, "an instance of the batch does not fit the solve kernel");
@@ -359,20 +362,27 @@ pa_status pa_batch_tune(pa_batch* b, int32_t generations, int32_t* chosen) {
     }
   };
   for (auto& g : b->groups)
-    if (st == PA_OK) st = build_group_args(b, g, g.C, generations, g.threads);
+    if (st == PA_OK) st = build_group_args(b, g, g.C, generations, g.threads, g.latency);
   for (size_t k = 0; k < b->groups.size() && st == PA_OK; ++k) {
     auto& g = b->groups[k];
     int best_C = g.C, best_T = g.threads;
+    bool best_lat = g.latency;
     float best_ms = 0.f;
     time_all(&best_ms);
-    // the tiling choice: clusters of 1024-thread CTAs (one CTA per SM) or of
+    // the tiling choice: clusters of 1024-thread CTAs (one CTA per SM; the
+    // throughput column split, or the one-instance latency split) or of
     // 256-thread CTAs (four per SM, several instances sharing an SM), each
     // with 1 to 16 CTAs per instance
-    for (int T : {1024, 256})
+    struct Tiling {
+      int T;
+      bool lat;
+    };
+    for (const Tiling tl : {Tiling{1024, false}, Tiling{1024, true}, Tiling{256, false}})
       for (int C : {1, 2, 4, 8, 16}) {
+        const int T = tl.T;
         if (st != PA_OK) break;
-        if (T == best_T && C == best_C) continue;
-        pa_status gs = build_group_args(b, g, C, generations, T);
+        if (T == best_T && tl.lat == best_lat && C == best_C) continue;
+        pa_status gs = build_group_args(b, g, C, generations, T, tl.lat);
         if (gs == PA_EUNSUPPORTED) continue;
         if (gs != PA_OK) {
           st = gs;
@@ -384,13 +394,14 @@ pa_status pa_batch_tune(pa_batch* b, int32_t generations, int32_t* chosen) {
           best_ms = ms;
           best_C = C;
           best_T = T;
+          best_lat = tl.lat;
         }
       }
-    if (st == PA_OK) st = build_group_args(b, g, best_C, generations, best_T);
+    if (st == PA_OK) st = build_group_args(b, g, best_C, generations, best_T, best_lat);
     if (chosen && st == PA_OK) chosen[k] = best_C;
   }
   for (auto& g : b->groups)  // arguments of one generation until the next solve rebuilds them
-    if (st == PA_OK) st = build_group_args(b, g, g.C, 1, g.threads);
+    if (st == PA_OK) st = build_group_args(b, g, g.C, 1, g.threads, g.latency);
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
   b->graph_G = -1;  // the captured graph used the previous shapes
@@ -402,12 +413,14 @@ pa_status pa_batch_tune(pa_batch* b, int32_t generations, int32_t* chosen) {
 }
 
 pa_status pa_batch_groups(pa_batch* b, int32_t* n_groups, int32_t* cluster_sizes,
-                          int32_t* cta_threads, int32_t* group_of_instance) {
+                          int32_t* cta_threads, int32_t* latency_split,
+                          int32_t* group_of_instance) {
   if (!b) return PA_EINVAL;
   if (n_groups) *n_groups = (int32_t)b->groups.size();
   for (size_t k = 0; k < b->groups.size(); ++k) {
     if (cluster_sizes) cluster_sizes[k] = b->groups[k].C;
     if (cta_threads) cta_threads[k] = b->groups[k].threads;
+    if (latency_split) latency_split[k] = b->groups[k].latency ? 1 : 0;
     if (group_of_instance)
       for (int i : b->groups[k].members) group_of_instance[i] = (int32_t)k;
   }
@@ -424,7 +437,7 @@ pa_status pa_batch_solve(pa_batch* b, int32_t generations, uint8_t* best_host, d
       b->graph = nullptr;
     }
     for (auto& g : b->groups) {
-      st = build_group_args(b, g, g.C, generations, g.threads);
+      st = build_group_args(b, g, g.C, generations, g.threads, g.latency);
       if (st != PA_OK) return bfail(b, st, "rebuilding batch arguments failed");
     }
     cudaGraph_t graph = nullptr;
