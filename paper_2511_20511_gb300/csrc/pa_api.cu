@@ -481,10 +481,27 @@ static pa_status run_generations(pa_ctx* ctx, int32_t generations, bool* final_e
   if (ctx->cfg.islands >= 2) {
     // Alg. 2: every `recluster` generations (and whenever the labels do not
     // belong to this population) K-means into islands and their member
-    // lists; the generations up to the next re-clustering then run in one
-    // cluster launch of the fused solve in island mode (which leaves the
-    // final population's fitness), or where that does not fit one at a time
-    // (fitness, one island generation)
+    // lists, and island generations in between.  All of it in one cluster
+    // launch of the fused solve in island mode, the K-means included, where
+    // that fits in shared memory; else per block of generations up to the
+    // next re-clustering: the K-means and list kernels, then one fused
+    // launch (or, where that does not fit either, one generation at a time:
+    // fitness, one island generation).  The fused launches leave the final
+    // population's fitness.
+    {
+      const cudaError_t e = pa::launch_solve(ctx, ctx->pop[ctx->cur], ctx->pop[ctx->cur ^ 1],
+                                             ctx->generation, generations, ctx->fit, nullptr,
+                                             nullptr, ctx->stream, ctx->isl_label,
+                                             &ctx->isl_res, true);
+      if (e == cudaSuccess) {
+        ctx->cur ^= 1;
+        ctx->generation += generations;
+        ctx->isl_valid = 1;
+        *final_evaluated = true;
+        return PA_OK;
+      }
+      if (e != cudaErrorNotSupported) return cuda_check(ctx, e, "island solve kernel");
+    }
     int32_t done = 0;
     while (done < generations) {
       uint8_t* cur = ctx->pop[ctx->cur];

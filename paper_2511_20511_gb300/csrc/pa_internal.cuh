@@ -131,10 +131,12 @@ cudaError_t launch_seed(pa_ctx* ctx, uint8_t* pop, cudaStream_t st);
 cudaError_t launch_argbest(const pa_ctx* ctx, const void* fit, const uint8_t* pop,
                            uint8_t* best_row, double* best_fit_dev, cudaStream_t st);
 // pa_solve.cu
-// isl_label / isl: island mode (Alg. 2) with these labels and member lists
+// isl_label / isl: island mode (Alg. 2) with these labels and member lists;
+// isl_km: the re-clustering inside the launch (labels and lists written back)
 cudaError_t launch_solve(pa_ctx* ctx, const uint8_t* pop_in, uint8_t* pop_out, int gen0, int G,
                          void* fit_out, uint8_t* best_row, double* best_fit, cudaStream_t st,
-                         const int32_t* isl_label = nullptr, const IslandLists* isl = nullptr);
+                         int32_t* isl_label = nullptr, IslandLists* isl = nullptr,
+                         bool isl_km = false);
 size_t solve_args_bytes();
 // latency: the one-instance kernel's column split (few concurrent
 // instances) instead of the throughput split; threads: CTA size, 1024 (one

@@ -39,16 +39,12 @@
 #include <algorithm>
 #include <atomic>
 
-#include "pa_internal.cuh"
+#include "pa_island_kmeans.cuh"
 
 namespace pa {
 namespace {
 
-namespace cg = cooperative_groups;
-
 constexpr int kIslandThreads = 1024;
-constexpr int kKmMaxW = 8;   // pair words of counts one lane sums at once (16 clusters)
-constexpr int kKmSplits = 8; // most warps sharing one group of 32 members (user ranges)
 
 struct KmArgs {
   const uint8_t* pop;  // [N][LK]
@@ -92,89 +88,6 @@ KmLayout km_layout(int N, int L, int K, int C, bool cnt_in_smem, bool pop_in_sme
 }
 
 constexpr size_t kKmSmemBudget = (size_t)kSmemBudget - 4096;  // beside the static arrays
-
-__device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v) {
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-  return v;
-}
-
-// Pilot of user u of member n (a pilot >= K reads as K-1): from the staged
-// words (clamped when staged), or from the rows.
-template <bool PS>
-__device__ __forceinline__ int km_pilot(const uint32_t* pw, int NP, const uint8_t* pop, int LK,
-                                        int K, int n, int u) {
-  if (PS) return (int)((pw[(u >> 2) * NP + n] >> (8 * (u & 3))) & 0xffu);
-  return min((int)pop[(int64_t)n * LK + u], K - 1);
-}
-
-// Word w of member n: the (clamped) pilots of users 4w .. 4w+3, low byte
-// first; bytes past the row end are K-1.
-template <bool PS>
-__device__ __forceinline__ uint32_t km_word(const uint32_t* pw, int NP, const uint8_t* pop, int LK,
-                                            int K, int n, int w) {
-  if (PS) return pw[w * NP + n];
-  uint32_t v = 0;
-#pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    const int u = 4 * w + j;
-    v |= (uint32_t)(u < LK ? min((int)pop[(int64_t)n * LK + u], K - 1) : K - 1) << (8 * j);
-  }
-  return v;
-}
-
-// S(n, c) for the 2*NW clusters of pair words i0 .. i0+NW-1 over the users
-// of words w0 .. w1-1: a lane sums packed 16-bit pairs (one load serves two
-// clusters) for wblk words at a time -- a half stays below 2^16 since each
-// count is at most N -- and widens them into S.  Words below wfull hold
-// four users each; only the row's last word is checked.
-template <int NW, bool PS>
-__device__ __forceinline__ void km_sums(int (&S)[2 * kKmMaxW], const uint32_t* cnt, int CWp,
-                                        int i0, int K, int LK, int w0, int w1, int wblk,
-                                        const uint32_t* pw, int NP, const uint8_t* pop, int n) {
-  const int wfull = LK >> 2, KC = K * CWp;
-#pragma unroll
-  for (int q = 0; q < 2 * NW; ++q) S[q] = 0;
-  for (int wb = w0; wb < w1; wb += wblk) {
-    const int we = min(w1, wb + wblk);
-    uint32_t P[NW];
-#pragma unroll
-    for (int i = 0; i < NW; ++i) P[i] = 0;
-    int w = wb;
-    for (; w < min(we, wfull); ++w) {
-      const uint32_t v = km_word<PS>(pw, NP, pop, LK, K, n, w);
-      const uint32_t* row = cnt + 4 * w * KC + i0;
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const uint32_t* e = row + j * KC + (int)((v >> (8 * j)) & 0xffu) * CWp;
-#pragma unroll
-        for (int i = 0; i < NW; ++i) P[i] += e[i];
-      }
-    }
-    for (; w < we; ++w) {  // the row's last, partial word
-      const uint32_t v = km_word<PS>(pw, NP, pop, LK, K, n, w);
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const int u = 4 * w + j;
-        if (u < LK) {
-          const uint32_t* e = cnt + u * KC + (int)((v >> (8 * j)) & 0xffu) * CWp + i0;
-#pragma unroll
-          for (int i = 0; i < NW; ++i) P[i] += e[i];
-        }
-      }
-    }
-#pragma unroll
-    for (int i = 0; i < NW; ++i) {
-      S[2 * i] += (int)(P[i] & 0xffffu);
-      S[2 * i + 1] += (int)(P[i] >> 16);
-    }
-  }
-}
-
-// Half h (0: low, 16: high) of a packed word.
-__device__ __forceinline__ long long km_half(uint32_t v, int h) {
-  return (long long)((v >> h) & 0xffffu);
-}
 
 // Every loop below is a nested 32-bit loop (counts and members stay below
 // 2^24 entries: L*K*K*CWp and N*L*K for N, L*K <= 4096).
@@ -413,297 +326,54 @@ __global__ void __launch_bounds__(kIslandThreads) k_island_kmeans(const KmArgs a
   if (tid == 0 && a.passes) *a.passes = passes;
 }
 
-// The cluster form of k_island_kmeans: CTA r of R assigns members
-// [N r / R, N (r+1) / R); every CTA holds the whole staged population and
-// its own copy of the counts, Q, m and the initial centroids (all computed
-// identically).  A pass: assignment of the own slice, the changed members
-// listed per CTA; one cluster barrier; every CTA reads the other CTAs'
-// changed lists and cluster sizes (distributed shared memory), decides the
-// same stop, and replays all changed members into its counts.  Lists and
-// sizes are double-buffered by pass parity, so a CTA can list the next
-// pass's changes while another still reads this pass's.
-struct KmClLayout {
-  int NP, W, us, Nr;
-  size_t o_lab, o_chg, o_gchg, o_cnt, o_sb, o_pw, total;
-};
-
-KmClLayout km_cl_layout(int N, int L, int K, int C, int R, int us) {
-  KmClLayout k;
-  const size_t LK = (size_t)L * K;
-  const int CWp = ((C + 1) / 2) | 1;
-  const size_t N4 = (size_t)((N + 3) & ~3);
-  k.NP = N | 1;
-  k.W = (int)((LK + 3) / 4);
-  k.us = us;
-  k.Nr = (N + R - 1) / R;
-  size_t b = 0;
-  k.o_lab = b;   // [N] labels of the own slice (whole range allocated)
-  b += 4 * N4;   // + [N] initial permutation
-  b += 4 * N4;
-  k.o_chg = b;   // [2][N] own changed members per pass parity
-  b += 4 * 2 * N4;
-  k.o_gchg = b;  // [N] every CTA's changed members of this pass
-  b += 4 * N4;
-  k.o_cnt = b;
-  b += 4 * LK * K * CWp;
-  k.o_sb = b;
-  if (us > 1) b += 4 * (size_t)us * C * k.Nr;
-  b = (b + 15) & ~size_t(15);
-  k.o_pw = b;
-  b += 4 * (size_t)k.W * k.NP;
-  k.total = (b + 15) & ~size_t(15);
-  return k;
-}
-
-constexpr int kKmClusterMax = 8;
-
 struct KmClArgs {
   KmArgs a;
   int Nr;
   int o_lab, o_chg, o_gchg;
 };
 
+// The cluster K-means from a population in global memory.
 __global__ void __launch_bounds__(kIslandThreads) k_island_kmeans_cl(const KmClArgs ca) {
   cg::cluster_group cluster = cg::this_cluster();
   const KmArgs& a = ca.a;
   extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ unsigned long long Q[kMaxIslands];
-  __shared__ int m[kMaxIslands];       // centroid sizes
-  __shared__ int nm[kMaxIslands];      // sizes of the new partition (all CTAs)
-  __shared__ int live[kMaxIslands];    // the cluster has members in the new partition
-  __shared__ int stale[kMaxIslands];   // its counts are not the sum over its members
-  __shared__ uint32_t rdraw[kMaxIslands];
-  __shared__ int nm_own[2][kMaxIslands];  // own slice's sizes, per pass parity
-  __shared__ int nchg_own[2];             // own slice's changed members, per pass parity
-  __shared__ int cnt_r[kKmClusterMax];    // changed members of each CTA in this pass
-  const int R = (int)cluster.num_blocks(), rank = (int)cluster.block_rank();
-  const int N = a.N, K = a.K, C = a.C, LK = a.L * a.K, LKK = LK * a.K;
-  const int CW = (C + 1) >> 1, CWp = a.CWp, NP = a.NP, W = (LK + 3) >> 2, us = a.us;
-  const int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31, warp = tid >> 5;
-  const int nwarps = nthr >> 5;
-  const unsigned full = 0xffffffffu;
-  const int n_lo = (int)((long long)N * rank / R), n_hi = (int)((long long)N * (rank + 1) / R);
-  const int Nr = ca.Nr;
-  int* lab = reinterpret_cast<int*>(smem + ca.o_lab);             // [N]
-  int* perm = lab + ((N + 3) & ~3);                               // [N]
-  int* chg = reinterpret_cast<int*>(smem + ca.o_chg);             // [2][N4]
-  int* gchg = reinterpret_cast<int*>(smem + ca.o_gchg);           // [N]
-  uint32_t* cnt = reinterpret_cast<uint32_t*>(smem + a.o_cnt);    // [LK*K][CWp]
-  int* sb = reinterpret_cast<int*>(smem + a.o_sb);                // [us][C][Nr]
-  uint32_t* pw = reinterpret_cast<uint32_t*>(smem + a.o_pw);      // [W][NP]
-  const int N4 = (N + 3) & ~3;
-  if (warp == nwarps - 1) {
-    for (int c = lane; c < C; c += 32) {
-      DrawStream ds(a.seed, 0, (uint64_t)a.gen, kTagIsland);
-      rdraw[c] = below(ds.draw((uint32_t)c), (uint32_t)(N - c));
-    }
-  } else {
-    const int sw = nwarps - 1, st = nthr - 32;
+  __shared__ KmShared sh;
+  const int N = a.N, K = a.K, LK = a.L * a.K, W = (LK + 3) >> 2, NP = a.NP;
+  KmView v;
+  v.sh = &sh;
+  v.pw = reinterpret_cast<uint32_t*>(smem + a.o_pw);
+  v.NP = NP;
+  v.cnt = reinterpret_cast<uint32_t*>(smem + a.o_cnt);
+  v.CWp = a.CWp;
+  v.lab = reinterpret_cast<int*>(smem + ca.o_lab);
+  v.perm = v.lab + ((N + 3) & ~3);
+  v.chg = reinterpret_cast<int*>(smem + ca.o_chg);
+  v.gchg = reinterpret_cast<int*>(smem + ca.o_gchg);
+  v.sb = reinterpret_cast<int*>(smem + a.o_sb);
+  v.us = a.us;
+  v.Nr = ca.Nr;
+  const KmParams p{a.N, a.L, a.K, a.C, a.max_iter, a.seed, a.gen};
+  uint32_t* pw = v.pw;
+  const uint8_t* pop = a.pop;
+  // word w of member n holds the pilots of users 4w .. 4w+3
+  const int passes = km_cluster(v, p, cluster, [&](int warp, int sw, int lane) {
     for (int n = warp; n < N; n += sw) {
-      const uint8_t* X = a.pop + (int64_t)n * LK;
+      const uint8_t* X = pop + (int64_t)n * LK;
       for (int w = lane; w < W; w += 32) {
-        uint32_t v = 0;
+        uint32_t x = 0;
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
           const int u = 4 * w + j;
-          v |= (uint32_t)(u < LK ? min((int)X[u], K - 1) : K - 1) << (8 * j);
+          x |= (uint32_t)(u < LK ? min((int)X[u], K - 1) : K - 1) << (8 * j);
         }
-        pw[w * NP + n] = v;
+        pw[w * NP + n] = x;
       }
     }
-    for (int i = tid; i < LKK * CWp; i += st) cnt[i] = 0;
-    for (int n = tid; n < N; n += st) {
-      perm[n] = n;
-      lab[n] = -1;
-    }
-    if (tid < kMaxIslands) {
-      Q[tid] = 0ULL;
-      stale[tid] = 1;
-      nm_own[0][tid] = 0;
-      nm_own[1][tid] = 0;
-    }
-    if (tid < 2) nchg_own[tid] = 0;
-  }
-  __syncthreads();
-  if (tid == 0) {
-    for (int c = 0; c < C; ++c) {
-      const int j = c + (int)rdraw[c];
-      const int t = perm[c];
-      perm[c] = perm[j];
-      perm[j] = t;
-      m[c] = 1;
-    }
-  }
-  __syncthreads();
-  for (int c = warp; c < C; c += nwarps) {
-    const int n = perm[c], h = (c & 1) * 16;
-    unsigned long long dq = 0;
-    for (int u = lane; u < LK; u += 32) {
-      const int x = km_pilot<true>(pw, NP, a.pop, LK, K, n, u);
-      const uint32_t o = atomicAdd(cnt + (u * K + x) * CWp + (c >> 1), 1u << h);
-      dq += (unsigned long long)(2 * km_half(o, h) + 1);
-    }
-    dq = warp_sum_u64(dq);
-    if (lane == 0) atomicAdd(&Q[c], dq);
-  }
-  __syncthreads();
-  const int G = (n_hi - n_lo + 31) >> 5;
-  const int wblk = max(1, 65535 / (4 * N));
-  auto fold = [&](int c, long long S, int& best, long long& bd) {
-    const long long mc = m[c];
-    const long long A = (long long)LK * mc * mc - 2 * mc * S + (long long)Q[c];
-    const long long mb = m[best];
-    if (c == 0 || A * mb * mb < bd * mc * mc) {
-      best = c;
-      bd = A;
-    }
-  };
-  auto record = [&](int n, int best, int par) {
-    const bool valid = n < n_hi;
-    const int old = valid ? lab[n] : 0;
-    const bool moved = valid && old != best;
-    const unsigned bm = __ballot_sync(full, moved);
-    if (bm) {
-      const int leader = __ffs(bm) - 1;
-      int base = 0;
-      if (lane == leader) base = atomicAdd(&nchg_own[par], __popc(bm));
-      base = __shfl_sync(full, base, leader);
-      if (moved)
-        chg[par * N4 + base + __popc(bm & ((1u << lane) - 1u))] = (n << 13) | ((old + 1) << 6) | best;
-    }
-    const unsigned same = __match_any_sync(full, valid ? best : -1 - lane);
-    if (valid) {
-      lab[n] = best;
-      if ((int)(__ffs(same) - 1) == lane) atomicAdd(&nm_own[par][best], __popc(same));
-    }
-  };
-  int passes = 0;
-  for (int it = 0; it < a.max_iter; ++it) {
-    const int par = it & 1;
-    // ---- assignment of the own slice
-    for (int t = warp; t < G * us; t += nwarps) {
-      const int g = t / us, s = t - g * us;
-      const int n = n_lo + g * 32 + lane;
-      const int nn = n < n_hi ? n : n_hi - 1;
-      const int w0 = (int)((long long)W * s / us), w1 = (int)((long long)W * (s + 1) / us);
-      int best = 0;
-      long long bd = 0;
-      for (int c0 = 0; c0 < C; c0 += 2 * kKmMaxW) {
-        int S[2 * kKmMaxW];
-        const int i0 = c0 >> 1;
-        switch (min(kKmMaxW, CW - i0)) {
-#define PA_KM_CASE(NW)                                                                    \
-  case NW:                                                                                \
-    km_sums<NW, true>(S, cnt, CWp, i0, K, LK, w0, w1, wblk, pw, NP, a.pop, nn);           \
-    break;
-          PA_KM_CASE(1)
-          PA_KM_CASE(2)
-          PA_KM_CASE(3)
-          PA_KM_CASE(4)
-          PA_KM_CASE(5)
-          PA_KM_CASE(6)
-          PA_KM_CASE(7)
-          default:
-            km_sums<8, true>(S, cnt, CWp, i0, K, LK, w0, w1, wblk, pw, NP, a.pop, nn);
-#undef PA_KM_CASE
-        }
-#pragma unroll
-        for (int q = 0; q < 2 * kKmMaxW; ++q) {
-          const int c = c0 + q;
-          if (c < C) {
-            if (us > 1) {
-              if (n < n_hi) sb[(s * C + c) * Nr + (n - n_lo)] = S[q];
-            } else {
-              fold(c, S[q], best, bd);
-            }
-          }
-        }
-      }
-      if (us == 1) record(n, best, par);
-    }
-    __syncthreads();
-    if (us > 1) {
-      for (int n0 = n_lo + warp * 32; n0 < n_hi; n0 += nthr) {
-        const int n = n0 + lane;
-        int best = 0;
-        long long bd = 0;
-        if (n < n_hi)
-          for (int c = 0; c < C; ++c) {
-            int S = 0;
-            for (int s = 0; s < us; ++s) S += sb[(s * C + c) * Nr + (n - n_lo)];
-            fold(c, S, best, bd);
-          }
-        record(n, best, par);
-      }
-    }
-    // ---- every CTA's labels, lists and sizes of this pass are visible
-    cluster.sync();
-    if (tid < R) cnt_r[tid] = *cluster.map_shared_rank(&nchg_own[par], tid);
-    if (tid >= 32 && tid < 32 + C) {
-      const int c = tid - 32;
-      int v = 0;
-      for (int r = 0; r < R; ++r) v += *cluster.map_shared_rank(&nm_own[par][c], r);
-      nm[c] = v;
-    }
-    __syncthreads();
-    int total = 0;
-    for (int r = 0; r < R; ++r) total += cnt_r[r];
-    ++passes;
-    if (total == 0 || it == a.max_iter - 1) break;
-    // every CTA's changed members, in CTA order
-    for (int k = tid; k < total; k += nthr) {
-      int r = 0, base = 0;
-      while (k >= base + cnt_r[r]) {
-        base += cnt_r[r];
-        ++r;
-      }
-      gchg[k] = *cluster.map_shared_rank(chg + par * N4 + (k - base), r);
-    }
-    for (int e = tid; e < LKK; e += nthr)
-      for (int i = 0; i < CW; ++i) {
-        const bool z0 = stale[2 * i] && nm[2 * i] > 0;
-        const bool z1 = 2 * i + 1 < C && stale[2 * i + 1] && nm[2 * i + 1] > 0;
-        if (z0 || z1) cnt[e * CWp + i] &= (z0 ? 0u : 0xffffu) | (z1 ? 0u : 0xffff0000u);
-      }
-    if (tid < C) {
-      live[tid] = nm[tid] > 0;
-      if (nm[tid] > 0) {
-        if (stale[tid]) Q[tid] = 0ULL;
-        m[tid] = nm[tid];
-      }
-    }
-    // the other parity's own lists were last read before this pass's barrier
-    if (tid < kMaxIslands) nm_own[par ^ 1][tid] = 0;
-    if (tid == 0) nchg_own[par ^ 1] = 0;
-    __syncthreads();
-    for (int k = warp; k < total; k += nwarps) {
-      const int e = gchg[k], n = e >> 13, A = ((e >> 6) & 127) - 1, Bc = e & 63;
-      const bool sub = A >= 0 && live[A];
-      const int hb = (Bc & 1) * 16, ha = (A & 1) * 16;
-      uint32_t* pb = cnt + (Bc >> 1);
-      uint32_t* pold = cnt + (sub ? A >> 1 : 0);
-      unsigned long long dqb = 0, dqa = 0;
-      for (int u = lane; u < LK; u += 32) {
-        const int o = (u * K + km_pilot<true>(pw, NP, a.pop, LK, K, n, u)) * CWp;
-        const uint32_t ob = atomicAdd(pb + o, 1u << hb);
-        dqb += (unsigned long long)(2 * km_half(ob, hb) + 1);
-        if (sub) {
-          const uint32_t oa = atomicAdd(pold + o, 0u - (1u << ha));
-          dqa += (unsigned long long)(1 - 2 * km_half(oa, ha));
-        }
-      }
-      dqb = warp_sum_u64(dqb);
-      dqa = warp_sum_u64(dqa);
-      if (lane == 0) {
-        atomicAdd(&Q[Bc], dqb);
-        if (sub) atomicAdd(&Q[A], dqa);
-      }
-    }
-    if (tid < C) stale[tid] = nm[tid] == 0;
-    __syncthreads();
-  }
-  for (int n = n_lo + tid; n < n_hi; n += nthr) a.label[n] = lab[n];
-  if (rank == 0 && tid == 0 && a.passes) *a.passes = passes;
+  });
+  const int R = (int)cluster.num_blocks(), rank = (int)cluster.block_rank();
+  const int n_lo = (int)((long long)N * rank / R), n_hi = (int)((long long)N * (rank + 1) / R);
+  for (int n = n_lo + (int)threadIdx.x; n < n_hi; n += blockDim.x) a.label[n] = v.lab[n];
+  if (rank == 0 && threadIdx.x == 0 && a.passes) *a.passes = passes;
   cluster.sync();  // the other CTAs may still read this CTA's lists
 }
 
@@ -904,7 +574,7 @@ cudaError_t launch_island_kmeans_cl(const pa_ctx* ctx, const uint8_t* pop, int g
                                     cudaStream_t st) {
   const pa_config& c = ctx->cfg;
   if (c.N < 64) return cudaErrorNotSupported;
-  const int R = std::min(kKmClusterMax, std::max(2, c.N / 32));
+  const int R = std::min(8, std::max(2, c.N / 32));  // portable cluster sizes
   const int Nr = (c.N + R - 1) / R;
   const int groups = (Nr + 31) / 32, W = (c.L * c.K + 3) / 4;
   int us = std::max(1, std::min({kKmSplits, kIslandThreads / 32 / groups, W}));

@@ -41,7 +41,7 @@ namespace pa {
 // islands of isl_label with member lists isl (E <= 8 only).
 cudaError_t launch_solve(pa_ctx* ctx, const uint8_t* pop_in, uint8_t* pop_out, int gen0, int G,
                          void* fit_out, uint8_t* best_row, double* best_fit, cudaStream_t st,
-                         const int32_t* isl_label, const IslandLists* isl) {
+                         int32_t* isl_label, IslandLists* isl, bool isl_km) {
   if (ctx->solve_C == 0 || ctx->t32.streamed) return cudaErrorNotSupported;
   const pa_config& c = ctx->cfg;
   if ((c.islands >= 2) != (isl != nullptr)) return cudaErrorNotSupported;
@@ -50,9 +50,41 @@ cudaError_t launch_solve(pa_ctx* ctx, const uint8_t* pop_in, uint8_t* pop_out, i
   for (int C : sizes) {
     if (ctx->solve_C > 0 && C != ctx->solve_C) continue;
     if (C > c.N) continue;
-    const SolveShape s = solve_shape(ctx, C, kSoloMaxNP, kSolveThreads);
+    SolveShape s = solve_shape(ctx, C, kSoloMaxNP, kSolveThreads);
     if (s.smem > (size_t)kSmemBudget - 64 * 4) continue;
     SolveArgs a{};
+    if (isl_km) {  // K-means arrays after the solve's (KmView of pa_island_kmeans.cuh)
+      const size_t N4 = (size_t)((c.N + 3) & ~3), LK = (size_t)c.L * c.K;
+      const int W = (int)((LK + 3) / 4), NP = c.N | 1, CWp = ((c.islands + 1) / 2) | 1;
+      const int Nr = (c.N + C - 1) / C, groups = (Nr + 31) / 32;
+      auto r16 = [](size_t v) { return (v + 15) & ~size_t(15); };
+      bool fits = false;
+      for (int us = std::max(1, std::min({kKmSplits, kSolveThreads / 32 / groups, W})); us >= 1;
+           --us) {
+        size_t b = r16(s.smem);
+        a.o_ksh = (int)b;
+        b = r16(b + sizeof(KmShared));
+        a.o_kpw = (int)b;
+        b = r16(b + 4 * (size_t)W * NP);
+        a.o_kcnt = (int)b;
+        b = r16(b + 4 * LK * c.K * CWp);
+        a.o_klab = (int)b;
+        b += 4 * 2 * N4;  // labels, initial permutation
+        a.o_kchg = (int)b;
+        b += 4 * 2 * N4;
+        a.o_kgchg = (int)b;
+        b += 4 * N4;
+        a.o_ksb = (int)b;
+        if (us > 1) b += 4 * (size_t)us * c.islands * Nr;
+        a.isl_us = us;
+        if (r16(b) <= (size_t)kSmemBudget - 64 * 4) {
+          s.smem = r16(b);
+          fits = true;
+          break;
+        }
+      }
+      if (!fits) continue;  // no room beside the solve at this cluster size
+    }
     a.pop_in = pop_in;
     a.pop_out = pop_out;
     a.fit_out = fit_out;
@@ -93,6 +125,16 @@ cudaError_t launch_solve(pa_ctx* ctx, const uint8_t* pop_in, uint8_t* pop_out, i
       a.isl_list = isl->list;
       a.isl_pos = isl->pos;
       a.isl_C = c.islands;
+      if (isl_km) {
+        a.isl_km = 1;
+        a.isl_R = c.recluster;
+        a.isl_iter = c.island_iter;
+        a.isl_fresh = ctx->isl_valid ? 0 : 1;
+        a.isl_label_out = isl_label;
+        a.isl_off_out = isl->off;
+        a.isl_list_out = isl->list;
+        a.isl_pos_out = isl->pos;
+      }
     }
     const bool fin = a.fin;
     const bool chk = ctx->solve_C < 0;
@@ -112,7 +154,7 @@ cudaError_t launch_solve(pa_ctx* ctx, const uint8_t* pop_in, uint8_t* pop_out, i
     if (e == cudaSuccess) ctx->solve_C = C;
     return e;
   }
-  ctx->solve_C = 0;
+  if (!isl_km) ctx->solve_C = 0;  // (the caller of isl_km falls back to launches per block)
   return cudaErrorNotSupported;
 }
 

@@ -9,6 +9,7 @@
 #include <algorithm>
 
 #include "pa_eval_device.cuh"
+#include "pa_island_kmeans.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -56,6 +57,17 @@ struct SolveArgs {
   const int32_t* isl_list;
   const int32_t* isl_pos;
   int isl_C;
+  // re-clustering inside the launch (isl_km): K-means of the population at
+  // every generation whose counter is a multiple of isl_R, and at the first
+  // when isl_fresh (at most isl_iter passes, isl_us user splits; shared
+  // memory at the o_k* offsets); the final labels and member lists are
+  // written back to isl_label_out, isl_off_out, isl_list_out, isl_pos_out
+  int isl_km, isl_R, isl_iter, isl_fresh, isl_us;
+  int o_ksh, o_kpw, o_kcnt, o_klab, o_kchg, o_kgchg, o_ksb;
+  int32_t* isl_label_out;
+  int32_t* isl_off_out;
+  int32_t* isl_list_out;
+  int32_t* isl_pos_out;
 };
 
 template <typename FT>
@@ -317,6 +329,78 @@ __host__ __device__ constexpr int fused_js(int NJ, int maxnp) {
 // pilot of each user) at offset 0 and its inverse INV (L*K bytes, user of
 // each pilot, row by row) at offset XO.  Crossover takes whole rows, so the
 // child's INV rows are its parents' INV rows; a swap mutation updates both.
+// Re-clustering inside the fused solve (island mode with isl_km): the
+// K-means of the cluster's population (each CTA gathers every member's
+// pilots from its owner's records), then every member's label and the
+// islands' member lists (ascending index) and positions in every CTA.
+__device__ __forceinline__ void island_recluster(const SolveArgs& a, unsigned char* smem,
+                                              cg::cluster_group& cluster,
+                                              const unsigned char* popc, int gen, int* ilab,
+                                              int* ipos, int* ilist, int* ioff, int* icnt) {
+  const int N = a.N, L = a.L, K = a.K, C = a.isl_C, LK = L * K, NT = a.NT, MS = a.MS;
+  const int W = (LK + 3) >> 2, NP = N | 1, N4 = (N + 3) & ~3;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+  const int R = (int)cluster.num_blocks();
+  KmView kv;
+  kv.sh = reinterpret_cast<KmShared*>(smem + a.o_ksh);
+  kv.pw = reinterpret_cast<uint32_t*>(smem + a.o_kpw);
+  kv.NP = NP;
+  kv.cnt = reinterpret_cast<uint32_t*>(smem + a.o_kcnt);
+  kv.CWp = ((C + 1) / 2) | 1;
+  kv.lab = reinterpret_cast<int*>(smem + a.o_klab);
+  kv.perm = kv.lab + N4;
+  kv.chg = reinterpret_cast<int*>(smem + a.o_kchg);
+  kv.gchg = reinterpret_cast<int*>(smem + a.o_kgchg);
+  kv.sb = reinterpret_cast<int*>(smem + a.o_ksb);
+  kv.us = a.isl_us;
+  kv.Nr = (N + R - 1) / R;
+  const KmParams kp{N, L, K, C, a.isl_iter, a.seed, gen};
+  uint32_t* pw = kv.pw;
+  const uint32_t kmask = (uint32_t)(K - 1) * 0x01010101u;
+  km_cluster(kv, kp, cluster, [&](int w0, int sw, int ln) {
+    // pilots of users 4w .. 4w+3 of member n: word w of its record (bytes
+    // past the row are the record's zero padding, never read as users)
+    for (int n = w0; n < N; n += sw) {
+      const uint32_t base = dsmem_addr(popc + (n % NT) * MS, n / NT);
+      for (int w = ln; w < W; w += 32) pw[w * NP + n] = __vminu4(ld_dsmem(base + 4 * w), kmask);
+    }
+  });
+  // every CTA's slice is final (written before the last pass's barrier)
+  for (int n = tid; n < N; n += blockDim.x) {
+    int r = 0;
+    while (n >= (int)((long long)N * (r + 1) / R)) ++r;
+    ilab[n] = *cluster.map_shared_rank(kv.lab + n, r);
+  }
+  for (int c = tid; c < C; c += blockDim.x) icnt[c] = 0;
+  __syncthreads();
+  for (int n = tid; n < N; n += blockDim.x) atomicAdd(&icnt[ilab[n]], 1);
+  __syncthreads();
+  if (tid == 0) {
+    int acc = 0;
+    for (int c = 0; c < C; ++c) {
+      ioff[c] = acc;
+      acc += icnt[c];
+    }
+    ioff[C] = acc;
+  }
+  __syncthreads();
+  for (int c = warp; c < C; c += nwarps) {
+    int run = 0;
+    for (int n0 = 0; n0 < N; n0 += 32) {
+      const int n = n0 + lane;
+      const bool in = n < N && ilab[n] == c;
+      const unsigned b = __ballot_sync(0xffffffffu, in);
+      if (in) {
+        const int r = run + __popc(b & ((1u << lane) - 1u));
+        ilist[ioff[c] + r] = n;
+        ipos[n] = r;
+      }
+      run += __popc(b);
+    }
+  }
+  __syncthreads();
+}
+
 template <typename FT, int NJ, int VEC, bool FIN, int MAXNP, bool ISL = false>
 __device__ __forceinline__ void solve_body(const SolveArgs& a, unsigned char* smem, int* elites,
                                            cg::cluster_group& cluster) {
@@ -475,6 +559,8 @@ __device__ __forceinline__ void solve_body(const SolveArgs& a, unsigned char* sm
     // ---- 2. all fitness values and members of generation g are visible
     cluster.sync();
     if (g == a.G) break;
+    if (ISL && a.isl_km && ((g == 0 && a.isl_fresh) || (a.gen0 + g) % a.isl_R == 0))
+      island_recluster(a, smem, cluster, POPp(cur), a.gen0 + g, ilab, ipos, ilist, ioff, ielite);
     const bool small_e = E <= kSmallE;
     // ---- 3. elites (CTA holding slots below E).  For E <= 8 warp 0 alone
     //         finds them (register lists) and then fills the elite slots while
@@ -687,6 +773,14 @@ __device__ __forceinline__ void solve_body(const SolveArgs& a, unsigned char* sm
     const uint8_t* src = cluster.map_shared_rank(POPp(cur), best / NT) + (best % NT) * MS;
     for (int r = lane; r < LK; r += 32) a.best_row[r] = src[r];
     if (lane == 0) *a.best_fit = (double)fit[best];
+  }
+  if (ISL && a.isl_km && rank == 0) {  // the last clustering, for the caller
+    for (int i = tid; i < N; i += blockDim.x) {
+      a.isl_label_out[i] = ilab[i];
+      a.isl_list_out[i] = ilist[i];
+      a.isl_pos_out[i] = ipos[i];
+    }
+    for (int i = tid; i <= iC; i += blockDim.x) a.isl_off_out[i] = ioff[i];
   }
   cluster.sync();  // keep this CTA's shared memory alive for remote readers
   if (a.stamp && rank == 0 && tid == 0) {
