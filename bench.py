@@ -778,9 +778,8 @@ def make_serving_instances(shapes):
 def run_islands(B, inputs, dev, steps=10):
     """The PK-means GA (Alg. 2) on the benchmark instance: C = 5 islands
     found by K-means over the population every 3 generations (Sec. 6.1),
-    N = 256, G = 200, finite-M SINR, FP32 -- the K-means of the population and
-    the island lists, then the generations up to the next re-clustering in
-    one cluster launch of the fused solve in island mode -- beside
+    N = 256, G = 200, finite-M SINR, FP32 -- one cluster launch of the fused
+    solve in island mode with the K-means of the population inside -- beside
     the plain one-population solve of the same instance; plus the island
     K-means alone (one re-clustering of 256 chromosomes)."""
     import numpy as np
@@ -820,9 +819,8 @@ def run_islands(B, inputs, dev, steps=10):
             out[key]["labels_per_island"] = np.bincount(lab.cpu().numpy(), minlength=C).tolist()
         ctx.close()
     out["what"] = ("host wall clock per whole solve (K-means seeding + 200 generations + final "
-                   "evaluation); islands: every third generation one population-K-means and one "
-                   "island-list launch, then the three generations in one cluster launch of the "
-                   "fused solve in island mode")
+                   "evaluation); islands: one cluster launch of the fused solve in island mode, "
+                   "the population K-means every third generation inside it")
     return out
 
 
