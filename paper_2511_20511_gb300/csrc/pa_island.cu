@@ -3,27 +3,28 @@
 // evolves on its own; the partition is re-applied every few generations
 // (Sec. 6.1: every three).
 //
-// Population K-means (k_island_kmeans, one 1024-thread CTA per call).  A
-// chromosome is represented by its one-hot pilot indicators e[u][p] =
-// (X[u] == p), one K-vector per user u.  A centroid of m members is
-// cnt[u][p] / m with cnt the members' pilot counts, and
+// Population K-means.  A chromosome is represented by its one-hot pilot
+// indicators e[u][p] = (X[u] == p), one K-vector per user u.  A centroid of
+// m members is cnt[u][p] / m with cnt the members' pilot counts, and
 //     m^2 |e(n) - cnt/m|^2 = LK m^2 - 2 m S(n) + Q,
 //     S(n) = sum_u cnt[u][X_n[u]],      Q = sum_u sum_p cnt[u][p]^2,
 // an integer, so the nearest centroid is found exactly: distances of two
 // clusters compare by cross-multiplying with the other's m^2 (products below
-// 2^62 for N, L*K <= 4096).  Counts live in shared memory (global memory for
-// large C*L*K*K); a warp computes one member's S for up to eight clusters at
-// a time (lanes over users, then a shuffle sum); the update adds one count
-// per (member, user) with shared-memory atomics, one warp per member --
-// integer sums, so the order does not matter.  When the counts and the population fit in shared
-// memory, a cluster of up to eight CTAs runs it instead (k_island_kmeans_cl):
-// each CTA assigns a slice of the members, keeps its own copy of the counts,
-// and after one cluster barrier per pass replays every CTA's changed members
-// into that copy (the same integer updates in every CTA).  Initial centroids are C distinct members by a
-// partial Fisher-Yates shuffle (Philox tag 4, keyed by the generation);
-// Lloyd passes run until no label changes or the pass limit; an emptied
-// cluster keeps its counts.
-//
+// 2^62 for N, L*K <= 4096).  The population is staged transposed (a word per
+// member and four users, pilots clamped below K); counts are packed 16-bit
+// pairs (one load serves two clusters); a lane takes one member, warps
+// split the users when the members are few (device code in
+// pa_island_kmeans.cuh).  Counts and Q are updated from the members that
+// changed cluster (Q from the values the atomics return).  Initial
+// centroids are C distinct members by a partial Fisher-Yates shuffle
+// (Philox tag 4, keyed by the generation); Lloyd passes run until no label
+// changes or the pass limit; an emptied cluster keeps its counts.
+// k_island_kmeans_cl runs it on a cluster of up to eight CTAs when counts
+// and population fit in shared memory (each CTA assigns a slice of the
+// members and replays every CTA's changed members into its own copy of the
+// counts); k_island_kmeans on one CTA otherwise (counts in global memory
+// for large C*L*K*K, rows read from global memory for large N*L*K).
+
 // Island lists (k_island_lists): members grouped by island in ascending
 // index (off, list) and each member's position in its island (pos), by a
 // count, a prefix over islands and warp-level ranks (__match_any_sync).

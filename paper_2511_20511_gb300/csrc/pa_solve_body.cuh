@@ -1,7 +1,8 @@
 // pa_solve_body.cuh -- the whole-GA-run device code shared by the one-instance
-// kernel (pa_solve.cu) and the batched kernels (pa_solve_batch.cu): member
-// records, elites, tournaments, crossover and mutation around the fused
-// evaluation, and the per-instance launch shape.
+// kernel (pa_solve.cu), its island mode (pa_solve_island.cu) and the batched
+// kernels (pa_solve_batch.cu): member records, elites, tournaments, crossover
+// and mutation around the fused evaluation, the island mode's re-clustering
+// and per-island selection, and the per-instance launch shape.
 #pragma once
 
 #include <cooperative_groups.h>

@@ -1,7 +1,8 @@
-// pa_solve_island.cu -- the fused solve in island mode (Alg. 2): the
-// generations between two re-clusterings in one cluster launch, tournaments
-// and elites within each member's island (k_solve with ISL; the launch and
-// the kernel are those of pa_solve_launch.cuh, instantiated here).
+// pa_solve_island.cu -- the fused solve in island mode (Alg. 2): tournaments
+// and elites within each member's island, and (isl_km) the population
+// K-means every few generations inside the same cluster launch, so that a
+// whole island solve is one launch (k_solve with ISL; the launch and the
+// kernel are those of pa_solve_launch.cuh, instantiated here).
 #include "pa_solve_launch.cuh"
 
 namespace pa {
