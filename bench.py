@@ -325,7 +325,7 @@ def run_ours(args):
     if args.only == "batch":
         insts = c3_instances(B, inputs, 512)
         batch = B.Batch(insts)
-        batch.tune(10)  # the shapes the benchmark's batched section uses
+        batch.tune(100)  # the shapes the benchmark's batched section uses
         for _ in range(args.warmup + args.steps):
             torch.cuda.nvtx.range_push("batch_solve")  # profilers can select the tuned solves
             batch.solve(100)
@@ -511,16 +511,17 @@ def c3_instances(B, inputs, n=512, seed0=0):
     return out
 
 
-def run_batched(B, inputs, G=100, n=512, reps=3):
+def run_batched(B, inputs, G=100, n=512, reps=3, tune_generations=None):
     """512 uneven instances: one batched solve (persistent cluster launches
-    per kernel variant, CUDA graph, tuned cluster sizes) against the same
-    instances solved one launch sequence per instance."""
+    per kernel variant, CUDA graph, shapes tuned on the batch itself with
+    the solve's generation count) against the same instances solved one
+    launch sequence per instance."""
     import numpy as np
     import torch
 
     insts = c3_instances(B, inputs, n)
     batch = B.Batch(insts)
-    chosen = batch.tune(10)
+    chosen = batch.tune(G if tune_generations is None else tune_generations)
     batch.solve(G)  # capture + warm
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -529,7 +530,7 @@ def run_batched(B, inputs, G=100, n=512, reps=3):
     t_batch = (time.perf_counter() - t0) / reps
     rows, fits = batch.solve(G)
     done_ms = np.sort(batch.completion_times_ms())  # per instance, since the batch started
-    _, cta_threads, lat_split, _ = batch.group_tiling()
+    _, cta_threads, lat_split, resident, _ = batch.group_tiling()
     batch.close()
     ctxs = [B.Context(d["cfg"], d["beta"], d["user_xy_mm"], d["bs_xy_mm"]) for d in insts]
     ctxs[0].solve(G)
@@ -562,6 +563,7 @@ def run_batched(B, inputs, G=100, n=512, reps=3):
                         "evals_per_s": evals / t_batch, "cluster_sizes": [int(x) for x in chosen],
                         "cta_threads": [int(x) for x in cta_threads],
                         "latency_split": [int(x) for x in lat_split],
+                        "resident_clusters": [int(x) for x in resident],
                         "completion_ms": {"p50": q(done_ms, 50), "p99": q(done_ms, 99),
                                           "max": float(done_ms[-1]),
                                           "what": "each instance's completion since the batch "

@@ -326,18 +326,20 @@ pa_status pa_batch_load(pa_batch* b, int32_t i, const double* beta, const int32_
  * does: the latency split) or of 256 threads (four per SM, so several
  * instances share an SM), in clusters of 1, 2, 4, 8 or 16 CTAs per
  * instance -- and keep the fastest, judged by the whole batch's time (the
- * groups run concurrently).  chosen (optional, one entry per group)
- * receives the chosen cluster sizes (pa_batch_groups gives the rest).
- * Runs real solves (results are discarded).  Synchronous.
+ * groups run concurrently); then, per group, how many of its persistent
+ * clusters may be resident at once (all that fit, or 7/8 down to 1/2 of
+ * that, leaving SMs to the groups running beside it).  chosen (optional,
+ * one entry per group) receives the chosen cluster sizes (pa_batch_groups
+ * gives the rest).  Runs real solves (results are discarded).  Synchronous.
  */
 pa_status pa_batch_tune(pa_batch* b, int32_t generations, int32_t* chosen);
 
 /* Number of kernel-variant groups, their cluster sizes, CTA sizes
- * (threads) and column splits (1: the latency split), and the group of
- * each instance (each output optional). */
+ * (threads), column splits (1: the latency split) and persistent clusters
+ * launched, and the group of each instance (each output optional). */
 pa_status pa_batch_groups(pa_batch* b, int32_t* n_groups, int32_t* cluster_sizes,
                           int32_t* cta_threads, int32_t* latency_split,
-                          int32_t* group_of_instance);
+                          int32_t* resident_clusters, int32_t* group_of_instance);
 
 /*
  * Solve every instance (Alg. 1 as in pa_solve): best_host receives the best

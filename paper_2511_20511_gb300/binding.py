@@ -78,7 +78,7 @@ _SIGS = {
     "pa_batch_load": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]),
     "pa_batch_tune": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p]),
     "pa_batch_groups": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
-                                  C.c_void_p]),
+                                  C.c_void_p, C.c_void_p]),
     "pa_batch_solve": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p]),
     "pa_batch_context": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_void_p)]),
     "pa_batch_completion_times": (C.c_int, [C.c_void_p, C.c_void_p]),
@@ -428,7 +428,8 @@ class Batch:
 
     def tune(self, generations):
         ng = C.c_int32(0)
-        self._bcheck(lib().pa_batch_groups(self.handle, C.byref(ng), None, None, None, None))
+        self._bcheck(lib().pa_batch_groups(self.handle, C.byref(ng), None, None, None, None,
+                                           None))
         chosen = np.zeros(max(1, ng.value), dtype=np.int32)
         self._bcheck(lib().pa_batch_tune(self.handle, int(generations), _host_ptr(chosen)))
         return chosen[:ng.value]
@@ -440,21 +441,23 @@ class Batch:
 
     def group_shapes(self):
         """(cluster size per group, CTA threads per group, group of each instance)."""
-        cs, th, _, gi = self.group_tiling()
+        cs, th, _, _, gi = self.group_tiling()
         return cs, th, gi
 
     def group_tiling(self):
-        """(cluster size, CTA threads, latency column split per group, group of
-        each instance)."""
+        """(cluster size, CTA threads, latency column split, persistent clusters
+        launched per group, group of each instance)."""
         ng = C.c_int32(0)
-        self._bcheck(lib().pa_batch_groups(self.handle, C.byref(ng), None, None, None, None))
+        self._bcheck(lib().pa_batch_groups(self.handle, C.byref(ng), None, None, None, None,
+                                           None))
         cs = np.zeros(max(1, ng.value), dtype=np.int32)
         th = np.zeros(max(1, ng.value), dtype=np.int32)
         lat = np.zeros(max(1, ng.value), dtype=np.int32)
+        rc = np.zeros(max(1, ng.value), dtype=np.int32)
         gi = np.zeros(self.n, dtype=np.int32)
         self._bcheck(lib().pa_batch_groups(self.handle, None, _host_ptr(cs), _host_ptr(th),
-                                           _host_ptr(lat), _host_ptr(gi)))
-        return cs[:ng.value], th[:ng.value], lat[:ng.value], gi
+                                           _host_ptr(lat), _host_ptr(rc), _host_ptr(gi)))
+        return cs[:ng.value], th[:ng.value], lat[:ng.value], rc[:ng.value], gi
 
     def solve(self, generations):
         best = np.zeros(int(self.offsets[-1]), dtype=np.uint8)

@@ -39,6 +39,7 @@ struct pa_batch {
     int C = 0;
     int threads = 1024;  // CTA size: 1024 (one CTA per SM) or 256 (four per SM)
     bool latency = false;  // 1024-thread CTAs with the one-instance column split
+    int cap8 = 8;  // resident clusters: cap8/8 of what fits (the rest of the GPU for the others)
     int clusters = 0;
     size_t smem = 0;
     std::vector<unsigned char> h_args;
@@ -137,7 +138,7 @@ pa_status build_group_args(pa_batch* b, pa_batch::Group& g, int C, int G, int th
   g.threads = threads;
   g.latency = latency;
   g.smem = smem;
-  g.clusters = std::min<int>((int)g.members.size(), maxc);
+  g.clusters = std::min<int>((int)g.members.size(), std::max(1, maxc * g.cap8 / 8));
   return PA_OK;
 }
 
@@ -398,6 +399,23 @@ pa_status pa_batch_tune(pa_batch* b, int32_t generations, int32_t* chosen) {
         }
       }
     if (st == PA_OK) st = build_group_args(b, g, best_C, generations, best_T, best_lat);
+    // then how much of the GPU the group's persistent clusters may hold at
+    // once: all that fits, or less, leaving SMs to the groups running beside
+    int best_cap = g.cap8;
+    for (int cap8 : {8, 7, 6, 5, 4}) {
+      if (st != PA_OK || cap8 == best_cap) continue;
+      g.cap8 = cap8;
+      st = build_group_args(b, g, best_C, generations, best_T, best_lat);
+      if (st != PA_OK) break;
+      float ms = 0.f;
+      time_all(&ms);
+      if (st == PA_OK && ms < best_ms) {
+        best_ms = ms;
+        best_cap = cap8;
+      }
+    }
+    g.cap8 = best_cap;
+    if (st == PA_OK) st = build_group_args(b, g, best_C, generations, best_T, best_lat);
     if (chosen && st == PA_OK) chosen[k] = best_C;
   }
   for (auto& g : b->groups)  // arguments of one generation until the next solve rebuilds them
@@ -414,13 +432,14 @@ pa_status pa_batch_tune(pa_batch* b, int32_t generations, int32_t* chosen) {
 
 pa_status pa_batch_groups(pa_batch* b, int32_t* n_groups, int32_t* cluster_sizes,
                           int32_t* cta_threads, int32_t* latency_split,
-                          int32_t* group_of_instance) {
+                          int32_t* resident_clusters, int32_t* group_of_instance) {
   if (!b) return PA_EINVAL;
   if (n_groups) *n_groups = (int32_t)b->groups.size();
   for (size_t k = 0; k < b->groups.size(); ++k) {
     if (cluster_sizes) cluster_sizes[k] = b->groups[k].C;
     if (cta_threads) cta_threads[k] = b->groups[k].threads;
     if (latency_split) latency_split[k] = b->groups[k].latency ? 1 : 0;
+    if (resident_clusters) resident_clusters[k] = b->groups[k].clusters;
     if (group_of_instance)
       for (int i : b->groups[k].members) group_of_instance[i] = (int32_t)k;
   }

@@ -126,7 +126,7 @@ def test_null_and_invalid_handles_rejected(B):
     assert lib.pa_batch_create(0, None, None, None, None, None, C.byref(out)) == B.PA_EINVAL
     assert lib.pa_batch_solve(None, 1, None, None) == B.PA_EINVAL
     assert lib.pa_batch_tune(None, 1, None) == B.PA_EINVAL
-    assert lib.pa_batch_groups(None, None, None, None, None, None) == B.PA_EINVAL
+    assert lib.pa_batch_groups(None, None, None, None, None, None, None) == B.PA_EINVAL
     lib.pa_batch_destroy(None)
     cfg = B.pa_config_default(7, 4)
     assert lib.pa_server_create(C.byref(cfg), 0, 1, 1 << 30, None, C.byref(out)) == B.PA_EINVAL
