@@ -148,6 +148,29 @@ def test_island_solve_fp64_trajectory(B, oracle, L, K, N, C, R, E, mode):
     assert (labels == ref["label"]).all()
 
 
+@pytest.mark.parametrize("L,K,N,C,R,E", [(19, 10, 1024, 5, 3, 2), (7, 4, 48, 3, 2, 9)])
+def test_island_solve_fallback_paths_fp64(B, oracle, L, K, N, C, R, E):
+    """The island solve where one launch cannot hold it: N = 1024 (the staged
+    population of the re-clustering does not fit beside the solve: K-means
+    and list kernels between fused launches per block, the K-means from
+    global memory), and E = 9 (island mode takes E <= 8: one generation at a
+    time by the evaluation and island-generation kernels) -- FP64
+    trajectories bit-exact against the oracle."""
+    inst = inputs.instance(L, K, seed=L * K + N)
+    cfg = _cfg(B, L, K, prec=1, mode=1, N=N, E=E, islands=C, recluster=R, seed=21)
+    G = 7
+    with B.Context(cfg, inst["beta"], inst["user_xy_mm"], inst["bs_xy_mm"]) as ctx:
+        best, bf = ctx.solve(G)
+        pop, fit, g = ctx.get_population()
+        labels = B.pa_get_islands(ctx.handle, N)
+    ref = oracle.solve_islands(inst["beta"], _sp(oracle, cfg), _gp(oracle, cfg), G, C, R,
+                               cfg.island_iter, inst["user_xy_mm"], inst["bs_xy_mm"])
+    assert g == G
+    assert (pop == ref["pop"]).all() and (fit == ref["fit"]).all()
+    assert (best == ref["best"]).all() and bf == ref["best_fit"]
+    assert (labels == ref["label"]).all()
+
+
 def test_island_solve_in_pieces_equals_whole(B, oracle):
     """pa_step in pieces (re-clustering keyed by the generation counter)
     gives the same population as one solve."""
