@@ -35,7 +35,9 @@ struct StreamArgs {
 };
 
 constexpr int kStreamThreads = 512;
-template <int JT, int VEC, bool FIN>
+// MINOBJ: the max-min objective (compiled apart, so the sum objective's
+// inner loop carries no objective test).
+template <int JT, int VEC, bool FIN, bool MINOBJ>
 __global__ void __launch_bounds__(kStreamThreads) k_eval_f32_stream(const StreamArgs a) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ __align__(8) uint64_t mbar;
@@ -94,12 +96,12 @@ __global__ void __launch_bounds__(kStreamThreads) k_eval_f32_stream(const Stream
     if (tid < NTK) {
       const int c = tid / K, p = tid - c * K;
       eval_pilot_f32<JT, VEC, FIN, 1>(sm, INV + c * KP + p, NTM * KP, 0, PART + tid * NPR,
-                                      a.obj != 0);
+                                      MINOBJ);
     }
     __syncthreads();
     for (int c = warp; c < nvalid; c += blockDim.x >> 5) {
       const float f =
-          member_value_bounded<32 * NPR>(PART + c * K * NPR, K * NPR, lane, a.obj != 0);
+          member_value_bounded<32 * NPR>(PART + c * K * NPR, K * NPR, lane, MINOBJ);
       if (lane == 0) a.partial[(n0 + c) * a.ntile + t] = f;
     }
     __syncthreads();
@@ -126,9 +128,9 @@ size_t stream_smem(int L, int K, int JT, int RSt, int NTM) {
          (((size_t)L * NTM * inv_pitch(K) + 15) & ~size_t(15));
 }
 
-template <int JT, int VEC, bool FIN>
-cudaError_t run_stream(const StreamArgs& a, size_t smem, int grid, cudaStream_t st) {
-  auto kern = k_eval_f32_stream<JT, VEC, FIN>;
+template <int JT, int VEC, bool FIN, bool MINOBJ>
+cudaError_t run_stream_obj(const StreamArgs& a, size_t smem, int grid, cudaStream_t st) {
+  auto kern = k_eval_f32_stream<JT, VEC, FIN, MINOBJ>;
   static std::atomic<uint64_t> prepared{0};
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -143,6 +145,12 @@ cudaError_t run_stream(const StreamArgs& a, size_t smem, int grid, cudaStream_t 
   kern<<<grid, kStreamThreads, smem, st>>>(a);
   count_launch();
   return cudaGetLastError();
+}
+
+template <int JT, int VEC, bool FIN>
+cudaError_t run_stream(const StreamArgs& a, size_t smem, int grid, cudaStream_t st) {
+  return a.obj ? run_stream_obj<JT, VEC, FIN, true>(a, smem, grid, st)
+               : run_stream_obj<JT, VEC, FIN, false>(a, smem, grid, st);
 }
 
 }  // namespace
