@@ -277,13 +277,12 @@ __device__ __forceinline__ void swap2(uint8_t* row, int K, uint32_t ui, uint32_t
   row[j] = t;
 }
 
-// 32-bit word w of a child: bytes below `split` from parent A, the rest from
-// parent B (row-wise crossover cut at a byte offset).
-__device__ __forceinline__ uint32_t merge_word(uint32_t a, uint32_t b, int w, int64_t split) {
-  const int64_t lo = 4 * (int64_t)w;
-  if (lo + 4 <= split) return a;
-  if (lo >= split) return b;
-  const int na = (int)(split - lo);  // 1..3 bytes from A
+// A child's 32-bit word from its parents' words: the first na bytes from
+// parent A, the rest from parent B (na <= 0: all B; na >= 4: all A) -- the
+// word holding a row-wise crossover cut.
+__device__ __forceinline__ uint32_t merge_word(uint32_t a, uint32_t b, int na) {
+  if (na >= 4) return a;
+  if (na <= 0) return b;
   const uint32_t mask = (1u << (8 * na)) - 1u;
   return (a & mask) | (b & ~mask);
 }
@@ -709,14 +708,20 @@ __device__ __forceinline__ void solve_body(const SolveArgs& a, unsigned char* sm
         const uint32_t rb = dsmem_addr(POPp(cur) + (pb_ % NT) * MS, pb_ / NT);
         for (int v = lane; v < (MS >> 4); v += 32) {
           const uint4 qa = ld_dsmem_v4(ra + 16 * v), qb = ld_dsmem_v4(rb + 16 * v);
-          const int w = 4 * v;
-          const int64_t o0 = 4 * (int64_t)w >= XO ? XO : 0, o1 = 4 * (int64_t)(w + 1) >= XO ? XO : 0;
-          const int64_t o2 = 4 * (int64_t)(w + 2) >= XO ? XO : 0, o3 = 4 * (int64_t)(w + 3) >= XO ? XO : 0;
+          // bytes below sp from A: the cut in X, and the same cut in INV
+          // (16-byte units never straddle XO); only one unit mixes the two
+          const int lo = 16 * v, sp = lo >= XO ? XO + (int)split : (int)split;
           uint4 o;
-          o.x = merge_word(qa.x, qb.x, w, split + o0);
-          o.y = merge_word(qa.y, qb.y, w + 1, split + o1);
-          o.z = merge_word(qa.z, qb.z, w + 2, split + o2);
-          o.w = merge_word(qa.w, qb.w, w + 3, split + o3);
+          if (lo + 16 <= sp) {
+            o = qa;
+          } else if (lo >= sp) {
+            o = qb;
+          } else {
+            o.x = merge_word(qa.x, qb.x, sp - lo);
+            o.y = merge_word(qa.y, qb.y, sp - lo - 4);
+            o.z = merge_word(qa.z, qb.z, sp - lo - 8);
+            o.w = merge_word(qa.w, qb.w, sp - lo - 12);
+          }
           reinterpret_cast<uint4*>(child)[v] = o;
         }
         __syncwarp();
