@@ -506,6 +506,8 @@ __device__ __forceinline__ void solve_body(const SolveArgs& a, unsigned char* sm
   // address) fall in distinct banks
   const int q = (tid / (16 * JS)) * 16 + (tid & 15), h = (tid >> 4) % JS;
   const bool one_chunk = nvalid <= a.CH;
+  // member m lives in CTA m / NT: a shift when NT is a power of two
+  const int nt_shift = (NT & (NT - 1)) == 0 ? __ffs(NT) - 1 : -1;
   const int n_elite_here = isl ? 0 : max(0, min(E - base_n, nvalid));
   const int E_draw = isl ? 0 : E;  // slots below E_draw take no draws (plain elites)
   for (int g = 0;; ++g) {
@@ -704,8 +706,10 @@ __device__ __forceinline__ void solve_body(const SolveArgs& a, unsigned char* sm
           split = (int64_t)cut * K;
         }
         // parents' records from their owners, 16 bytes per lane and load
-        const uint32_t ra = dsmem_addr(POPp(cur) + (pa_ % NT) * MS, pa_ / NT);
-        const uint32_t rb = dsmem_addr(POPp(cur) + (pb_ % NT) * MS, pb_ / NT);
+        const int oa = nt_shift >= 0 ? pa_ >> nt_shift : pa_ / NT;
+        const int ob = nt_shift >= 0 ? pb_ >> nt_shift : pb_ / NT;
+        const uint32_t ra = dsmem_addr(POPp(cur) + (pa_ - oa * NT) * MS, oa);
+        const uint32_t rb = dsmem_addr(POPp(cur) + (pb_ - ob * NT) * MS, ob);
         for (int v = lane; v < (MS >> 4); v += 32) {
           const uint4 qa = ld_dsmem_v4(ra + 16 * v), qb = ld_dsmem_v4(rb + 16 * v);
           // bytes below sp from A: the cut in X, and the same cut in INV
