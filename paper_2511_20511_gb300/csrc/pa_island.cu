@@ -222,7 +222,7 @@ __global__ void __launch_bounds__(kIslandThreads) k_island_kmeans(const KmArgs a
       const int g = t / us, s = t - g * us;
       const int n = g * 32 + lane;
       const int nn = n < N ? n : N - 1;
-      const int w0 = (int)((long long)W * s / us), w1 = (int)((long long)W * (s + 1) / us);
+      const int w0 = W * s / us, w1 = W * (s + 1) / us;
       int best = 0;
       long long bd = 0;
       for (int c0 = 0; c0 < C; c0 += 2 * kKmMaxW) {
@@ -372,7 +372,7 @@ __global__ void __launch_bounds__(kIslandThreads) k_island_kmeans_cl(const KmClA
     }
   });
   const int R = (int)cluster.num_blocks(), rank = (int)cluster.block_rank();
-  const int n_lo = (int)((long long)N * rank / R), n_hi = (int)((long long)N * (rank + 1) / R);
+  const int n_lo = N * rank / R, n_hi = N * (rank + 1) / R;  // N * R < 2^31
   for (int n = n_lo + (int)threadIdx.x; n < n_hi; n += blockDim.x) a.label[n] = v.lab[n];
   if (rank == 0 && threadIdx.x == 0 && a.passes) *a.passes = passes;
   cluster.sync();  // the other CTAs may still read this CTA's lists

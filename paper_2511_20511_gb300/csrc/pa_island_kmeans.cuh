@@ -194,7 +194,7 @@ __device__ __forceinline__ int km_cluster(const KmView& kv, const KmParams& p,
   const int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31, warp = tid >> 5;
   const int nwarps = nthr >> 5;
   const unsigned full = 0xffffffffu;
-  const int n_lo = (int)((long long)N * rank / R), n_hi = (int)((long long)N * (rank + 1) / R);
+  const int n_lo = N * rank / R, n_hi = N * (rank + 1) / R;  // N * R < 2^31
   const int Nr = kv.Nr;
   int* lab = kv.lab;
   int* perm = kv.perm;
@@ -286,7 +286,7 @@ __device__ __forceinline__ int km_cluster(const KmView& kv, const KmParams& p,
       const int g = t / us, s = t - g * us;
       const int n = n_lo + g * 32 + lane;
       const int nn = n < n_hi ? n : n_hi - 1;
-      const int w0 = (int)((long long)W * s / us), w1 = (int)((long long)W * (s + 1) / us);
+      const int w0 = W * s / us, w1 = W * (s + 1) / us;
       int best = 0;
       long long bd = 0;
       for (int c0 = 0; c0 < C; c0 += 2 * kKmMaxW) {

@@ -360,15 +360,18 @@ __device__ __forceinline__ void island_recluster(const SolveArgs& a, unsigned ch
   km_cluster(kv, kp, cluster, [&](int w0, int sw, int ln) {
     // pilots of users 4w .. 4w+3 of member n: word w of its record (bytes
     // past the row are the record's zero padding, never read as users)
+    const int nts = (NT & (NT - 1)) == 0 ? __ffs(NT) - 1 : -1;  // owner by a shift
     for (int n = w0; n < N; n += sw) {
-      const uint32_t base = dsmem_addr(popc + (n % NT) * MS, n / NT);
+      const int r = nts >= 0 ? n >> nts : n / NT;
+      const uint32_t base = dsmem_addr(popc + (n - r * NT) * MS, r);
       for (int w = ln; w < W; w += 32) pw[w * NP + n] = __vminu4(ld_dsmem(base + 4 * w), kmask);
     }
   });
-  // every CTA's slice is final (written before the last pass's barrier)
+  // every CTA's slice is final (written before the last pass's barrier);
+  // member n of CTA r: n < N (r + 1) / R, the smallest such r
   for (int n = tid; n < N; n += blockDim.x) {
-    int r = 0;
-    while (n >= (int)((long long)N * (r + 1) / R)) ++r;
+    int r = (n * R) / N;  // N * R < 2^31
+    while (n >= N * (r + 1) / R) ++r;
     ilab[n] = *cluster.map_shared_rank(kv.lab + n, r);
   }
   for (int c = tid; c < C; c += blockDim.x) icnt[c] = 0;
