@@ -306,6 +306,13 @@ __device__ __forceinline__ uint32_t dsmem_addr(const void* local, int rank) {
   asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
   return r;
 }
+// Remote store of one fitness value (shared::cluster address from mapa).
+__device__ __forceinline__ void st_dsmem_ft(uint32_t addr, float v) {
+  asm volatile("st.shared::cluster.f32 [%0], %1;" : : "r"(addr), "f"(v) : "memory");
+}
+__device__ __forceinline__ void st_dsmem_ft(uint32_t addr, double v) {
+  asm volatile("st.shared::cluster.f64 [%0], %1;" : : "r"(addr), "d"(v) : "memory");
+}
 
 // Column pairs per thread in the fused FP32 evaluation: the largest divisor
 // of NJ/2 not above MAXNP; JS = NJ/2 / NP threads share a (member, pilot).
@@ -501,6 +508,12 @@ __device__ __forceinline__ void solve_body(const SolveArgs& a, unsigned char* sm
   const F32Smem sm{T, OWN, BN, L, K, a.RS, a.M32, a.pc32};
 
   int cur = 0;
+  // lane r's CTA r: its two fitness buffers, mapped once (the fitness push)
+  uint32_t fitr0 = 0, fitr1 = 0;
+  if ((tid & 31) < C) {
+    fitr0 = dsmem_addr(FITp(0), tid & 31);
+    fitr1 = dsmem_addr(FITp(1), tid & 31);
+  }
   const int lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
   const int T_ = a.tour, nblk = a.nblk, E = a.E;
   // FP32 evaluation roles: q = member*K + pilot, column-pair share h.  Each
@@ -541,7 +554,7 @@ __device__ __forceinline__ void solve_body(const SolveArgs& a, unsigned char* sm
           const float f =
               member_value_bounded<16 * NPR>(PART + c * K * NPR, K * NPR, lane, a.obj != 0);
           const int n = base_n + c0 + c;
-          if (lane < C) cluster.map_shared_rank(fit, lane)[n] = (FT)f;
+          if (lane < C) st_dsmem_ft(((g & 1) ? fitr1 : fitr0) + (uint32_t)(sizeof(FT) * n), (FT)f);
         }
       } else {
         for (int i = tid; i < nv * LK; i += blockDim.x) {
