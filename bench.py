@@ -45,7 +45,7 @@ L, K, TAU_P, M_ANT, N_POP, G_GEN, KMEANS_K = 19, 10, 10, 256.0, 256, 200, 10
 BATCH_LOG2 = 20
 # DRAM bytes (read + write) per launch of the two roofline kernels, from one
 # ncu capture of each; None while a kernel has changed since its capture
-TRAFFIC_K_SOLVE = 147_456
+TRAFFIC_K_SOLVE = 146_688
 TRAFFIC_EVAL = 205_056_000
 METRIC = ("chromosome fitness evals/sec and GA gens/sec (L=19,K=10); "
           "p50/p99 solve latency served vs plain")
