@@ -51,7 +51,7 @@ typedef enum {
   PA_ENOMEM = 2,        /* device or host allocation failed               */
   PA_ECUDA = 3,         /* a CUDA call failed (see pa_last_error)         */
   PA_ETIMEOUT = 4,      /* a bounded device wait gave up                  */
-  PA_EUNSUPPORTED = 5,  /* valid but outside what this build implements   */
+  PA_EUNSUPPORTED = 5,  /* valid but outside what the library implements */
   PA_EBUSY = 6          /* resource (slot, memory budget) not available   */
 } pa_status;
 
